@@ -1,0 +1,27 @@
+"""FP64 CPU oracle for the realfast search hot path.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by
+the CPU-baseline leg of the benchmark, never by the engine itself.
+"""
+
+from .realfast_oracle import (  # noqa: F401
+    C_LIGHT,
+    DISP_CONST,
+    EDGE_FULL,
+    EDGE_PARTIAL,
+    ImageStats,
+    OraclePlan,
+    baseline_uvw,
+    cell_table,
+    dedisperse_resample,
+    delay_table,
+    dirty_image_complex,
+    dirty_image_dft,
+    dirty_image_fft,
+    grid_full_plane,
+    image_stats,
+    n_valid_times,
+    round_half_away,
+    search_segment,
+    stokes_i,
+)

@@ -1,0 +1,317 @@
+"""Plain FP64 CPU oracle of the realfast search hot path.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path imports this module:
+only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` call it.  It shares no code with the CUDA engine.
+
+What it computes (Law et al. 2018, "realfast", Sec. 2.2 and Sec. 3.1): for a
+segment of visibilities, for every DM trial, every boxcar width dt and every
+output integration t', a dedispersed, resampled Stokes-I visibility set is
+imaged by nearest-neighbour gridding and a 2D inverse DFT; each dirty image's
+peak is compared with the image noise and images whose peak S/N reaches the
+threshold emit one candidate.
+
+The paper states the pipeline in words only.  The readings taken where it is
+silent are listed with each function; in short:
+
+* delay  delta[d][c] = floor(4.1488e-3 DM_d (f_c^-2 - f_top^-2) / t_int + 1/2)
+  with f in GHz (dispersion law, Sec. 2.1 footnote), evaluated in the fixed
+  FP64 order of :func:`delay_table`.
+* resample  R[d,s,t'][b,c] = sum_{j<dt_s} S[t' dt_s + j + delta[d][c]][b,c],
+  S = mean of the two polarisations (Stokes I, Sec. 3.1).  FULL edge rule
+  t' < floor((nint - max_c delta[d][c]) / dt_s); PARTIAL edge rule
+  t' < floor(nint / dt_s) with samples past the segment given weight 0.
+* grid  (iu, iv) = round-half-away(u_m f_c / c * N cell), same for v; a
+  visibility is on the grid iff |iu| < N/2 and |iv| < N/2; w is ignored.
+* image  I[y][x] = (1/W) sum_{on-grid b,c} Re(R_bc exp(+2 pi i (iu (x - N/2) +
+  iv (y - N/2)) / N)),  W = sum_{on-grid b,c} n_c (samples summed).
+* stats  mu = mean(I), sigma = population std of all N^2 pixels, peak = max I
+  (lowest y N + x on ties), snr = peak / sigma, candidate iff snr >= threshold.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+C_LIGHT = 299792458.0
+DISP_CONST = 4.1488e-3          # s GHz^2 per pc cm^-3 (Sec. 2.1 footnote, refined constant)
+
+EDGE_FULL = "full"
+EDGE_PARTIAL = "partial"
+
+
+# ----------------------------------------------------------------------------
+# Geometry and tables
+# ----------------------------------------------------------------------------
+
+def baseline_uvw(ant_uvw: np.ndarray) -> np.ndarray:
+    """Baseline uvw for every antenna pair (Sec. 2.2: N_bl = N_ant (N_ant - 1) / 2).
+
+    Order: (i, j) with i < j, i outer; uvw_b = uvw_j - uvw_i.
+    """
+    ant = np.asarray(ant_uvw, dtype=np.float64)
+    n = ant.shape[0]
+    rows = []
+    for i in range(n):
+        for j in range(i + 1, n):
+            rows.append(ant[j] - ant[i])
+    return np.array(rows, dtype=np.float64).reshape(-1, 3)
+
+
+def delay_table(dm_list: Sequence[float], freq_hz: Sequence[float], inttime_s: float) -> np.ndarray:
+    """Integer-sample dispersion delays delta[d][c] (Sec. 2.1 footnote).
+
+    tau = 4.1488 ms * DM * (f^-2 - f_top^-2), f in GHz, referenced to the
+    highest channel so that every delay is >= 0, in units of the integration
+    time and rounded half up.  FP64 evaluation order:
+    ((K * dm) * (1/(f*f) - 1/(ft*ft))) / tint with f = f_hz * 1e-9.
+    """
+    f = np.asarray(freq_hz, dtype=np.float64) * 1e-9
+    ft = np.float64(np.max(np.asarray(freq_hz, dtype=np.float64))) * 1e-9
+    dm = np.asarray(dm_list, dtype=np.float64)
+    dinv = (1.0 / (f * f)) - (1.0 / (ft * ft))
+    d = ((DISP_CONST * dm)[:, None] * dinv[None, :]) / np.float64(inttime_s)
+    return np.floor(d + 0.5).astype(np.int64)
+
+
+def round_half_away(x: np.ndarray) -> np.ndarray:
+    """Nearest integer, ties away from zero: sign(x) * floor(|x| + 1/2)."""
+    x = np.asarray(x, dtype=np.float64)
+    return np.where(x >= 0, np.floor(x + 0.5), -np.floor(-x + 0.5)).astype(np.int64)
+
+
+def cell_table(bl_uvw: np.ndarray, freq_hz: Sequence[float], npix: int, cell_rad: float):
+    """Nearest uv cell of every (baseline, channel) and its on-grid flag.
+
+    u in wavelengths is u_m f / c; the cell size is du = 1 / (N cell), so the
+    cell index is round(u_m f / c * N cell).  FP64 order:
+    (u_m * (f / c)) * (N * cell).  Returns iu, iv [nbl, nchan] int64 and
+    ongrid [nbl, nchan] bool (|iu| < N/2 and |iv| < N/2).
+    """
+    f = np.asarray(freq_hz, dtype=np.float64)
+    s = f / C_LIGHT
+    fov = np.float64(npix) * np.float64(cell_rad)
+    u = np.asarray(bl_uvw, dtype=np.float64)[:, 0]
+    v = np.asarray(bl_uvw, dtype=np.float64)[:, 1]
+    iu = round_half_away((u[:, None] * s[None, :]) * fov)
+    iv = round_half_away((v[:, None] * s[None, :]) * fov)
+    half = npix // 2
+    ongrid = (np.abs(iu) < half) & (np.abs(iv) < half)
+    return iu, iv, ongrid
+
+
+def n_valid_times(nint: int, max_delay: int, dt: int, edge: str) -> int:
+    """Number of output integrations t' searched for one (DM, dt) trial.
+
+    FULL: the whole dispersed sweep must lie inside the segment (segments
+    overlap by the largest sweep, Sec. 3.2), so t' < floor((nint - max delay) / dt).
+    PARTIAL: t' < floor(nint / dt); samples past the segment get weight 0.
+    """
+    if edge == EDGE_FULL:
+        span = nint - int(max_delay)
+        return max(span // dt, 0) if span > 0 else 0
+    return nint // dt
+
+
+# ----------------------------------------------------------------------------
+# Per-image arithmetic
+# ----------------------------------------------------------------------------
+
+def stokes_i(vis: np.ndarray) -> np.ndarray:
+    """Stokes I = mean over the polarisation axis (Sec. 3.1, Table 1: two pols).
+
+    vis: complex [nint, nbl, nchan, npol] -> complex128 [nint, nbl, nchan].
+    """
+    v = np.asarray(vis)
+    return v.astype(np.complex128).mean(axis=3)
+
+
+def dedisperse_resample(S: np.ndarray, delays_d: np.ndarray, dt: int, t: int, nint: Optional[int] = None):
+    """R[b,c] = sum_{j<dt} S[t*dt + j + delta[c]][b, c] and n[c] = samples present.
+
+    Samples at index >= nint carry weight 0 (only reachable under PARTIAL).
+    ``S`` is indexed by absolute integration; pass ``nint`` when S holds a
+    longer buffer than the segment.
+    """
+    nint_s = S.shape[0] if nint is None else nint
+    nbl, nchan = S.shape[1], S.shape[2]
+    R = np.zeros((nbl, nchan), dtype=np.complex128)
+    n = np.zeros(nchan, dtype=np.int64)
+    cidx = np.arange(nchan)
+    for j in range(dt):
+        tt = t * dt + j + np.asarray(delays_d, dtype=np.int64)
+        ok = tt < nint_s
+        if not np.any(ok):
+            continue
+        tcl = np.where(ok, tt, 0)
+        samp = S[tcl[None, :], np.arange(nbl)[:, None], cidx[None, :]]
+        R += np.where(ok[None, :], samp, 0)
+        n += ok
+    return R, n
+
+
+def grid_full_plane(R: np.ndarray, iu: np.ndarray, iv: np.ndarray, ongrid: np.ndarray, npix: int) -> np.ndarray:
+    """Full-plane Hermitian uv grid G[v mod N][u mod N] (nearest-neighbour).
+
+    Each on-grid visibility adds R at (iu, iv) and conj(R) at (-iu, -iv), so
+    the sky image is real.
+    """
+    N = npix
+    m = ongrid
+    r = R[m]
+    u = iu[m]
+    v = iv[m]
+    i1 = (v % N) * N + (u % N)
+    i2 = ((-v) % N) * N + ((-u) % N)
+    re = np.bincount(i1, weights=r.real, minlength=N * N) + np.bincount(i2, weights=r.real, minlength=N * N)
+    im = np.bincount(i1, weights=r.imag, minlength=N * N) - np.bincount(i2, weights=r.imag, minlength=N * N)
+    return (re + 1j * im).reshape(N, N)
+
+
+def dirty_image_fft(G: np.ndarray, W: float) -> np.ndarray:
+    """I[y][x] = Re(sum_{v,u} G[v][u] e^{+2 pi i (u (x - N/2) + v (y - N/2)) / N}) / (2W).
+
+    numpy's inverse FFT is used as the DFT step (it divides by N^2, which is
+    multiplied back); the (x - N/2, y - N/2) shift is an fftshift.
+    """
+    N = G.shape[0]
+    raw = np.fft.ifft2(G) * (N * N)
+    return np.fft.fftshift(raw).real / (2.0 * W)
+
+
+def dirty_image_complex(G: np.ndarray) -> np.ndarray:
+    """The shifted complex DFT of the full plane (before taking Re and scaling)."""
+    N = G.shape[0]
+    return np.fft.fftshift(np.fft.ifft2(G) * (N * N))
+
+
+def dirty_image_dft(R: np.ndarray, iu: np.ndarray, iv: np.ndarray, ongrid: np.ndarray, npix: int, W: float) -> np.ndarray:
+    """Brute-force O(N^2 nvis) evaluation of the image definition (small N only)."""
+    N = npix
+    m = ongrid
+    r = R[m]
+    u = iu[m].astype(np.float64)
+    v = iv[m].astype(np.float64)
+    xs = np.arange(N, dtype=np.float64) - N // 2
+    ex = np.exp(2j * np.pi * np.outer(u, xs) / N)       # [nvis, N] over x
+    ey = np.exp(2j * np.pi * np.outer(v, xs) / N)       # [nvis, N] over y
+    img = np.einsum("k,ky,kx->yx", r, ey, ex)
+    return img.real / W
+
+
+@dataclasses.dataclass
+class ImageStats:
+    mean: float
+    sigma: float
+    peak: float
+    x: int
+    y: int
+    snr: float
+
+
+def image_stats(I: np.ndarray) -> ImageStats:
+    """Population mean/std of all pixels, the maximum pixel and peak/sigma (Sec. 3.1).
+
+    Ties for the maximum go to the lowest linear index y N + x.
+    """
+    N = I.shape[1]
+    flat = np.asarray(I, dtype=np.float64).ravel()
+    mu = flat.mean()
+    sigma = float(np.sqrt(np.mean((flat - mu) ** 2)))
+    k = int(np.argmax(flat))
+    peak = float(flat[k])
+    y, x = divmod(k, N)
+    snr = peak / sigma if sigma > 0 else 0.0
+    return ImageStats(float(mu), sigma, peak, x, y, snr)
+
+
+# ----------------------------------------------------------------------------
+# Segment search
+# ----------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class OraclePlan:
+    """Everything fixed for a segment shape (the 'state' of Sec. 3.2)."""
+    ant_uvw: np.ndarray
+    freq_hz: np.ndarray
+    inttime_s: float
+    npix: int
+    cell_rad: float
+    dm_list: np.ndarray
+    dt_list: List[int]
+    threshold: float
+    edge: str = EDGE_FULL
+    npol: int = 2
+
+    def __post_init__(self):
+        self.bl_uvw = baseline_uvw(self.ant_uvw)
+        self.delays = delay_table(self.dm_list, self.freq_hz, self.inttime_s)
+        self.iu, self.iv, self.ongrid = cell_table(self.bl_uvw, self.freq_hz, self.npix, self.cell_rad)
+        self.max_delay = self.delays.max(axis=1)
+
+    @property
+    def nbl(self):
+        return self.bl_uvw.shape[0]
+
+    def n_times(self, nint: int, d: int, s: int) -> int:
+        return n_valid_times(nint, int(self.max_delay[d]), int(self.dt_list[s]), self.edge)
+
+    def image_list(self, nint: int):
+        """All searched images (d, s, t') in (d, s, t') order."""
+        out = []
+        for d in range(len(self.dm_list)):
+            for s in range(len(self.dt_list)):
+                for t in range(self.n_times(nint, d, s)):
+                    out.append((d, s, t))
+        return out
+
+    def count_images(self, nint: int) -> int:
+        return sum(self.n_times(nint, d, s) for d in range(len(self.dm_list)) for s in range(len(self.dt_list)))
+
+    def weight(self, n: np.ndarray) -> float:
+        """W = sum over on-grid (b, c) of the samples summed into R[b, c]."""
+        return float((self.ongrid.sum(axis=0) * n).sum())
+
+    def image(self, S: np.ndarray, d: int, s: int, t: int, nint: Optional[int] = None, method: str = "fft"):
+        """Dirty image of trial (d, s, t') and its weight W (None if W = 0)."""
+        R, n = dedisperse_resample(S, self.delays[d], int(self.dt_list[s]), t, nint)
+        W = self.weight(n)
+        if W <= 0:
+            return None, 0.0
+        if method == "dft":
+            return dirty_image_dft(R, self.iu, self.iv, self.ongrid, self.npix, W), W
+        G = grid_full_plane(R, self.iu, self.iv, self.ongrid, self.npix)
+        return dirty_image_fft(G, W), W
+
+    def candidate(self, d: int, s: int, t: int, st: ImageStats) -> Dict:
+        N = self.npix
+        return dict(dm_idx=d, dt_idx=s, t_idx=t, x=st.x, y=st.y, snr=st.snr, peak=st.peak,
+                    sigma=st.sigma, dm=float(self.dm_list[d]),
+                    l_rad=(st.x - N // 2) * self.cell_rad, m_rad=(st.y - N // 2) * self.cell_rad)
+
+
+def search_segment(plan: OraclePlan, vis: np.ndarray, nint: Optional[int] = None,
+                   images: Optional[Sequence] = None, with_stats: bool = False):
+    """Run the search over every image (or the listed (d, s, t') images).
+
+    Returns the candidate list sorted by (dm_idx, dt_idx, t_idx) and, with
+    ``with_stats``, a dict (d, s, t) -> ImageStats for every imaged trial.
+    """
+    n = vis.shape[0] if nint is None else nint
+    S = stokes_i(vis[:n])
+    todo = plan.image_list(n) if images is None else list(images)
+    cands, stats = [], {}
+    for (d, s, t) in todo:
+        I, W = plan.image(S, d, s, t, n)
+        if I is None:
+            continue
+        st = image_stats(I)
+        if with_stats:
+            stats[(d, s, t)] = st
+        if st.sigma > 0 and st.snr >= plan.threshold:
+            cands.append(plan.candidate(d, s, t, st))
+    cands.sort(key=lambda c: (c["dm_idx"], c["dt_idx"], c["t_idx"]))
+    return (cands, stats) if with_stats else cands
