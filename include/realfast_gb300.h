@@ -1,0 +1,259 @@
+/*
+ * realfast_gb300.h -- C ABI of the GB300 engine for the realfast transient
+ * search hot path (Law et al. 2018, arXiv:1802.03084).
+ *
+ * The engine takes one segment of fast-sampled visibilities and, for every
+ * DM trial, every boxcar width dt and every output integration t', forms a
+ * Stokes-I dirty image by integer-sample dedispersion, boxcar resampling,
+ * nearest-neighbour uv gridding and a 2D inverse FFT, and thresholds the
+ * image peak against the image noise (Sec. 3.1 "Algorithm": a Stokes I image
+ * per DM and time width, thresholded for point sources; Fig. 2: loops over
+ * dispersion and sampling time).  The plan is the immutable "state" of
+ * Sec. 3.2: it is fixed by the metadata (antenna positions, channels,
+ * integration time) and the preferences (image size, DM and dt lists,
+ * threshold), so any candidate can be reproduced from it.
+ *
+ * Conventions used by every entry point:
+ *   - All pointers are plain host or device pointers; sizes are element
+ *     counts unless stated.  No call keeps a pointer it was given after it
+ *     returns, except the plan handle itself.
+ *   - Every call returns an rf_status; no call aborts, prints or throws.
+ *     On failure rf_last_error() gives a thread-local message.
+ *   - A plan is used by one caller at a time: a call made while another call
+ *     on the same plan is in progress returns RF_ERR_BUSY.
+ *   - Device work is issued on the caller's CUDA stream (a cudaStream_t
+ *     passed as void*; NULL means the legacy default stream).  Calls that
+ *     return results on the host synchronise that stream before returning.
+ */
+#ifndef REALFAST_GB300_H
+#define REALFAST_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rf_status {
+  RF_OK = 0,
+  RF_ERR_INVALID_ARG = 1, /* a NULL pointer, a size out of range, a bad flag */
+  RF_ERR_NO_MEMORY = 2,   /* a device or host allocation failed            */
+  RF_ERR_CUDA = 3,        /* a CUDA runtime error (message has the detail) */
+  RF_ERR_SHAPE = 4,       /* nint out of range for the plan                */
+  RF_ERR_CAPACITY = 5,    /* the caller's output array is too small        */
+  RF_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up            */
+  RF_ERR_BUSY = 7,        /* the plan is in use by another call            */
+  RF_ERR_NO_DEVICE = 8    /* no usable CUDA device                         */
+} rf_status;
+
+/* ---- plan flags (rf_plan_desc.flags) ---------------------------------- */
+/* Store the Stokes-I visibilities on the device as FP16 (round to nearest)
+ * instead of FP32; dedispersion sums, gridding and FFT stay FP32. */
+#define RF_STORE_FP16 0x1u
+/* PARTIAL edge rule: search t' < floor(nint/dt) for every DM; samples past
+ * the end of the segment get weight 0.  Default (FULL): only t' whose whole
+ * dispersed sweep lies in the segment, t' < floor((nint - max_c delay)/dt). */
+#define RF_EDGE_PARTIAL 0x2u
+/* Build the host tables only; no device memory is touched.  Such a plan
+ * answers the table queries (rf_plan_info, rf_plan_delays, rf_plan_cells,
+ * rf_count_images) and rejects searches with RF_ERR_INVALID_ARG. */
+#define RF_HOST_ONLY 0x100u
+
+/* ---- search forms (rf_plan_set_form) --------------------------------- */
+#define RF_FORM_BATCHED 0 /* all trials through the fused persistent launch */
+#define RF_FORM_PLAIN 1   /* one unfused launch set per (DM, dt) trial     */
+
+/*
+ * Plan description.  Everything is copied by rf_plan_create; the caller keeps
+ * ownership of the arrays.
+ *
+ * ant_uvw_m  [nant][3] antenna (u, v, w) in metres, row major.  Baseline b
+ *            runs over antenna pairs (i, j), i < j, i outer, and has
+ *            uvw_b = uvw_j - uvw_i (Sec. 2.2: N_bl = N_ant (N_ant - 1)/2).
+ *            w is not used (w-term ignored).
+ * freq_hz    [nchan] channel centre frequencies, any order; the highest is
+ *            the dispersion reference f_top.
+ * npol       1 or 2; with 2 the input is Stokes-I formed as the mean of the
+ *            two polarisations (Sec. 3.1).
+ * inttime_s  integration time in seconds (> 0).
+ * npix       image side N, a power of two in [16, 8192].
+ * cell_rad   pixel size in radians (> 0); the uv cell is 1/(N cell_rad).
+ * dm_list    [ndm] dispersion measures in pc cm^-3, each >= 0.
+ * dt_list    [ndt] boxcar widths in integrations, each in [1, 1024].
+ * threshold_sigma  candidate threshold on peak / sigma (> 0).
+ * flags      RF_STORE_FP16 | RF_EDGE_PARTIAL | RF_HOST_ONLY.
+ * max_nint   largest segment length (integrations) this plan will search;
+ *            sizes the device buffers.
+ * device     CUDA device ordinal the plan lives on.
+ */
+typedef struct rf_plan_desc {
+  int32_t nant;
+  const double* ant_uvw_m;
+  int32_t nchan;
+  const double* freq_hz;
+  int32_t npol;
+  double inttime_s;
+  int32_t npix;
+  double cell_rad;
+  int32_t ndm;
+  const double* dm_list;
+  int32_t ndt;
+  const int32_t* dt_list;
+  double threshold_sigma;
+  uint32_t flags;
+  int32_t max_nint;
+  int32_t device;
+} rf_plan_desc;
+
+/*
+ * One candidate: the peak of the image of trial (dm_idx, dt_idx, t_idx)
+ * whose peak / sigma reached the threshold (Sec. 3.1; at most one per image).
+ * x, y     peak pixel; l_rad = (x - N/2) cell, m_rad = (y - N/2) cell.
+ * peak     peak pixel value (units of the visibilities, a weighted mean).
+ * sigma    population standard deviation of all N^2 pixels.
+ * snr      peak / sigma.
+ * t_idx    output integration t' (start integration t' * dt at f_top).
+ */
+typedef struct rf_candidate {
+  int32_t dm_idx;
+  int32_t dt_idx;
+  int32_t t_idx;
+  int32_t x;
+  int32_t y;
+  float snr;
+  float peak;
+  float sigma;
+  double dm;
+  double l_rad;
+  double m_rad;
+} rf_candidate;
+
+/* Statistics of one searched image (whether or not it became a candidate). */
+typedef struct rf_image_stat {
+  int32_t dm_idx;
+  int32_t dt_idx;
+  int32_t t_idx;
+  int32_t x;
+  int32_t y;
+  float peak;
+  float sigma;
+  float snr;
+  double mean;
+  double weight; /* W: samples summed over on-grid (baseline, channel) */
+} rf_image_stat;
+
+/* Derived plan facts. */
+typedef struct rf_plan_info {
+  int32_t nbl;
+  int32_t nchan;
+  int32_t npix;
+  int32_t ndm;
+  int32_t ndt;
+  int32_t iu_max;        /* largest |u| cell of an on-grid visibility      */
+  int32_t iv_max;        /* largest |v| cell of an on-grid visibility      */
+  int32_t n_offgrid;     /* (baseline, channel) pairs off the grid         */
+  int32_t n_cells;       /* occupied cells of the half plane               */
+  int32_t n_entries;     /* gridding entries (iu = 0 pairs count twice)    */
+  int32_t max_delay;     /* largest delay in integrations over all trials  */
+  int32_t images_per_group; /* consecutive t' imaged together              */
+  uint64_t device_bytes; /* device memory held by the plan                 */
+} rf_plan_info;
+
+/*
+ * rf_plan_create: validate `desc`, build the FP64 host tables (baselines,
+ * delay table of Sec. 2.1's dispersion law rounded to integrations, nearest
+ * uv cells), upload them and allocate the device buffers for segments of up
+ * to max_nint integrations.  On success *out owns all device state.
+ * Errors: RF_ERR_INVALID_ARG (bad desc), RF_ERR_NO_DEVICE, RF_ERR_NO_MEMORY,
+ * RF_ERR_CUDA.  *out is set to NULL on failure.
+ */
+rf_status rf_plan_create(const rf_plan_desc* desc, struct rf_plan** out);
+
+/* rf_plan_destroy: free everything the plan owns.  NULL is accepted.  The
+ * caller must not have work in flight on the plan. */
+rf_status rf_plan_destroy(struct rf_plan* plan);
+
+/* Thread-local message for the last failing call on this thread ("" if none). */
+const char* rf_last_error(void);
+
+/*
+ * rf_search_segment: search one segment (Sec. 3.1-3.2).
+ * vis      [nint][nbl][nchan][npol] complex64 (interleaved float re, im),
+ *          host memory (pinned or pageable) or device memory on the plan's
+ *          device; the kind is detected.  Host data is copied in chunks.
+ * nint     integrations in the segment, 1 <= nint <= max_nint.
+ * stream   cudaStream_t to run on (NULL = default stream).
+ * out      host array of `cap` candidates; receives the candidates sorted by
+ *          (dm_idx, dt_idx, t_idx).
+ * n_out    receives the number of candidates.  If it exceeds cap, the first
+ *          cap are written and RF_ERR_CAPACITY is returned.
+ * Returns after the stream has finished the segment.
+ * Errors: RF_ERR_INVALID_ARG, RF_ERR_SHAPE (nint out of range), RF_ERR_BUSY,
+ * RF_ERR_CAPACITY, RF_ERR_CUDA, RF_ERR_TIMEOUT.
+ */
+rf_status rf_search_segment(struct rf_plan* plan, const void* vis, int32_t nint, void* stream,
+                            rf_candidate* out, size_t cap, size_t* n_out);
+
+/*
+ * rf_search_segment_stats: as rf_search_segment, and also returns the
+ * statistics of every searched image in (dm_idx, dt_idx, t_idx) order in the
+ * host array `stats` of `stats_cap` entries (*n_stats = images searched).
+ * Candidates go to `out` exactly as in rf_search_segment (out may be NULL
+ * when cap is 0).  Meant for verification; it is slower than the search.
+ */
+rf_status rf_search_segment_stats(struct rf_plan* plan, const void* vis, int32_t nint, void* stream,
+                                  rf_candidate* out, size_t cap, size_t* n_out,
+                                  rf_image_stat* stats, size_t stats_cap, size_t* n_stats);
+
+/*
+ * rf_render_images: compute the full dirty images I[y][x] (float32, N x N,
+ * row major, y = v axis) of `n` listed trials.  trials is a host array of n
+ * triples (dm_idx, dt_idx, t_idx); images is a host array of n * N * N floats.
+ * A trial outside the searched set (t_idx beyond the edge rule) or with
+ * weight 0 is rejected with RF_ERR_INVALID_ARG.
+ */
+rf_status rf_render_images(struct rf_plan* plan, const void* vis, int32_t nint, void* stream,
+                           const int32_t* trials, int32_t n, float* images);
+
+/* Select the search form: RF_FORM_BATCHED (default) or RF_FORM_PLAIN. */
+rf_status rf_plan_set_form(struct rf_plan* plan, int32_t form);
+
+/* Derived facts of a plan (see rf_plan_info). */
+rf_status rf_plan_get_info(const struct rf_plan* plan, rf_plan_info* info);
+
+/* Copy the delay table, [ndm][nchan] int32 integrations, to host `out`. */
+rf_status rf_plan_delays(const struct rf_plan* plan, int32_t* out);
+
+/* Copy the nearest cells, [nbl][nchan] each, to host arrays (any may be NULL):
+ * iu, iv the unfolded cell indices and ongrid 1 if |iu| < N/2 and |iv| < N/2. */
+rf_status rf_plan_cells(const struct rf_plan* plan, int32_t* iu, int32_t* iv, uint8_t* ongrid);
+
+/* Number of images the search makes for a segment of nint integrations. */
+rf_status rf_count_images(const struct rf_plan* plan, int32_t nint, int64_t* n_images);
+
+/*
+ * Per-kernel timing.  With profiling enabled a plan brackets every kernel
+ * launch (and host-to-device copy) it issues with a pair of CUDA events on
+ * the caller's stream and, when the call has synchronised, adds the elapsed
+ * time to a per-kernel total.  The totals cover every call since profiling
+ * was last enabled.  rf_plan_get_profile fills up to `cap` records and sets
+ * *n to the number of kernel kinds.
+ */
+typedef struct rf_kernel_profile {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+} rf_kernel_profile;
+
+rf_status rf_plan_set_profiling(struct rf_plan* plan, int32_t enable);
+rf_status rf_plan_get_profile(const struct rf_plan* plan, rf_kernel_profile* out, int32_t cap, int32_t* n);
+
+/* Library version string. */
+const char* rf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REALFAST_GB300_H */

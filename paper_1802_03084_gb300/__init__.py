@@ -1,0 +1,373 @@
+"""Python binding of the realfast GB300 engine (C ABI in include/realfast_gb300.h).
+
+The functions here carry the C names and only marshal arguments: every step
+of the search runs in the CUDA kernels of ``librealfast_gb300.so``.  There is
+no CPU fallback: if the library is missing, :func:`lib` raises.
+
+Device buffers and streams may be PyTorch tensors and streams; host inputs
+may be numpy arrays or (pinned) CPU tensors.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional, Sequence
+
+import numpy as np
+
+from .build import lib_path
+
+__all__ = [
+    "RfError", "RfPlanDesc", "RfCandidate", "RfImageStat", "RfPlanInfo",
+    "lib", "make_desc", "rf_plan_create", "rf_plan_destroy", "rf_search_segment",
+    "rf_search_segment_stats", "rf_render_images", "rf_plan_set_form", "rf_plan_get_info",
+    "rf_plan_delays", "rf_plan_cells", "rf_count_images", "rf_last_error", "rf_version",
+    "rf_plan_set_profiling", "rf_plan_get_profile", "RfKernelProfile",
+    "Plan", "CANDIDATE_DTYPE", "STAT_DTYPE", "declared_symbols",
+    "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
+]
+
+RF_OK = 0
+RF_ERR_INVALID_ARG = 1
+RF_ERR_NO_MEMORY = 2
+RF_ERR_CUDA = 3
+RF_ERR_SHAPE = 4
+RF_ERR_CAPACITY = 5
+RF_ERR_TIMEOUT = 6
+RF_ERR_BUSY = 7
+RF_ERR_NO_DEVICE = 8
+STATUS_NAMES = {0: "RF_OK", 1: "RF_ERR_INVALID_ARG", 2: "RF_ERR_NO_MEMORY", 3: "RF_ERR_CUDA",
+                4: "RF_ERR_SHAPE", 5: "RF_ERR_CAPACITY", 6: "RF_ERR_TIMEOUT", 7: "RF_ERR_BUSY",
+                8: "RF_ERR_NO_DEVICE"}
+
+RF_STORE_FP16 = 0x1
+RF_EDGE_PARTIAL = 0x2
+RF_HOST_ONLY = 0x100
+RF_FORM_BATCHED = 0
+RF_FORM_PLAIN = 1
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "realfast_gb300.h")
+
+
+class RfError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class RfPlanDesc(ctypes.Structure):
+    _fields_ = [
+        ("nant", ctypes.c_int32), ("ant_uvw_m", ctypes.POINTER(ctypes.c_double)),
+        ("nchan", ctypes.c_int32), ("freq_hz", ctypes.POINTER(ctypes.c_double)),
+        ("npol", ctypes.c_int32), ("inttime_s", ctypes.c_double),
+        ("npix", ctypes.c_int32), ("cell_rad", ctypes.c_double),
+        ("ndm", ctypes.c_int32), ("dm_list", ctypes.POINTER(ctypes.c_double)),
+        ("ndt", ctypes.c_int32), ("dt_list", ctypes.POINTER(ctypes.c_int32)),
+        ("threshold_sigma", ctypes.c_double), ("flags", ctypes.c_uint32),
+        ("max_nint", ctypes.c_int32), ("device", ctypes.c_int32),
+    ]
+
+
+class RfCandidate(ctypes.Structure):
+    _fields_ = [("dm_idx", ctypes.c_int32), ("dt_idx", ctypes.c_int32), ("t_idx", ctypes.c_int32),
+                ("x", ctypes.c_int32), ("y", ctypes.c_int32), ("snr", ctypes.c_float),
+                ("peak", ctypes.c_float), ("sigma", ctypes.c_float), ("dm", ctypes.c_double),
+                ("l_rad", ctypes.c_double), ("m_rad", ctypes.c_double)]
+
+
+class RfImageStat(ctypes.Structure):
+    _fields_ = [("dm_idx", ctypes.c_int32), ("dt_idx", ctypes.c_int32), ("t_idx", ctypes.c_int32),
+                ("x", ctypes.c_int32), ("y", ctypes.c_int32), ("peak", ctypes.c_float),
+                ("sigma", ctypes.c_float), ("snr", ctypes.c_float), ("mean", ctypes.c_double),
+                ("weight", ctypes.c_double)]
+
+
+class RfPlanInfo(ctypes.Structure):
+    _fields_ = [("nbl", ctypes.c_int32), ("nchan", ctypes.c_int32), ("npix", ctypes.c_int32),
+                ("ndm", ctypes.c_int32), ("ndt", ctypes.c_int32), ("iu_max", ctypes.c_int32),
+                ("iv_max", ctypes.c_int32), ("n_offgrid", ctypes.c_int32), ("n_cells", ctypes.c_int32),
+                ("n_entries", ctypes.c_int32), ("max_delay", ctypes.c_int32),
+                ("images_per_group", ctypes.c_int32), ("device_bytes", ctypes.c_uint64)]
+
+
+class RfKernelProfile(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+def _np_dtype(struct) -> np.dtype:
+    m = {ctypes.c_int32: "i4", ctypes.c_float: "f4", ctypes.c_double: "f8", ctypes.c_uint64: "u8"}
+    names = [f[0] for f in struct._fields_]
+    fmts = [m[f[1]] for f in struct._fields_]
+    offs = [getattr(struct, n).offset for n in names]
+    return np.dtype({"names": names, "formats": fmts, "offsets": offs, "itemsize": ctypes.sizeof(struct)})
+
+
+CANDIDATE_DTYPE = _np_dtype(RfCandidate)
+STAT_DTYPE = _np_dtype(RfImageStat)
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the engine library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1802_03084_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    S = ctypes.c_size_t
+    sig = {
+        "rf_plan_create": ([ctypes.POINTER(RfPlanDesc), ctypes.POINTER(P)], ctypes.c_int),
+        "rf_plan_destroy": ([P], ctypes.c_int),
+        "rf_last_error": ([], ctypes.c_char_p),
+        "rf_version": ([], ctypes.c_char_p),
+        "rf_search_segment": ([P, P, ctypes.c_int32, P, P, S, ctypes.POINTER(S)], ctypes.c_int),
+        "rf_search_segment_stats": ([P, P, ctypes.c_int32, P, P, S, ctypes.POINTER(S), P, S, ctypes.POINTER(S)],
+                                    ctypes.c_int),
+        "rf_render_images": ([P, P, ctypes.c_int32, P, P, ctypes.c_int32, P], ctypes.c_int),
+        "rf_plan_set_form": ([P, ctypes.c_int32], ctypes.c_int),
+        "rf_plan_get_info": ([P, ctypes.POINTER(RfPlanInfo)], ctypes.c_int),
+        "rf_plan_delays": ([P, P], ctypes.c_int),
+        "rf_plan_cells": ([P, P, P, P], ctypes.c_int),
+        "rf_count_images": ([P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "rf_plan_set_profiling": ([P, ctypes.c_int32], ctypes.c_int),
+        "rf_plan_get_profile": ([P, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _LIB = L
+    return L
+
+
+def declared_symbols() -> list:
+    """Function names declared in include/realfast_gb300.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rf_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(status: int):
+    if status != RF_OK:
+        raise RfError(status, rf_last_error())
+
+
+def rf_last_error() -> str:
+    return lib().rf_last_error().decode()
+
+
+def rf_version() -> str:
+    return lib().rf_version().decode()
+
+
+def make_desc(ant_uvw, freq_hz, inttime_s, npix, cell_rad, dm_list, dt_list, threshold,
+              npol=2, flags=0, max_nint=1, device=0) -> RfPlanDesc:
+    """Build an RfPlanDesc; the numpy arrays it points to are kept on it."""
+    ant = np.ascontiguousarray(ant_uvw, dtype=np.float64)
+    fr = np.ascontiguousarray(freq_hz, dtype=np.float64)
+    dm = np.ascontiguousarray(dm_list, dtype=np.float64)
+    dt = np.ascontiguousarray(dt_list, dtype=np.int32)
+    D = ctypes.POINTER(ctypes.c_double)
+    d = RfPlanDesc(nant=ant.shape[0], ant_uvw_m=ant.ctypes.data_as(D), nchan=fr.shape[0],
+                   freq_hz=fr.ctypes.data_as(D), npol=npol, inttime_s=inttime_s, npix=npix,
+                   cell_rad=cell_rad, ndm=dm.shape[0], dm_list=dm.ctypes.data_as(D), ndt=dt.shape[0],
+                   dt_list=dt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), threshold_sigma=threshold,
+                   flags=flags, max_nint=max_nint, device=device)
+    d._keep = (ant, fr, dm, dt)
+    return d
+
+
+def rf_plan_create(desc: RfPlanDesc) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().rf_plan_create(ctypes.byref(desc), ctypes.byref(h)))
+    return h
+
+
+def rf_plan_destroy(plan) -> None:
+    _check(lib().rf_plan_destroy(plan))
+
+
+def _ptr(x) -> int:
+    """Data pointer of a torch tensor or numpy array (must be C contiguous)."""
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    a = np.asarray(x)
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C contiguous")
+    return a.ctypes.data
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def rf_search_segment(plan, vis, nint: int, stream=None, cap: Optional[int] = None) -> np.ndarray:
+    """Search one segment; returns a structured array (CANDIDATE_DTYPE)."""
+    L = lib()
+    if cap is None:
+        n = ctypes.c_int64()
+        _check(L.rf_count_images(plan, nint, ctypes.byref(n)))
+        cap = max(int(n.value), 1)
+    out = np.zeros(cap, dtype=CANDIDATE_DTYPE)
+    n_out = ctypes.c_size_t()
+    _check(L.rf_search_segment(plan, _ptr(vis), nint, _stream(stream), out.ctypes.data, cap, ctypes.byref(n_out)))
+    return out[:n_out.value]
+
+
+def rf_search_segment_stats(plan, vis, nint: int, stream=None):
+    """Search and also return the statistics of every searched image."""
+    L = lib()
+    n = ctypes.c_int64()
+    _check(L.rf_count_images(plan, nint, ctypes.byref(n)))
+    cap = max(int(n.value), 1)
+    out = np.zeros(cap, dtype=CANDIDATE_DTYPE)
+    st = np.zeros(cap, dtype=STAT_DTYPE)
+    n_out = ctypes.c_size_t()
+    n_st = ctypes.c_size_t()
+    _check(L.rf_search_segment_stats(plan, _ptr(vis), nint, _stream(stream), out.ctypes.data, cap,
+                                     ctypes.byref(n_out), st.ctypes.data, cap, ctypes.byref(n_st)))
+    return out[:n_out.value], st[:n_st.value]
+
+
+def rf_render_images(plan, vis, nint: int, trials: Sequence, npix: int, stream=None) -> np.ndarray:
+    """Full dirty images of the listed (dm_idx, dt_idx, t_idx) trials, [n, N, N] float32."""
+    tr = np.ascontiguousarray(np.asarray(trials, dtype=np.int32).reshape(-1, 3))
+    out = np.zeros((tr.shape[0], npix, npix), dtype=np.float32)
+    _check(lib().rf_render_images(plan, _ptr(vis), nint, _stream(stream), tr.ctypes.data, tr.shape[0],
+                                  out.ctypes.data))
+    return out
+
+
+def rf_plan_set_form(plan, form: int) -> None:
+    _check(lib().rf_plan_set_form(plan, form))
+
+
+def rf_plan_get_info(plan) -> RfPlanInfo:
+    info = RfPlanInfo()
+    _check(lib().rf_plan_get_info(plan, ctypes.byref(info)))
+    return info
+
+
+def rf_plan_delays(plan) -> np.ndarray:
+    info = rf_plan_get_info(plan)
+    out = np.zeros((info.ndm, info.nchan), dtype=np.int32)
+    _check(lib().rf_plan_delays(plan, out.ctypes.data))
+    return out
+
+
+def rf_plan_cells(plan):
+    info = rf_plan_get_info(plan)
+    iu = np.zeros((info.nbl, info.nchan), dtype=np.int32)
+    iv = np.zeros_like(iu)
+    on = np.zeros((info.nbl, info.nchan), dtype=np.uint8)
+    _check(lib().rf_plan_cells(plan, iu.ctypes.data, iv.ctypes.data, on.ctypes.data))
+    return iu, iv, on.astype(bool)
+
+
+def rf_count_images(plan, nint: int) -> int:
+    n = ctypes.c_int64()
+    _check(lib().rf_count_images(plan, nint, ctypes.byref(n)))
+    return int(n.value)
+
+
+def rf_plan_set_profiling(plan, enable: bool) -> None:
+    _check(lib().rf_plan_set_profiling(plan, 1 if enable else 0))
+
+
+def rf_plan_get_profile(plan) -> dict:
+    """{kernel name: (launches, total_ms)} accumulated since profiling was enabled."""
+    arr = (RfKernelProfile * 16)()
+    n = ctypes.c_int32()
+    _check(lib().rf_plan_get_profile(plan, arr, 16, ctypes.byref(n)))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n.value, 16))}
+
+
+class Plan:
+    """Owning wrapper around an rf_plan handle."""
+
+    def __init__(self, ant_uvw, freq_hz, inttime_s, npix, cell_rad, dm_list, dt_list, threshold,
+                 npol=2, flags=0, max_nint=1, device=0):
+        self.desc = make_desc(ant_uvw, freq_hz, inttime_s, npix, cell_rad, dm_list, dt_list, threshold,
+                              npol=npol, flags=flags, max_nint=max_nint, device=device)
+        self.npix = npix
+        self.handle = rf_plan_create(self.desc)
+
+    @classmethod
+    def from_spec(cls, spec, ant_uvw, freq_hz, flags=None, max_nint=None, device=0):
+        """Plan for a ``synth.SegmentSpec``-like object (edge/store fields select flags)."""
+        if flags is None:
+            flags = 0
+            if getattr(spec, "edge", "full") == "partial":
+                flags |= RF_EDGE_PARTIAL
+            if getattr(spec, "store", "fp32") == "fp16":
+                flags |= RF_STORE_FP16
+        return cls(ant_uvw, freq_hz, spec.inttime_s, spec.npix, spec.cell_rad, spec.dm_list, spec.dt_list,
+                   spec.threshold, npol=spec.npol, flags=flags, max_nint=max_nint or spec.nint, device=device)
+
+    def search(self, vis, nint=None, stream=None):
+        return rf_search_segment(self.handle, vis, nint if nint is not None else len(vis), stream)
+
+    def search_stats(self, vis, nint=None, stream=None):
+        return rf_search_segment_stats(self.handle, vis, nint if nint is not None else len(vis), stream)
+
+    def render(self, vis, trials, nint=None, stream=None):
+        return rf_render_images(self.handle, vis, nint if nint is not None else len(vis), trials, self.npix, stream)
+
+    def info(self) -> RfPlanInfo:
+        return rf_plan_get_info(self.handle)
+
+    def delays(self):
+        return rf_plan_delays(self.handle)
+
+    def cells(self):
+        return rf_plan_cells(self.handle)
+
+    def count_images(self, nint: int) -> int:
+        return rf_count_images(self.handle, nint)
+
+    def set_form(self, form: int):
+        rf_plan_set_form(self.handle, form)
+
+    def set_profiling(self, enable: bool = True):
+        rf_plan_set_profiling(self.handle, enable)
+
+    def profile(self) -> dict:
+        return rf_plan_get_profile(self.handle)
+
+    def close(self):
+        if self.handle:
+            rf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

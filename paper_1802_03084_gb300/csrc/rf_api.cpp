@@ -1,0 +1,883 @@
+// rf_api.cpp -- the C ABI of include/realfast_gb300.h: plan construction
+// (FP64 host tables), device buffers, and the orchestration of one segment
+// search.  Compiled with -ffp-contract=off so the FP64 table arithmetic is
+// plain IEEE double in the stated order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "realfast_gb300.h"
+#include "rf_engine.h"
+
+using rf::DevCand;
+using rf::DevStat;
+using rf::GridEntry;
+using rf::Group;
+using rf::SegmentGeom;
+using rf::StatPartial;
+
+namespace {
+
+thread_local std::string g_err;
+
+rf_status fail(rf_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define RF_CUDA(call)                                                                            \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) return fail(RF_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                       __FILE__, __LINE__);                                      \
+  } while (0)
+
+constexpr double kDispConst = 4.1488e-3;  // s GHz^2 per pc cm^-3 (Sec. 2.1 footnote)
+constexpr double kCLight = 299792458.0;   // m/s
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr uint32_t kKnownFlags = RF_STORE_FP16 | RF_EDGE_PARTIAL | RF_HOST_ONLY;
+constexpr size_t kStageBytes = 256ull << 20;   // host->device chunk of raw visibilities
+constexpr size_t kTBudgetBytes = 1024ull << 20;  // column-FFT scratch per wave
+
+// Round half away from zero: sign(x) floor(|x| + 1/2).
+inline double round_half_away(double x) { return x >= 0.0 ? std::floor(x + 0.5) : -std::floor(-x + 0.5); }
+
+inline bool finite(double x) { return std::isfinite(x); }
+
+struct Wave {
+  int g_begin, g_end;
+  int img_begin, img_end;
+};
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// Marks a plan busy for the duration of a call.
+struct BusyGuard {
+  std::atomic<int>* flag;
+  bool owned = false;
+  explicit BusyGuard(std::atomic<int>* f) : flag(f) {
+    int expected = 0;
+    owned = flag->compare_exchange_strong(expected, 1);
+  }
+  ~BusyGuard() {
+    if (owned) flag->store(0);
+  }
+};
+
+enum KernelKind { K_H2D = 0, K_INGEST, K_WEIGHTS, K_GRID_COLFFT, K_ROWFFT_STATS, K_FINALIZE, K_NKINDS };
+const char* const kKindNames[K_NKINDS] = {"h2d_copy", "ingest", "weights", "grid_colfft", "rowfft_stats",
+                                           "finalize"};
+
+// Event-pair timing of every launch a plan issues while profiling is on.
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;  // pairs
+  std::vector<int> kind;        // per pair
+  size_t used = 0;
+  int64_t launches[K_NKINDS] = {};
+  double total_ms[K_NKINDS] = {};
+
+  cudaEvent_t begin(int k, cudaStream_t st) {
+    if (!on) return nullptr;
+    if (used == kind.size()) {
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return nullptr;
+      ev.push_back(a);
+      ev.push_back(b);
+      kind.push_back(k);
+    }
+    kind[used] = k;
+    cudaEventRecord(ev[2 * used], st);
+    return ev[2 * used + 1];
+  }
+  void end(cudaEvent_t e, cudaStream_t st) {
+    if (!on || !e) return;
+    cudaEventRecord(e, st);
+    ++used;
+  }
+  // after the stream has synchronised
+  void collect() {
+    for (size_t i = 0; i < used; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]) == cudaSuccess) {
+        launches[kind[i]]++;
+        total_ms[kind[i]] += ms;
+      } else {
+        cudaGetLastError();
+      }
+    }
+    used = 0;
+  }
+  void reset() {
+    used = 0;
+    for (int k = 0; k < K_NKINDS; ++k) {
+      launches[k] = 0;
+      total_ms[k] = 0.0;
+    }
+  }
+  void destroy() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    ev.clear();
+    kind.clear();
+    used = 0;
+  }
+};
+
+// Brackets one launch with the plan's profiler.
+#define RF_TIMED(prof, kindv, st, call)            \
+  do {                                             \
+    cudaEvent_t e_end_ = (prof).begin(kindv, st);  \
+    RF_CUDA(call);                                 \
+    (prof).end(e_end_, st);                        \
+  } while (0)
+
+}  // namespace
+
+struct rf_plan {
+  // copy of the description
+  int nant = 0, nchan = 0, npol = 0, npix = 0, ndm = 0, ndt = 0, max_nint = 0, device = 0;
+  uint32_t flags = 0;
+  double inttime = 0, cell = 0, threshold = 0;
+  std::vector<double> ant_uvw, freq, dm;
+  std::vector<int> dt;
+  int form = RF_FORM_BATCHED;
+
+  // host tables
+  int nbl = 0;
+  std::vector<double> bl_u, bl_v;
+  std::vector<int32_t> delays;     // [ndm][nchan]
+  std::vector<int32_t> max_delay;  // [ndm]
+  std::vector<int32_t> iu, iv;     // [nbl][nchan]
+  std::vector<uint8_t> ongrid;     // [nbl][nchan]
+  std::vector<int32_t> col_cell_ptr, cell_rc, cell_ent_ptr;
+  std::vector<GridEntry> ent;
+  std::vector<int32_t> ongrid_chan;
+  int n_on = 0, iu_max = 0, iv_max = 0, ncol = 1, n_offgrid = 0;
+  rf::ImageKernelShape shape{};
+
+  // device state
+  bool host_only = false;
+  std::vector<void*> allocs;
+  uint64_t device_bytes = 0;
+  rf::DevTables tb{};
+  void* d_S = nullptr;
+  int nint_pad = 0;
+  float2* d_T = nullptr;
+  int slots_max = 0;
+  StatPartial* d_partials = nullptr;
+  double* d_weight = nullptr;
+  int4* d_img_info = nullptr;
+  Group* d_groups = nullptr;
+  int img_cap = 0, group_cap = 0;
+  DevCand* d_cands = nullptr;
+  int* d_ncand = nullptr;
+  DevStat* d_stats = nullptr;
+  float2* d_stage = nullptr;
+  int stage_nint = 0;
+
+  // image list of the last nint searched
+  int cached_nint = -1;
+  std::vector<int4> img_info;
+  std::vector<Group> groups;
+  std::vector<Wave> waves;
+
+  std::atomic<int> busy{0};
+  Profiler prof;
+
+  template <class T>
+  rf_status dalloc(T** p, size_t count) {
+    void* q = nullptr;
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(RF_ERR_NO_MEMORY, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    allocs.push_back(q);
+    device_bytes += bytes;
+    *p = static_cast<T*>(q);
+    return RF_OK;
+  }
+
+  ~rf_plan() {
+    if (!allocs.empty() || !prof.ev.empty()) {
+      DeviceGuard dg(device);
+      for (void* p : allocs) cudaFree(p);
+      prof.destroy();
+    }
+  }
+};
+
+namespace {
+
+int n_times(const rf_plan* p, int nint, int d, int s) {
+  const int dt = p->dt[s];
+  if (p->flags & RF_EDGE_PARTIAL) return nint / dt;
+  const int span = nint - p->max_delay[d];
+  return span > 0 ? span / dt : 0;
+}
+
+int64_t count_images(const rf_plan* p, int nint) {
+  int64_t n = 0;
+  for (int d = 0; d < p->ndm; ++d)
+    for (int s = 0; s < p->ndt; ++s) n += n_times(p, nint, d, s);
+  return n;
+}
+
+rf_status validate(const rf_plan_desc* d) {
+  if (!d) return fail(RF_ERR_INVALID_ARG, "desc is NULL");
+  if (d->nant < 2 || d->nant > 4096) return fail(RF_ERR_INVALID_ARG, "nant %d out of [2, 4096]", d->nant);
+  if (!d->ant_uvw_m) return fail(RF_ERR_INVALID_ARG, "ant_uvw_m is NULL");
+  if (d->nchan < 1 || d->nchan > 65536) return fail(RF_ERR_INVALID_ARG, "nchan %d out of [1, 65536]", d->nchan);
+  if (!d->freq_hz) return fail(RF_ERR_INVALID_ARG, "freq_hz is NULL");
+  if (d->npol != 1 && d->npol != 2) return fail(RF_ERR_INVALID_ARG, "npol must be 1 or 2");
+  if (!(d->inttime_s > 0.0) || !finite(d->inttime_s)) return fail(RF_ERR_INVALID_ARG, "inttime_s must be > 0");
+  if (d->npix < 16 || d->npix > 8192 || (d->npix & (d->npix - 1)))
+    return fail(RF_ERR_INVALID_ARG, "npix %d is not a power of two in [16, 8192]", d->npix);
+  if (!(d->cell_rad > 0.0) || !finite(d->cell_rad)) return fail(RF_ERR_INVALID_ARG, "cell_rad must be > 0");
+  if (d->ndm < 1 || !d->dm_list) return fail(RF_ERR_INVALID_ARG, "need ndm >= 1 and dm_list");
+  if (d->ndt < 1 || d->ndt > 64 || !d->dt_list) return fail(RF_ERR_INVALID_ARG, "need 1 <= ndt <= 64 and dt_list");
+  if (!(d->threshold_sigma > 0.0) || !finite(d->threshold_sigma))
+    return fail(RF_ERR_INVALID_ARG, "threshold_sigma must be > 0");
+  if (d->flags & ~kKnownFlags) return fail(RF_ERR_INVALID_ARG, "unknown flag bits 0x%x", d->flags & ~kKnownFlags);
+  if (d->max_nint < 1 || d->max_nint > (1 << 24)) return fail(RF_ERR_INVALID_ARG, "max_nint %d out of range", d->max_nint);
+  for (int i = 0; i < 3 * d->nant; ++i)
+    if (!finite(d->ant_uvw_m[i])) return fail(RF_ERR_INVALID_ARG, "ant_uvw_m[%d] is not finite", i);
+  for (int c = 0; c < d->nchan; ++c)
+    if (!(d->freq_hz[c] > 0.0) || !finite(d->freq_hz[c])) return fail(RF_ERR_INVALID_ARG, "freq_hz[%d] must be > 0", c);
+  for (int i = 0; i < d->ndm; ++i)
+    if (!(d->dm_list[i] >= 0.0) || !finite(d->dm_list[i])) return fail(RF_ERR_INVALID_ARG, "dm_list[%d] must be >= 0", i);
+  for (int i = 0; i < d->ndt; ++i)
+    if (d->dt_list[i] < 1 || d->dt_list[i] > 1024) return fail(RF_ERR_INVALID_ARG, "dt_list[%d] out of [1, 1024]", i);
+  const int64_t nbl = (int64_t)d->nant * (d->nant - 1) / 2;
+  if (nbl * d->nchan > (1ll << 28)) return fail(RF_ERR_INVALID_ARG, "nbl * nchan too large");
+  return RF_OK;
+}
+
+// Host tables in FP64 (Sec. 2.1 dispersion law; Sec. 2.2 baselines).
+rf_status build_tables(rf_plan* p) {
+  const int nant = p->nant, nchan = p->nchan, N = p->npix;
+  p->nbl = nant * (nant - 1) / 2;
+  const int nbl = p->nbl;
+  p->bl_u.resize(nbl);
+  p->bl_v.resize(nbl);
+  int b = 0;
+  for (int i = 0; i < nant; ++i)
+    for (int j = i + 1; j < nant; ++j, ++b) {
+      p->bl_u[b] = p->ant_uvw[3 * j + 0] - p->ant_uvw[3 * i + 0];
+      p->bl_v[b] = p->ant_uvw[3 * j + 1] - p->ant_uvw[3 * i + 1];
+    }
+
+  // delay[d][c] = floor(((K dm) (1/(f f) - 1/(ft ft))) / tint + 1/2), f in GHz
+  double ftop_hz = p->freq[0];
+  for (double f : p->freq) ftop_hz = std::max(ftop_hz, f);
+  const double ft = ftop_hz * 1e-9;
+  std::vector<double> dinv(nchan);
+  for (int c = 0; c < nchan; ++c) {
+    const double f = p->freq[c] * 1e-9;
+    dinv[c] = (1.0 / (f * f)) - (1.0 / (ft * ft));
+  }
+  p->delays.assign((size_t)p->ndm * nchan, 0);
+  p->max_delay.assign(p->ndm, 0);
+  for (int d = 0; d < p->ndm; ++d) {
+    const double kd = kDispConst * p->dm[d];
+    int mx = 0;
+    for (int c = 0; c < nchan; ++c) {
+      const double x = (kd * dinv[c]) / p->inttime;
+      const double r = std::floor(x + 0.5);
+      if (!(r >= 0.0) || r > (double)(1 << 26)) return fail(RF_ERR_INVALID_ARG, "delay of DM %g out of range", p->dm[d]);
+      const int v = (int)r;
+      p->delays[(size_t)d * nchan + c] = v;
+      mx = std::max(mx, v);
+    }
+    p->max_delay[d] = mx;
+  }
+
+  // nearest cells: i = round_half_away((u_m (f / c)) (N cell))
+  const double fov = (double)N * p->cell;
+  p->iu.assign((size_t)nbl * nchan, 0);
+  p->iv.assign((size_t)nbl * nchan, 0);
+  p->ongrid.assign((size_t)nbl * nchan, 0);
+  p->ongrid_chan.assign(nchan, 0);
+  const int half = N / 2;
+  p->n_on = 0;
+  p->n_offgrid = 0;
+  p->iu_max = 0;
+  p->iv_max = 0;
+  for (int bb = 0; bb < nbl; ++bb)
+    for (int c = 0; c < nchan; ++c) {
+      const double s = p->freq[c] / kCLight;
+      const double xu = (p->bl_u[bb] * s) * fov;
+      const double xv = (p->bl_v[bb] * s) * fov;
+      const double ru = round_half_away(xu), rv = round_half_away(xv);
+      const size_t k = (size_t)bb * nchan + c;
+      const bool on = std::fabs(ru) < half && std::fabs(rv) < half;
+      p->iu[k] = on ? (int)ru : (int)std::max(-2147483647.0, std::min(2147483647.0, ru));
+      p->iv[k] = on ? (int)rv : (int)std::max(-2147483647.0, std::min(2147483647.0, rv));
+      p->ongrid[k] = on ? 1 : 0;
+      if (on) {
+        p->n_on++;
+        p->ongrid_chan[c]++;
+        p->iu_max = std::max(p->iu_max, std::abs((int)ru));
+        p->iv_max = std::max(p->iv_max, std::abs((int)rv));
+      } else {
+        p->n_offgrid++;
+      }
+    }
+
+  // half-plane columns 0..iu_max: entries sorted by (col, row, bc, flags)
+  struct E {
+    int col, row, bc, flags;
+  };
+  std::vector<E> es;
+  es.reserve((size_t)p->n_on + nbl);
+  auto mod = [N](int x) { return ((x % N) + N) % N; };
+  for (int bb = 0; bb < nbl; ++bb)
+    for (int c = 0; c < nchan; ++c) {
+      const size_t k = (size_t)bb * nchan + c;
+      if (!p->ongrid[k]) continue;
+      const int u = p->iu[k], v = p->iv[k];
+      const int neg = ((u + v) & 1) ? rf::ENT_NEG : 0;
+      const int bc = c * nbl + bb;
+      if (u > 0) {
+        es.push_back({u, mod(v), bc, neg});
+      } else if (u < 0) {
+        es.push_back({-u, mod(-v), bc, rf::ENT_CONJ | neg});
+      } else {
+        es.push_back({0, mod(v), bc, neg});
+        es.push_back({0, mod(-v), bc, rf::ENT_CONJ | neg});
+      }
+    }
+  std::sort(es.begin(), es.end(), [](const E& a, const E& b2) {
+    if (a.col != b2.col) return a.col < b2.col;
+    if (a.row != b2.row) return a.row < b2.row;
+    if (a.bc != b2.bc) return a.bc < b2.bc;
+    return a.flags < b2.flags;
+  });
+  p->ncol = p->n_on > 0 ? p->iu_max + 1 : 1;
+  p->col_cell_ptr.assign(p->ncol + 1, 0);
+  p->cell_rc.clear();
+  p->cell_ent_ptr.clear();
+  p->ent.clear();
+  p->ent.reserve(es.size());
+  size_t i = 0;
+  for (int col = 0; col < p->ncol; ++col) {
+    p->col_cell_ptr[col] = (int)p->cell_rc.size();
+    while (i < es.size() && es[i].col == col) {
+      const int row = es[i].row;
+      p->cell_rc.push_back((col << 13) | row);
+      p->cell_ent_ptr.push_back((int)p->ent.size());
+      while (i < es.size() && es[i].col == col && es[i].row == row) {
+        const int c = es[i].bc / nbl;
+        p->ent.push_back({es[i].bc, (c << 2) | es[i].flags});
+        ++i;
+      }
+    }
+  }
+  p->col_cell_ptr[p->ncol] = (int)p->cell_rc.size();
+  p->cell_ent_ptr.push_back((int)p->ent.size());
+  if (!rf::image_kernel_shape(N, &p->shape)) return fail(RF_ERR_INVALID_ARG, "npix %d has no kernel", N);
+  return RF_OK;
+}
+
+// Image and group lists for a segment of nint integrations, in (d, s, t') order.
+void build_lists(rf_plan* p, int nint) {
+  const int B = p->shape.images_per_group;
+  p->img_info.clear();
+  p->groups.clear();
+  p->waves.clear();
+  for (int d = 0; d < p->ndm; ++d)
+    for (int s = 0; s < p->ndt; ++s) {
+      const int nt = n_times(p, nint, d, s);
+      for (int t0 = 0; t0 < nt; t0 += B) {
+        Group g{};
+        g.d = d;
+        g.s = s;
+        g.t0 = t0;
+        g.nimg = std::min(B, nt - t0);
+        g.img0 = (int)p->img_info.size();
+        p->groups.push_back(g);
+        for (int k = 0; k < g.nimg; ++k) p->img_info.push_back(make_int4(d, s, t0 + k, 0));
+      }
+    }
+  Wave w{0, 0, 0, 0};
+  for (int gi = 0; gi < (int)p->groups.size(); ++gi) {
+    const Group& g = p->groups[gi];
+    if (g.img0 + g.nimg - w.img_begin > p->slots_max) {
+      w.g_end = gi;
+      w.img_end = g.img0;
+      p->waves.push_back(w);
+      w = Wave{gi, gi, g.img0, g.img0};
+    }
+  }
+  w.g_end = (int)p->groups.size();
+  w.img_end = (int)p->img_info.size();
+  if (w.img_end > w.img_begin) p->waves.push_back(w);
+  p->cached_nint = nint;
+}
+
+rf_status alloc_device(rf_plan* p) {
+  const int N = p->npix;
+  auto up = [&](auto** dst, const auto& vec) -> rf_status {
+    using T = typename std::decay<decltype(vec[0])>::type;
+    T* d = nullptr;
+    rf_status s = p->dalloc(&d, vec.size());
+    if (s != RF_OK) return s;
+    if (!vec.empty()) RF_CUDA(cudaMemcpy(d, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice));
+    *dst = d;
+    return RF_OK;
+  };
+  int32_t *d_delays, *d_dt, *d_ccp, *d_crc, *d_cep, *d_ogc;
+  GridEntry* d_ent;
+  rf_status s;
+  if ((s = up(&d_delays, p->delays)) != RF_OK) return s;
+  std::vector<int32_t> dtv(p->dt.begin(), p->dt.end());
+  if ((s = up(&d_dt, dtv)) != RF_OK) return s;
+  if ((s = up(&d_ccp, p->col_cell_ptr)) != RF_OK) return s;
+  if ((s = up(&d_crc, p->cell_rc)) != RF_OK) return s;
+  if ((s = up(&d_cep, p->cell_ent_ptr)) != RF_OK) return s;
+  if ((s = up(&d_ent, p->ent)) != RF_OK) return s;
+  if ((s = up(&d_ogc, p->ongrid_chan)) != RF_OK) return s;
+  std::vector<float2> tw(N);
+  for (int m = 0; m < N; ++m) {
+    const double a = kTwoPi * (double)m / (double)N;
+    tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  float2* d_tw;
+  if ((s = up(&d_tw, tw)) != RF_OK) return s;
+  p->tb.delays = d_delays;
+  p->tb.dt_list = d_dt;
+  p->tb.col_cell_ptr = d_ccp;
+  p->tb.cell_rc = d_crc;
+  p->tb.cell_ent_ptr = d_cep;
+  p->tb.ent = d_ent;
+  p->tb.ongrid_chan = d_ogc;
+  p->tb.twiddle = d_tw;
+
+  // Stokes-I time series S[c * nbl + b][t]
+  p->nint_pad = (p->max_nint + 31) / 32 * 32;
+  const size_t esz = (p->flags & RF_STORE_FP16) ? 4 : 8;
+  unsigned char* dS;
+  if ((s = p->dalloc(&dS, (size_t)p->nbl * p->nchan * p->nint_pad * esz)) != RF_OK) return s;
+  p->d_S = dS;
+
+  // image lists for the largest segment
+  const int64_t nimg_max = count_images(p, p->max_nint);
+  if (nimg_max > (1ll << 30)) return fail(RF_ERR_INVALID_ARG, "too many images per segment (%lld)", (long long)nimg_max);
+  p->img_cap = (int)std::max<int64_t>(nimg_max, 1);
+  const int B = p->shape.images_per_group;
+  p->group_cap = p->img_cap;  // at most one group per image
+  if ((s = p->dalloc(&p->d_img_info, p->img_cap)) != RF_OK) return s;
+  if ((s = p->dalloc(&p->d_groups, p->group_cap)) != RF_OK) return s;
+  if ((s = p->dalloc(&p->d_weight, p->img_cap)) != RF_OK) return s;
+  if ((s = p->dalloc(&p->d_cands, p->img_cap)) != RF_OK) return s;
+  if ((s = p->dalloc(&p->d_ncand, 1)) != RF_OK) return s;
+
+  // column-FFT scratch, whole groups per wave
+  const size_t per_slot = (size_t)p->ncol * N * sizeof(float2);
+  int slots = (int)std::min<size_t>(kTBudgetBytes / per_slot, (size_t)p->img_cap);
+  slots = std::min(slots, 32768);  // images per wave ride on gridDim.y
+  slots = std::max(slots, B);
+  p->slots_max = slots;
+  if ((s = p->dalloc(&p->d_T, (size_t)slots * p->ncol * N)) != RF_OK) return s;
+  const int nrb = N / p->shape.rows_per_cta;
+  if ((s = p->dalloc(&p->d_partials, (size_t)slots * nrb)) != RF_OK) return s;
+
+  // host->device staging of raw visibilities
+  const size_t per_int = (size_t)p->nbl * p->nchan * p->npol * sizeof(float2);
+  p->stage_nint = (int)std::max<size_t>(1, std::min<size_t>(kStageBytes / per_int, (size_t)p->max_nint));
+  if ((s = p->dalloc(&p->d_stage, (size_t)p->stage_nint * p->nbl * p->nchan * p->npol)) != RF_OK) return s;
+  return RF_OK;
+}
+
+SegmentGeom geom(const rf_plan* p, int nint) {
+  SegmentGeom g;
+  g.nint = nint;
+  g.nint_pad = p->nint_pad;
+  g.nbl = p->nbl;
+  g.nchan = p->nchan;
+  g.npix = p->npix;
+  g.ncol = p->ncol;
+  g.ndm = p->ndm;
+  g.fp16 = (p->flags & RF_STORE_FP16) != 0;
+  return g;
+}
+
+// Copy (if on the host) and ingest the segment into S.
+rf_status ingest(rf_plan* p, const void* vis, int nint, cudaStream_t st) {
+  cudaPointerAttributes attr;
+  bool on_device = false;
+  if (cudaPointerGetAttributes(&attr, vis) == cudaSuccess) {
+    on_device = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+    if (on_device && attr.type == cudaMemoryTypeDevice && attr.device != p->device)
+      return fail(RF_ERR_INVALID_ARG, "vis is on device %d, plan is on device %d", attr.device, p->device);
+  } else {
+    cudaGetLastError();
+  }
+  const SegmentGeom g = geom(p, nint);
+  if (on_device) {
+    if ((uintptr_t)vis % 16 != 0) return fail(RF_ERR_INVALID_ARG, "device vis must be 16-byte aligned");
+    RF_TIMED(p->prof, K_INGEST, st, rf::launch_ingest(static_cast<const float2*>(vis), nint, 0, p->npol, g, p->d_S, st));
+    return RF_OK;
+  }
+  const size_t per_int = (size_t)p->nbl * p->nchan * p->npol * sizeof(float2);
+  const unsigned char* src = static_cast<const unsigned char*>(vis);
+  for (int t = 0; t < nint; t += p->stage_nint) {
+    const int nt = std::min(p->stage_nint, nint - t);
+    RF_TIMED(p->prof, K_H2D, st,
+             cudaMemcpyAsync(p->d_stage, src + (size_t)t * per_int, (size_t)nt * per_int, cudaMemcpyHostToDevice, st));
+    RF_TIMED(p->prof, K_INGEST, st, rf::launch_ingest(p->d_stage, nt, t, p->npol, g, p->d_S, st));
+  }
+  return RF_OK;
+}
+
+// Pass A / pass B / finalize over the image list currently on the device.
+rf_status run_waves(rf_plan* p, int nint, const std::vector<Wave>& waves, int nimg_total, DevStat* d_stats,
+                    float* d_images, cudaStream_t st) {
+  const SegmentGeom g = geom(p, nint);
+  RF_TIMED(p->prof, K_WEIGHTS, st,
+           rf::launch_weights(p->d_img_info, nimg_total, (p->flags & RF_EDGE_PARTIAL) != 0, g, p->tb,
+                              (double)p->n_on, p->d_weight, st));
+  for (const Wave& w : waves) {
+    const int ng = w.g_end - w.g_begin;
+    const int ni = w.img_end - w.img_begin;
+    RF_TIMED(p->prof, K_GRID_COLFFT, st,
+             rf::launch_grid_colfft(g, p->tb, p->d_S, p->d_groups, w.g_begin, ng, w.img_begin, p->d_T, st));
+    float* im = d_images ? d_images + (size_t)w.img_begin * p->npix * p->npix : nullptr;
+    RF_TIMED(p->prof, K_ROWFFT_STATS, st,
+             rf::launch_rowfft_stats(g, p->tb, p->d_T, ni, w.img_begin, p->d_weight, p->d_partials, im, st));
+    RF_TIMED(p->prof, K_FINALIZE, st,
+             rf::launch_finalize(g, p->d_partials, p->d_img_info, p->d_weight, ni, w.img_begin, p->threshold,
+                                 p->d_cands, p->d_ncand, p->img_cap, d_stats, st));
+  }
+  return RF_OK;
+}
+
+rf_status search_impl(rf_plan* p, const void* vis, int nint, void* stream, rf_candidate* out, size_t cap,
+                      size_t* n_out, bool want_stats, rf_image_stat* stats, size_t stats_cap, size_t* n_stats) {
+  if (!p) return fail(RF_ERR_INVALID_ARG, "plan is NULL");
+  if (p->host_only) return fail(RF_ERR_INVALID_ARG, "plan was created with RF_HOST_ONLY");
+  if (!vis) return fail(RF_ERR_INVALID_ARG, "vis is NULL");
+  if (!n_out) return fail(RF_ERR_INVALID_ARG, "n_out is NULL");
+  if (cap > 0 && !out) return fail(RF_ERR_INVALID_ARG, "out is NULL with cap > 0");
+  if (nint < 1 || nint > p->max_nint) return fail(RF_ERR_SHAPE, "nint %d out of [1, %d]", nint, p->max_nint);
+  if (p->form != RF_FORM_BATCHED) return fail(RF_ERR_INVALID_ARG, "search form %d not available", p->form);
+  BusyGuard bg(&p->busy);
+  if (!bg.owned) return fail(RF_ERR_BUSY, "plan is in use by another call");
+  DeviceGuard dg(p->device);
+  if (!dg.ok) return fail(RF_ERR_CUDA, "cannot select device %d", p->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  *n_out = 0;
+
+  rf_status s = ingest(p, vis, nint, st);
+  if (s != RF_OK) return s;
+  if (p->cached_nint != nint) {
+    build_lists(p, nint);
+    if (!p->img_info.empty()) {
+      RF_CUDA(cudaMemcpyAsync(p->d_img_info, p->img_info.data(), p->img_info.size() * sizeof(int4),
+                              cudaMemcpyHostToDevice, st));
+      RF_CUDA(cudaMemcpyAsync(p->d_groups, p->groups.data(), p->groups.size() * sizeof(Group),
+                              cudaMemcpyHostToDevice, st));
+    }
+  }
+  const int nimg = (int)p->img_info.size();
+  DevStat* d_stats = nullptr;
+  if (want_stats && stats) {
+    if (!p->d_stats) {
+      s = p->dalloc(&p->d_stats, p->img_cap);
+      if (s != RF_OK) return s;
+    }
+    d_stats = p->d_stats;
+  }
+  RF_CUDA(cudaMemsetAsync(p->d_ncand, 0, sizeof(int), st));
+  if (nimg > 0) {
+    s = run_waves(p, nint, p->waves, nimg, d_stats, nullptr, st);
+    if (s != RF_OK) return s;
+  }
+  int ncand = 0;
+  RF_CUDA(cudaMemcpyAsync(&ncand, p->d_ncand, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RF_CUDA(cudaStreamSynchronize(st));
+  ncand = std::min(ncand, p->img_cap);
+  std::vector<DevCand> dc(ncand);
+  if (ncand > 0)
+    RF_CUDA(cudaMemcpyAsync(dc.data(), p->d_cands, ncand * sizeof(DevCand), cudaMemcpyDeviceToHost, st));
+  std::vector<DevStat> ds;
+  if (d_stats && nimg > 0) {
+    ds.resize(nimg);
+    RF_CUDA(cudaMemcpyAsync(ds.data(), d_stats, (size_t)nimg * sizeof(DevStat), cudaMemcpyDeviceToHost, st));
+  }
+  RF_CUDA(cudaStreamSynchronize(st));
+  p->prof.collect();
+  std::sort(dc.begin(), dc.end(), [](const DevCand& a, const DevCand& b) {
+    if (a.d != b.d) return a.d < b.d;
+    if (a.s != b.s) return a.s < b.s;
+    return a.t < b.t;
+  });
+  const int half = p->npix / 2;
+  const size_t nw = std::min<size_t>(cap, dc.size());
+  for (size_t k = 0; k < nw; ++k) {
+    rf_candidate& c = out[k];
+    c.dm_idx = dc[k].d;
+    c.dt_idx = dc[k].s;
+    c.t_idx = dc[k].t;
+    c.x = dc[k].x;
+    c.y = dc[k].y;
+    c.snr = dc[k].snr;
+    c.peak = dc[k].peak;
+    c.sigma = dc[k].sigma;
+    c.dm = p->dm[dc[k].d];
+    c.l_rad = (double)(dc[k].x - half) * p->cell;
+    c.m_rad = (double)(dc[k].y - half) * p->cell;
+  }
+  *n_out = dc.size();
+  if (want_stats && n_stats) *n_stats = (size_t)nimg;
+  if (d_stats) {
+    const size_t ns = std::min<size_t>(stats_cap, (size_t)nimg);
+    for (size_t k = 0; k < ns; ++k) {
+      rf_image_stat& o = stats[k];
+      o.dm_idx = p->img_info[k].x;
+      o.dt_idx = p->img_info[k].y;
+      o.t_idx = p->img_info[k].z;
+      o.x = ds[k].x;
+      o.y = ds[k].y;
+      o.peak = ds[k].peak;
+      o.sigma = ds[k].sigma;
+      o.snr = ds[k].snr;
+      o.mean = ds[k].mean;
+      o.weight = ds[k].weight;
+    }
+    if ((size_t)nimg > stats_cap) return fail(RF_ERR_CAPACITY, "%d image stats, capacity %zu", nimg, stats_cap);
+  }
+  if (dc.size() > cap) return fail(RF_ERR_CAPACITY, "%zu candidates, capacity %zu", dc.size(), cap);
+  return RF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rf_last_error(void) { return g_err.c_str(); }
+
+const char* rf_version(void) { return "realfast_gb300 0.1.0 (sm_103a)"; }
+
+rf_status rf_plan_create(const rf_plan_desc* desc, rf_plan** out) {
+  if (!out) return fail(RF_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  rf_status s = validate(desc);
+  if (s != RF_OK) return s;
+  rf_plan* p = new (std::nothrow) rf_plan();
+  if (!p) return fail(RF_ERR_NO_MEMORY, "host allocation failed");
+  p->nant = desc->nant;
+  p->nchan = desc->nchan;
+  p->npol = desc->npol;
+  p->npix = desc->npix;
+  p->ndm = desc->ndm;
+  p->ndt = desc->ndt;
+  p->max_nint = desc->max_nint;
+  p->device = desc->device;
+  p->flags = desc->flags;
+  p->inttime = desc->inttime_s;
+  p->cell = desc->cell_rad;
+  p->threshold = desc->threshold_sigma;
+  p->ant_uvw.assign(desc->ant_uvw_m, desc->ant_uvw_m + 3 * desc->nant);
+  p->freq.assign(desc->freq_hz, desc->freq_hz + desc->nchan);
+  p->dm.assign(desc->dm_list, desc->dm_list + desc->ndm);
+  p->dt.assign(desc->dt_list, desc->dt_list + desc->ndt);
+  p->host_only = (desc->flags & RF_HOST_ONLY) != 0;
+  s = build_tables(p);
+  if (s != RF_OK) {
+    delete p;
+    return s;
+  }
+  if (!p->host_only) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+      cudaGetLastError();
+      delete p;
+      return fail(RF_ERR_NO_DEVICE, "no CUDA device available");
+    }
+    if (p->device < 0 || p->device >= ndev) {
+      delete p;
+      return fail(RF_ERR_INVALID_ARG, "device %d out of [0, %d)", desc->device, ndev);
+    }
+    DeviceGuard dg(p->device);
+    if (!dg.ok) {
+      delete p;
+      return fail(RF_ERR_CUDA, "cannot select device %d", desc->device);
+    }
+    s = alloc_device(p);
+    if (s != RF_OK) {
+      std::string keep = g_err;
+      delete p;
+      g_err = keep;
+      return s;
+    }
+  }
+  *out = p;
+  return RF_OK;
+}
+
+rf_status rf_plan_destroy(rf_plan* plan) {
+  if (!plan) return RF_OK;
+  if (plan->busy.load() != 0) return fail(RF_ERR_BUSY, "plan is in use");
+  delete plan;
+  return RF_OK;
+}
+
+rf_status rf_search_segment(rf_plan* plan, const void* vis, int32_t nint, void* stream, rf_candidate* out,
+                            size_t cap, size_t* n_out) {
+  return search_impl(plan, vis, nint, stream, out, cap, n_out, false, nullptr, 0, nullptr);
+}
+
+rf_status rf_search_segment_stats(rf_plan* plan, const void* vis, int32_t nint, void* stream, rf_candidate* out,
+                                  size_t cap, size_t* n_out, rf_image_stat* stats, size_t stats_cap,
+                                  size_t* n_stats) {
+  if (!stats && stats_cap > 0) return fail(RF_ERR_INVALID_ARG, "stats is NULL with stats_cap > 0");
+  return search_impl(plan, vis, nint, stream, out, cap, n_out, true, stats, stats_cap, n_stats);
+}
+
+rf_status rf_render_images(rf_plan* p, const void* vis, int32_t nint, void* stream, const int32_t* trials,
+                           int32_t n, float* images) {
+  if (!p) return fail(RF_ERR_INVALID_ARG, "plan is NULL");
+  if (p->host_only) return fail(RF_ERR_INVALID_ARG, "plan was created with RF_HOST_ONLY");
+  if (!vis || !trials || !images || n < 1) return fail(RF_ERR_INVALID_ARG, "bad render arguments");
+  if (nint < 1 || nint > p->max_nint) return fail(RF_ERR_SHAPE, "nint %d out of [1, %d]", nint, p->max_nint);
+  if (n > p->img_cap) return fail(RF_ERR_INVALID_ARG, "at most %d images per call", p->img_cap);
+  for (int k = 0; k < n; ++k) {
+    const int d = trials[3 * k], s = trials[3 * k + 1], t = trials[3 * k + 2];
+    if (d < 0 || d >= p->ndm || s < 0 || s >= p->ndt || t < 0 || t >= n_times(p, nint, d, s))
+      return fail(RF_ERR_INVALID_ARG, "trial %d (%d, %d, %d) is not searched", k, d, s, t);
+  }
+  BusyGuard bg(&p->busy);
+  if (!bg.owned) return fail(RF_ERR_BUSY, "plan is in use by another call");
+  DeviceGuard dg(p->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rf_status s = ingest(p, vis, nint, st);
+  if (s != RF_OK) return s;
+  std::vector<int4> info(n);
+  std::vector<Group> grp(n);
+  for (int k = 0; k < n; ++k) {
+    info[k] = make_int4(trials[3 * k], trials[3 * k + 1], trials[3 * k + 2], 0);
+    grp[k] = Group{trials[3 * k], trials[3 * k + 1], trials[3 * k + 2], 1, k, {0, 0, 0}};
+  }
+  p->cached_nint = -1;  // the lists below replace the cached search lists
+  RF_CUDA(cudaMemcpyAsync(p->d_img_info, info.data(), n * sizeof(int4), cudaMemcpyHostToDevice, st));
+  RF_CUDA(cudaMemcpyAsync(p->d_groups, grp.data(), n * sizeof(Group), cudaMemcpyHostToDevice, st));
+  std::vector<Wave> waves;
+  for (int k = 0; k < n; k += p->slots_max) {
+    const int e = std::min(n, k + p->slots_max);
+    waves.push_back(Wave{k, e, k, e});
+  }
+  const size_t npx = (size_t)p->npix * p->npix;
+  float* d_img = nullptr;
+  cudaError_t e = cudaMalloc(&d_img, (size_t)n * npx * sizeof(float));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RF_ERR_NO_MEMORY, "render buffer: %s", cudaGetErrorString(e));
+  }
+  RF_CUDA(cudaMemsetAsync(p->d_ncand, 0, sizeof(int), st));
+  s = run_waves(p, nint, waves, n, nullptr, d_img, st);
+  if (s == RF_OK) {
+    e = cudaMemcpyAsync(images, d_img, (size_t)n * npx * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = fail(RF_ERR_CUDA, "render copy: %s", cudaGetErrorString(e));
+  }
+  cudaStreamSynchronize(st);
+  p->prof.collect();
+  cudaFree(d_img);
+  return s;
+}
+
+rf_status rf_plan_set_form(rf_plan* plan, int32_t form) {
+  if (!plan) return fail(RF_ERR_INVALID_ARG, "plan is NULL");
+  if (form != RF_FORM_BATCHED && form != RF_FORM_PLAIN) return fail(RF_ERR_INVALID_ARG, "unknown form %d", form);
+  plan->form = form;
+  return RF_OK;
+}
+
+rf_status rf_plan_set_profiling(rf_plan* plan, int32_t enable) {
+  if (!plan) return fail(RF_ERR_INVALID_ARG, "plan is NULL");
+  BusyGuard bg(&plan->busy);
+  if (!bg.owned) return fail(RF_ERR_BUSY, "plan is in use by another call");
+  plan->prof.on = enable != 0;
+  plan->prof.reset();
+  return RF_OK;
+}
+
+rf_status rf_plan_get_profile(const rf_plan* plan, rf_kernel_profile* out, int32_t cap, int32_t* n) {
+  if (!plan || !n || (cap > 0 && !out)) return fail(RF_ERR_INVALID_ARG, "NULL argument");
+  *n = K_NKINDS;
+  for (int k = 0; k < K_NKINDS && k < cap; ++k) {
+    std::memset(out[k].name, 0, sizeof(out[k].name));
+    std::strncpy(out[k].name, kKindNames[k], sizeof(out[k].name) - 1);
+    out[k].launches = plan->prof.launches[k];
+    out[k].total_ms = plan->prof.total_ms[k];
+  }
+  return RF_OK;
+}
+
+rf_status rf_plan_get_info(const rf_plan* p, rf_plan_info* info) {
+  if (!p || !info) return fail(RF_ERR_INVALID_ARG, "NULL argument");
+  info->nbl = p->nbl;
+  info->nchan = p->nchan;
+  info->npix = p->npix;
+  info->ndm = p->ndm;
+  info->ndt = p->ndt;
+  info->iu_max = p->iu_max;
+  info->iv_max = p->iv_max;
+  info->n_offgrid = p->n_offgrid;
+  info->n_cells = (int32_t)p->cell_rc.size();
+  info->n_entries = (int32_t)p->ent.size();
+  int mx = 0;
+  for (int v : p->max_delay) mx = std::max(mx, v);
+  info->max_delay = mx;
+  info->images_per_group = p->shape.images_per_group;
+  info->device_bytes = p->device_bytes;
+  return RF_OK;
+}
+
+rf_status rf_plan_delays(const rf_plan* p, int32_t* out) {
+  if (!p || !out) return fail(RF_ERR_INVALID_ARG, "NULL argument");
+  std::memcpy(out, p->delays.data(), p->delays.size() * sizeof(int32_t));
+  return RF_OK;
+}
+
+rf_status rf_plan_cells(const rf_plan* p, int32_t* iu, int32_t* iv, uint8_t* ongrid) {
+  if (!p) return fail(RF_ERR_INVALID_ARG, "plan is NULL");
+  if (iu) std::memcpy(iu, p->iu.data(), p->iu.size() * sizeof(int32_t));
+  if (iv) std::memcpy(iv, p->iv.data(), p->iv.size() * sizeof(int32_t));
+  if (ongrid) std::memcpy(ongrid, p->ongrid.data(), p->ongrid.size());
+  return RF_OK;
+}
+
+rf_status rf_count_images(const rf_plan* p, int32_t nint, int64_t* n_images) {
+  if (!p || !n_images) return fail(RF_ERR_INVALID_ARG, "NULL argument");
+  if (nint < 0) return fail(RF_ERR_SHAPE, "nint must be >= 0");
+  *n_images = count_images(p, nint);
+  return RF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+// rf_engine.h -- internal interface between the host orchestration
+// (rf_api.cpp) and the CUDA kernels.  Plain C++ types only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rf {
+
+// Gridding entry flags (low bits of GridEntry.cflags).
+constexpr int ENT_CONJ = 1;  // contribute conj(R) (folded into the half plane)
+constexpr int ENT_NEG = 2;   // checkerboard sign (-1)^(iu + iv) is -1
+
+// One contribution of a (baseline, channel) visibility to a half-plane cell.
+// row = bc index c * nbl + b of the Stokes-I time series; cflags = (c << 2) | flags.
+struct GridEntry {
+  int32_t bc;
+  int32_t cflags;
+};
+
+// Device tables of a plan (all device pointers).
+struct DevTables {
+  const int32_t* delays;        // [ndm][nchan] integrations
+  const int32_t* dt_list;       // [ndt]
+  const int32_t* col_cell_ptr;  // [ncol + 1] first cell of each half-plane column
+  const int32_t* cell_rc;       // [ncells] (col << 13) | row, row = iv mod N
+  const int32_t* cell_ent_ptr;  // [ncells + 1] first entry of each cell
+  const GridEntry* ent;         // [nent]
+  const int32_t* ongrid_chan;   // [nchan] on-grid baselines per channel
+  const float2* twiddle;        // [npix] exp(+2 pi i m / N)
+};
+
+// Group of consecutive output integrations of one (DM, dt) trial imaged
+// together by the gridding/column-FFT kernel.
+struct Group {
+  int32_t d;
+  int32_t s;
+  int32_t t0;
+  int32_t nimg;
+  int32_t img0;  // index of the group's first image in the image list
+  int32_t pad[3];
+};
+
+// Row-block partial statistics of one image (raw pixel units).
+struct StatPartial {
+  double sum;
+  double sumsq;
+  float max;
+  int32_t idx;  // y * N + x of max (lowest on ties)
+  int32_t pad[2];
+};
+
+// Candidate record written on the device.
+struct DevCand {
+  int32_t d, s, t, x, y;
+  float snr, peak, sigma;
+};
+
+// Per-image statistics written on the device (verification path).
+struct DevStat {
+  float peak, sigma, snr;
+  int32_t x, y;
+  int32_t pad;
+  double mean;
+  double weight;
+};
+
+struct SegmentGeom {
+  int nint;       // integrations in this segment
+  int nint_pad;   // row pitch of the Stokes-I buffer (elements)
+  int nbl;
+  int nchan;
+  int npix;
+  int ncol;       // half-plane columns imaged: 0 .. iu_max
+  int ndm;
+  bool fp16;      // Stokes-I stored as half2
+};
+
+// ---------------------------------------------------------------- launchers
+// All launchers return cudaSuccess or the launch error.
+
+// Stokes-I ingest of integrations [t_begin, t_begin + nt) from `vis`
+// ([nt][nbl][nchan][npol] complex64, already offset to t_begin) into the
+// time-major buffer S[c * nbl + b][t].
+cudaError_t launch_ingest(const float2* vis, int nt, int t_begin, int npol, const SegmentGeom& g, void* S,
+                          cudaStream_t st);
+
+// W of each listed image (img_info[i] = {d, s, t, 0}); n_on = on-grid
+// (baseline, channel) pairs.
+cudaError_t launch_weights(const int4* img_info, int nimg, bool partial, const SegmentGeom& g,
+                           const DevTables& tb, double n_on, double* weight, cudaStream_t st);
+
+// Gridding + column FFT (pass A) of groups [g_begin, g_begin + ngroups).
+// Writes Tbuf[slot][col][y], slot = image index - img_base.
+cudaError_t launch_grid_colfft(const SegmentGeom& g, const DevTables& tb, const void* S, const Group* groups,
+                               int g_begin, int ngroups, int img_base, float2* Tbuf, cudaStream_t st);
+
+// Row C2R (pass B) + statistics of `nimg` images in slots [0, nimg) whose
+// first image index is img_base.  Optionally writes the scaled images.
+cudaError_t launch_rowfft_stats(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, int nimg,
+                                int img_base, const double* weight, StatPartial* partials, float* images,
+                                cudaStream_t st);
+
+// Reduce row-block partials, compute sigma / snr, append candidates and
+// (optionally) per-image stats for images [img_base, img_base + nimg).
+cudaError_t launch_finalize(const SegmentGeom& g, const StatPartial* partials, const int4* img_info,
+                            const double* weight, int nimg, int img_base, double threshold, DevCand* cands,
+                            int* ncand, int cand_cap, DevStat* stats, cudaStream_t st);
+
+// Compile-time layout facts per image size, for host-side sizing.
+struct ImageKernelShape {
+  int images_per_group;   // B
+  int cols_per_cta;       // C
+  int threads_a;
+  int smem_a;
+  int rows_per_cta;       // RB (pass B)
+  int threads_b;
+  int smem_b;
+};
+bool image_kernel_shape(int npix, ImageKernelShape* out);
+
+}  // namespace rf

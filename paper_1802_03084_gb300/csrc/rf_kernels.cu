@@ -1,0 +1,257 @@
+// rf_kernels.cu -- Stokes-I ingest, per-image weights, per-image finalisation
+// (noise, S/N, threshold, candidate append) and the launch dispatch by image
+// size for the imaging kernels.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <float.h>
+#include <limits.h>
+
+#include "rf_engine.h"
+
+namespace rf {
+
+// ----------------------------------------------------------------- ingest --
+// Stokes I (Sec. 3.1: a Stokes I image; Table 1: two polarisations) is the
+// mean of the polarisations.  The input [t][b][c][p] is transposed through a
+// 32x32 shared tile into the time-major S[c * nbl + b][t] so that the
+// dedispersion gathers of consecutive t' read consecutive addresses.
+template <bool FP16, int NPOL>
+__global__ void __launch_bounds__(256) k_ingest(const float2* __restrict__ vis, int nt, int t_begin, int nbl,
+                                                int nchan, int nint_pad, void* __restrict__ S) {
+  __shared__ float2 tile[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int nq = nbl * nchan;
+  const int q0 = blockIdx.x * 32;
+  const int t0 = blockIdx.y * 32;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int tt = t0 + ty + 8 * k;
+    const int q = q0 + tx;
+    float2 s = make_float2(0.f, 0.f);
+    if (tt < nt && q < nq) {
+      if (NPOL == 2) {
+        const float4 p = __ldg(reinterpret_cast<const float4*>(vis) + (size_t)tt * nq + q);
+        s = make_float2(0.5f * (p.x + p.z), 0.5f * (p.y + p.w));
+      } else {
+        s = __ldg(vis + (size_t)tt * nq + q);
+      }
+    }
+    tile[ty + 8 * k][tx] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int q = q0 + ty + 8 * k;
+    const int tt = t0 + tx;
+    if (q < nq && tt < nt) {
+      const int b = q / nchan;
+      const int c = q - b * nchan;
+      const size_t o = (size_t)(c * nbl + b) * nint_pad + t_begin + tt;
+      const float2 v = tile[tx][ty + 8 * k];
+      if (FP16)
+        reinterpret_cast<__half2*>(S)[o] = __floats2half2_rn(v.x, v.y);
+      else
+        reinterpret_cast<float2*>(S)[o] = v;
+    }
+  }
+}
+
+cudaError_t launch_ingest(const float2* vis, int nt, int t_begin, int npol, const SegmentGeom& g, void* S,
+                          cudaStream_t st) {
+  if (nt <= 0) return cudaSuccess;
+  const int nq = g.nbl * g.nchan;
+  dim3 grid((nq + 31) / 32, (nt + 31) / 32);
+  dim3 block(32, 8);
+  if (npol == 2) {
+    if (g.fp16)
+      k_ingest<true, 2><<<grid, block, 0, st>>>(vis, nt, t_begin, g.nbl, g.nchan, g.nint_pad, S);
+    else
+      k_ingest<false, 2><<<grid, block, 0, st>>>(vis, nt, t_begin, g.nbl, g.nchan, g.nint_pad, S);
+  } else {
+    if (g.fp16)
+      k_ingest<true, 1><<<grid, block, 0, st>>>(vis, nt, t_begin, g.nbl, g.nchan, g.nint_pad, S);
+    else
+      k_ingest<false, 1><<<grid, block, 0, st>>>(vis, nt, t_begin, g.nbl, g.nchan, g.nint_pad, S);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- weights --
+// W = sum over on-grid (b, c) of the samples summed into R[b, c].  Under the
+// FULL edge rule every channel sums dt samples; under PARTIAL channel c sums
+// clamp(nint - (t dt + delta[d][c]), 0, dt) of them.
+__global__ void k_weights(const int4* __restrict__ img_info, int nimg, int partial, int nint, int nchan,
+                          const int* __restrict__ delays, const int* __restrict__ dt_list,
+                          const int* __restrict__ ongrid_chan, double n_on, double* __restrict__ weight) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nimg) return;
+  const int4 info = img_info[i];
+  const int dt = dt_list[info.y];
+  if (!partial) {
+    weight[i] = (double)dt * n_on;
+    return;
+  }
+  const int* dl = delays + (size_t)info.x * nchan;
+  const int tb = info.z * dt;
+  long long w = 0;
+  for (int c = 0; c < nchan; ++c) {
+    int n = nint - (tb + dl[c]);
+    n = n < 0 ? 0 : (n > dt ? dt : n);
+    w += (long long)n * ongrid_chan[c];
+  }
+  weight[i] = (double)w;
+}
+
+cudaError_t launch_weights(const int4* img_info, int nimg, bool partial, const SegmentGeom& g,
+                           const DevTables& tb, double n_on, double* weight, cudaStream_t st) {
+  if (nimg <= 0) return cudaSuccess;
+  k_weights<<<(nimg + 255) / 256, 256, 0, st>>>(img_info, nimg, partial ? 1 : 0, g.nint, g.nchan, tb.delays,
+                                                 tb.dt_list, tb.ongrid_chan, n_on, weight);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- finalize --
+// Per image: reduce the row-block partials (FP64), then
+//   mean = sum / N^2,  sigma = sqrt(sum_sq / N^2 - mean^2)  (population),
+//   peak = max pixel (lowest y N + x on ties),  snr = peak / sigma,
+// and append a candidate iff snr >= threshold (Sec. 3.1).  Raw pixel sums are
+// scaled by 1 / (2 W) here.
+__device__ __forceinline__ void fmax_merge(float& m, int& i, float m2, int i2) {
+  if (m2 > m || (m2 == m && i2 < i)) {
+    m = m2;
+    i = i2;
+  }
+}
+
+__global__ void k_finalize(int npix, int nrb, const StatPartial* __restrict__ partials,
+                           const int4* __restrict__ img_info, const double* __restrict__ weight, int nimg,
+                           int img_base, double threshold, DevCand* __restrict__ cands, int* __restrict__ ncand,
+                           int cand_cap, DevStat* __restrict__ stats) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nimg) return;
+  const int img = img_base + i;
+  const StatPartial* pp = partials + (size_t)i * nrb;
+  double sum = 0.0, sq = 0.0;
+  float mx = -FLT_MAX;
+  int mi = INT_MAX;
+  for (int r = 0; r < nrb; ++r) {
+    const StatPartial p = pp[r];
+    sum += p.sum;
+    sq += p.sumsq;
+    fmax_merge(mx, mi, p.max, p.idx);
+  }
+  const double W = weight[img];
+  const int4 info = img_info[img];
+  DevStat ds;
+  ds.pad = 0;
+  ds.weight = W;
+  if (!(W > 0.0)) {
+    ds.peak = 0.f;
+    ds.sigma = 0.f;
+    ds.snr = 0.f;
+    ds.x = 0;
+    ds.y = 0;
+    ds.mean = 0.0;
+    if (stats) stats[img] = ds;
+    return;
+  }
+  const double inv = 0.5 / W;
+  const double n2 = (double)npix * (double)npix;
+  const double mean = sum * inv / n2;
+  double var = sq * inv * inv / n2 - mean * mean;
+  var = var > 0.0 ? var : 0.0;
+  const double sigma = sqrt(var);
+  const double peak = (double)mx * inv;
+  const double snr = sigma > 0.0 ? peak / sigma : 0.0;
+  const int y = mi / npix;
+  const int x = mi - y * npix;
+  ds.peak = (float)peak;
+  ds.sigma = (float)sigma;
+  ds.snr = (float)snr;
+  ds.x = x;
+  ds.y = y;
+  ds.mean = mean;
+  if (stats) stats[img] = ds;
+  if (sigma > 0.0 && snr >= threshold) {
+    const int k = atomicAdd(ncand, 1);
+    if (k < cand_cap) {
+      DevCand c;
+      c.d = info.x;
+      c.s = info.y;
+      c.t = info.z;
+      c.x = x;
+      c.y = y;
+      c.snr = (float)snr;
+      c.peak = (float)peak;
+      c.sigma = (float)sigma;
+      cands[k] = c;
+    }
+  }
+}
+
+cudaError_t launch_finalize(const SegmentGeom& g, const StatPartial* partials, const int4* img_info,
+                            const double* weight, int nimg, int img_base, double threshold, DevCand* cands,
+                            int* ncand, int cand_cap, DevStat* stats, cudaStream_t st) {
+  if (nimg <= 0) return cudaSuccess;
+  ImageKernelShape sh;
+  if (!image_kernel_shape(g.npix, &sh)) return cudaErrorInvalidValue;
+  const int nrb = g.npix / sh.rows_per_cta;
+  k_finalize<<<(nimg + 127) / 128, 128, 0, st>>>(g.npix, nrb, partials, img_info, weight, nimg, img_base,
+                                                  threshold, cands, ncand, cand_cap, stats);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- dispatch --
+template <int N, bool FP16>
+cudaError_t run_grid_colfft(const SegmentGeom&, const DevTables&, const void*, const Group*, int, int, int,
+                            float2*, cudaStream_t);
+template <int N>
+cudaError_t run_rowfft_stats(const SegmentGeom&, const DevTables&, const float2*, int, int, const double*,
+                             StatPartial*, float*, cudaStream_t);
+template <int N>
+void fill_shape(ImageKernelShape*);
+
+#define RF_FOR_EACH_N(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
+
+cudaError_t launch_grid_colfft(const SegmentGeom& g, const DevTables& tb, const void* S, const Group* groups,
+                               int g_begin, int ngroups, int img_base, float2* Tbuf, cudaStream_t st) {
+  switch (g.npix) {
+#define RF_CASE(N)                                                                               \
+  case N:                                                                                        \
+    return g.fp16 ? run_grid_colfft<N, true>(g, tb, S, groups, g_begin, ngroups, img_base, Tbuf, st) \
+                  : run_grid_colfft<N, false>(g, tb, S, groups, g_begin, ngroups, img_base, Tbuf, st);
+    RF_FOR_EACH_N(RF_CASE)
+#undef RF_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_rowfft_stats(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, int nimg,
+                                int img_base, const double* weight, StatPartial* partials, float* images,
+                                cudaStream_t st) {
+  switch (g.npix) {
+#define RF_CASE(N) \
+  case N:          \
+    return run_rowfft_stats<N>(g, tb, Tbuf, nimg, img_base, weight, partials, images, st);
+    RF_FOR_EACH_N(RF_CASE)
+#undef RF_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+bool image_kernel_shape(int npix, ImageKernelShape* out) {
+  switch (npix) {
+#define RF_CASE(N)      \
+  case N:               \
+    fill_shape<N>(out); \
+    return true;
+    RF_FOR_EACH_N(RF_CASE)
+#undef RF_CASE
+    default:
+      return false;
+  }
+}
+
+}  // namespace rf
