@@ -1,0 +1,430 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the realfast search engine on GB300.
+
+One step = one full segment search (every DM x dt x t' dirty image, peak,
+noise, threshold, candidates) of the ``realtime`` workload: 351 baselines,
+256 channels over 1-2 GHz, 1024 x 5 ms integrations, 128 DM trials 0-1500 on
+the smearing grid, dt {1,2,4,8}, 1024^2 images: 177,521 images per segment.
+The segment (1.47 GB of complex64 visibilities) is larger than L2, so the
+inputs are not L2-resident between steps.
+
+``value``: dirty images per second with the segment resident in HBM.
+``e2e``: the same metric through the same C-ABI call with the segment in
+pinned host memory (host-to-device copies inside the timed region).
+``roofline``: the dominant kernel's algorithmic throughput from CUDA events
+recorded around each of its launches during the timed region.
+``cpu_baseline``: the FP64 oracle on a bounded sample of the same images on
+the host cores (a reported baseline, not the target).
+
+``--impl reference`` times the oracle alone on the host cores, each step a
+bounded sample of the same workload.
+
+Multi-GPU (torchrun): every rank searches its own segment (weak scaling, no
+data-path collective); timing is the max over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "dirty images/sec (DM×dt×int) and visibility GB/s vs HBM peak; p99 latency/real-time"
+UNIT = "images/s"
+FP32_LANES_PER_SM = 128
+GB300_SMS = 152
+GB300_MAX_SM_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
+    ap.add_argument("--config", default="realtime")
+    ap.add_argument("--form", default="batched", choices=["batched", "plain"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks --
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------- CPU oracle --
+def _oracle_worker(args):
+    import numpy as np
+    from multiprocessing import shared_memory
+    import oracle
+    (shm_name, shape, plan_kw, items) = args
+    shm = shared_memory.SharedMemory(name=shm_name)
+    try:
+        S = np.ndarray(shape, dtype=np.complex128, buffer=shm.buf)
+        op = oracle.OraclePlan(**plan_kw)
+        out = []
+        for (d, s, t) in items:
+            I, W = op.image(S, d, s, t)
+            st = oracle.image_stats(I)
+            out.append((d, s, t, st.peak, st.sigma, st.x, st.y))
+        del S
+        return out
+    finally:
+        shm.close()
+
+
+class OracleRunner:
+    """The FP64 oracle, as it stands, over a spawn pool of all host cores."""
+
+    def __init__(self, spec, seg):
+        import numpy as np
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        import oracle
+        self.np = np
+        S = oracle.stokes_i(seg["vis"])
+        self.shm = shared_memory.SharedMemory(create=True, size=S.nbytes)
+        buf = np.ndarray(S.shape, dtype=np.complex128, buffer=self.shm.buf)
+        buf[...] = S
+        self.shape = S.shape
+        del S, buf
+        self.plan_kw = dict(ant_uvw=seg["ant_uvw"], freq_hz=seg["freq_hz"], inttime_s=spec.inttime_s,
+                            npix=spec.npix, cell_rad=spec.cell_rad, dm_list=spec.dm_list, dt_list=spec.dt_list,
+                            threshold=spec.threshold, edge=spec.edge)
+        op = oracle.OraclePlan(**self.plan_kw)
+        self.images = op.image_list(spec.nint)
+        self.cores = os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        self.rng = np.random.default_rng(12345)
+
+    def sample(self, n):
+        idx = self.rng.choice(len(self.images), size=n, replace=False)
+        return [self.images[i] for i in sorted(idx)]
+
+    def run(self, items):
+        chunks = [items[i::self.cores] for i in range(self.cores)]
+        jobs = [(self.shm.name, self.shape, self.plan_kw, c) for c in chunks if c]
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_worker, jobs)
+        return time.perf_counter() - t0, [r for part in res for r in part]
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        self.shm.close()
+        self.shm.unlink()
+
+
+def cpu_baseline(spec, seg, seconds):
+    run = OracleRunner(spec, seg)
+    try:
+        run.run(run.sample(run.cores))                      # warm the workers
+        t1, _ = run.run(run.sample(run.cores))              # one image per core: per-image time
+        n = max(run.cores, int(run.cores * seconds / max(t1, 1e-3)))
+        n = min(n, len(run.images))
+        t, _ = run.run(run.sample(n))
+        return {"value": n / t, "unit": UNIT, "cores": run.cores, "kind": "oracle",
+                "sample": f"{n} images drawn uniformly (seed 12345) from the {len(run.images)} (DM, dt, t') "
+                          f"images of the {spec.name} segment, FP64 numpy, {t:.1f} s wall"}
+    finally:
+        run.close()
+
+
+# ------------------------------------------------------------ work counts --
+def work_per_image(spec, info, fp16):
+    """Algorithmic bytes and flops per image for each imaging kernel."""
+    N = spec.npix
+    ncol = info.iu_max + 1
+    nbl, nchan = info.nbl, info.nchan
+    mean_dt = None
+    return {
+        "grid_colfft": {
+            # visibility gather (per sample) + column-FFT output written once
+            "bytes_per_sample": (4 if fp16 else 8) * info.n_entries,
+            "bytes_fixed": 8 * N * ncol,
+            "flops": ncol * 5.0 * N * math.log2(N),
+        },
+        "rowfft_stats": {
+            "bytes_fixed": 8 * N * ncol,   # column-FFT output read once
+            "bytes_per_sample": 0,
+            "flops": (N / 2) * 5.0 * N * math.log2(N),
+        },
+    }
+
+
+def roofline(prof, spec, info, n_images, samples_per_step, steps, fp16, hbm_peak, peak_kind, clock_mhz):
+    work = work_per_image(spec, info, fp16)
+    per = {}
+    for name, w in work.items():
+        launches, ms = prof.get(name, (0, 0.0))
+        if launches == 0:
+            continue
+        imgs_per_launch = n_images * steps / launches
+        samples_per_launch = samples_per_step * steps / launches
+        bytes_per_launch = w["bytes_fixed"] * imgs_per_launch + w["bytes_per_sample"] * samples_per_launch
+        flops_per_launch = w["flops"] * imgs_per_launch
+        avg_s = ms / launches / 1e3
+        per[name] = dict(launches=launches, total_ms=ms, avg_us=avg_s * 1e6, images_per_launch=imgs_per_launch,
+                         gbs=bytes_per_launch / avg_s / 1e9, tflops=flops_per_launch / avg_s / 1e12)
+    if not per:
+        return None, per
+    dom = max(per, key=lambda k: per[k]["total_ms"])
+    d = per[dom]
+    fp32_peak = GB300_SMS * FP32_LANES_PER_SM * 2 * GB300_MAX_SM_MHZ * 1e6 / 1e12
+    hbm_frac = d["gbs"] / hbm_peak
+    alu_frac = d["tflops"] / fp32_peak
+    if alu_frac >= hbm_frac:
+        r = {"bound": "alu", "achieved": round(d["tflops"], 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+             "frac": round(alu_frac, 4), "traffic": None, "kernel": dom,
+             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz max SM clock",
+             "flops_model": "5 N log2 N per length-N complex FFT",
+             "hbm_achieved_gbs": round(d["gbs"], 1), "hbm_frac": round(hbm_frac, 4),
+             "hbm_peak": hbm_peak, "hbm_peak_source": peak_kind}
+    else:
+        r = {"bound": "hbm", "achieved": round(d["gbs"], 1), "peak": hbm_peak, "unit": "GB/s",
+             "frac": round(hbm_frac, 4), "traffic": None, "kernel": dom, "peak_source": peak_kind,
+             "alu_tflops": round(d["tflops"], 3), "alu_frac": round(alu_frac, 4)}
+    r["avg_launch_us"] = round(d["avg_us"], 2)
+    return r, per
+
+
+# ---------------------------------------------------------------- reference --
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import numpy as np
+    import synth
+    spec = synth.config(args.config)
+    seg = synth.make_segment(spec)
+    run = OracleRunner(spec, seg)
+    try:
+        n = run.cores * 2
+        for _ in range(args.warmup):
+            run.run(run.sample(n))
+        t_total = 0.0
+        for _ in range(args.steps):
+            t, _ = run.run(run.sample(n))
+            t_total += t
+        value = args.steps * n / t_total
+        sample = f"{n} images per step drawn uniformly from the {len(run.images)} images of the {spec.name} segment"
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": workload_name(spec)},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": run.cores, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+    finally:
+        run.close()
+    return 0
+
+
+def workload_name(spec):
+    return (f"{spec.name}: 351 baselines x {spec.nchan} ch ({spec.f_lo_hz/1e9:.1f}-{(spec.f_lo_hz+spec.bw_hz)/1e9:.1f}"
+            f" GHz) x {spec.nint} x {spec.inttime_s*1e3:g} ms, {len(spec.dm_list)} DM trials "
+            f"0-{spec.dm_list.max():.0f}, dt {list(spec.dt_list)}, {spec.npix}^2 images, "
+            f"{'FP16' if spec.store == 'fp16' else 'FP32'} storage")
+
+
+# ------------------------------------------------------------------- engine --
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import synth
+    import paper_1802_03084_gb300 as rf
+    from paper_1802_03084_gb300.build import build
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if rank == 0:
+        build()
+    if dist:
+        dist.barrier()
+    rf.lib()
+
+    spec = synth.config(args.config)
+    spec.seed += 1000 * rank       # each rank searches its own segment
+    seg = synth.make_segment(spec)
+    nint = spec.nint
+    vis_dev = torch.from_numpy(seg["vis"]).cuda()
+    vis_pin = torch.from_numpy(seg["vis"]).pin_memory() if not args.no_e2e else None
+    torch.cuda.synchronize()
+    plan = rf.Plan.from_spec(spec, seg["ant_uvw"], seg["freq_hz"], max_nint=nint, device=local_rank)
+    if args.form == "plain":
+        plan.set_form(rf.RF_FORM_PLAIN)
+    info = plan.info()
+    n_images = plan.count_images(nint)
+    fp16 = spec.store == "fp16"
+    # samples gathered per step: sum over images of dt (each image sums dt samples per entry)
+    d_max = plan.delays().max(axis=1)
+    samples_per_step = 0
+    for d in range(len(spec.dm_list)):
+        for dt in spec.dt_list:
+            span = nint - int(d_max[d])
+            nt = max(span // dt, 0) if span > 0 else 0
+            samples_per_step += nt * dt
+
+    for _ in range(max(args.warmup, 0)):
+        cands = plan.search(vis_dev, nint)
+    plan.set_profiling(True)
+    clocks = Clocks(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        cands = plan.search(vis_dev, nint)
+    ev1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    prof = plan.profile()
+    plan.set_profiling(False)
+    n_cand = len(cands)
+
+    e2e = None
+    if vis_pin is not None:
+        plan.search(vis_pin, nint)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            c2 = plan.search(vis_pin, nint)
+        e1.record()
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ems], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * args.steps * n_images / (ems / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(seg["vis"].nbytes),
+               "d2h_bytes_per_step": int(4 + len(c2) * rf.CANDIDATE_DTYPE.itemsize),
+               "ms_per_step": ems / args.steps}
+
+    hbm_peak, peak_kind = peaks()
+    roof, per_kernel = roofline(prof, spec, info, n_images, samples_per_step, args.steps, fp16, hbm_peak,
+                                peak_kind, clk.get("sm_mhz"))
+    launches = sum(v[0] for k, v in prof.items() if k != "h2d_copy")
+    value = world * args.steps * n_images / (ms / 1e3)
+    seg_s = nint * spec.inttime_s
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if not fp16 else "f16-storage/f32", "data": "synthetic",
+        "config": {"workload": workload_name(spec), "images_per_step": n_images, "form": args.form,
+                   "l2": f"inputs larger than L2 ({seg['vis'].nbytes / 1e9:.2f} GB segment per step)",
+                   "parallelism": f"dp{world} (one segment per GPU)"},
+        "visibility_gbs": world * args.steps * seg["vis"].nbytes / (ms / 1e3) / 1e9,
+        "realtime_factor": seg_s / (ms / args.steps / 1e3),
+        "segment_latency_ms": ms / args.steps,
+        "segment_duration_ms": seg_s * 1e3,
+        "candidates_per_step": n_cand,
+        "roofline": roof,
+        "kernels": {k: {kk: (round(vv, 3) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                    for k, v in per_kernel.items()},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(spec, seg, args.cpu_seconds)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
