@@ -172,8 +172,9 @@ struct rf_plan {
   std::vector<int32_t> max_delay;  // [ndm]
   std::vector<int32_t> iu, iv;     // [nbl][nchan]
   std::vector<uint8_t> ongrid;     // [nbl][nchan]
-  std::vector<int32_t> col_cell_ptr, cell_rc, cell_ent_ptr;
+  std::vector<int32_t> col_ent_ptr, col_warp_ptr;
   std::vector<GridEntry> ent;
+  int n_cells = 0;
   std::vector<int32_t> ongrid_chan;
   int n_on = 0, iu_max = 0, iv_max = 0, ncol = 1, n_offgrid = 0;
   rf::ImageKernelShape shape{};
@@ -378,27 +379,48 @@ rf_status build_tables(rf_plan* p) {
     return a.flags < b2.flags;
   });
   p->ncol = p->n_on > 0 ? p->iu_max + 1 : 1;
-  p->col_cell_ptr.assign(p->ncol + 1, 0);
-  p->cell_rc.clear();
-  p->cell_ent_ptr.clear();
+  if (!rf::image_kernel_shape(N, &p->shape)) return fail(RF_ERR_INVALID_ARG, "npix %d has no kernel", N);
   p->ent.clear();
   p->ent.reserve(es.size());
+  p->col_ent_ptr.assign(p->ncol + 1, 0);
+  p->n_cells = 0;
+  std::vector<int> cell_start;  // entry index where each cell begins
   size_t i = 0;
   for (int col = 0; col < p->ncol; ++col) {
-    p->col_cell_ptr[col] = (int)p->cell_rc.size();
+    p->col_ent_ptr[col] = (int)p->ent.size();
+    int prev_row = -1;
     while (i < es.size() && es[i].col == col) {
-      const int row = es[i].row;
-      p->cell_rc.push_back((col << 13) | row);
-      p->cell_ent_ptr.push_back((int)p->ent.size());
-      while (i < es.size() && es[i].col == col && es[i].row == row) {
-        const int c = es[i].bc / nbl;
-        p->ent.push_back({es[i].bc, (c << 2) | es[i].flags});
-        ++i;
+      if (es[i].row != prev_row) {
+        cell_start.push_back((int)p->ent.size());
+        prev_row = es[i].row;
+        p->n_cells++;
       }
+      const int c = es[i].bc / nbl;
+      p->ent.push_back({es[i].bc, (c << 2) | es[i].flags, es[i].row, 0});
+      ++i;
     }
   }
-  p->col_cell_ptr[p->ncol] = (int)p->cell_rc.size();
-  p->cell_ent_ptr.push_back((int)p->ent.size());
+  p->col_ent_ptr[p->ncol] = (int)p->ent.size();
+  cell_start.push_back((int)p->ent.size());
+  // Split each column's entries into WPC ranges that start on cell boundaries
+  // and hold about the same number of entries.
+  const int wpc = p->shape.warps_per_col;
+  p->col_warp_ptr.assign((size_t)p->ncol * (wpc + 1), 0);
+  size_t ci = 0;  // index into cell_start
+  for (int col = 0; col < p->ncol; ++col) {
+    const int eb = p->col_ent_ptr[col], ee = p->col_ent_ptr[col + 1];
+    int32_t* w = &p->col_warp_ptr[(size_t)col * (wpc + 1)];
+    while (ci < cell_start.size() && cell_start[ci] < eb) ++ci;
+    w[0] = eb;
+    size_t cj = ci;
+    for (int k = 1; k < wpc; ++k) {
+      const long target = eb + (long)(ee - eb) * k / wpc;
+      while (cj < cell_start.size() && cell_start[cj] < target) ++cj;
+      int b2 = (cj < cell_start.size()) ? std::min(cell_start[cj], ee) : ee;
+      w[k] = std::max(b2, w[k - 1]);
+    }
+    w[wpc] = ee;
+  }
   if (!rf::image_kernel_shape(N, &p->shape)) return fail(RF_ERR_INVALID_ARG, "npix %d has no kernel", N);
   return RF_OK;
 }
@@ -450,15 +472,13 @@ rf_status alloc_device(rf_plan* p) {
     *dst = d;
     return RF_OK;
   };
-  int32_t *d_delays, *d_dt, *d_ccp, *d_crc, *d_cep, *d_ogc;
+  int32_t *d_delays, *d_dt, *d_cwp, *d_ogc;
   GridEntry* d_ent;
   rf_status s;
   if ((s = up(&d_delays, p->delays)) != RF_OK) return s;
   std::vector<int32_t> dtv(p->dt.begin(), p->dt.end());
   if ((s = up(&d_dt, dtv)) != RF_OK) return s;
-  if ((s = up(&d_ccp, p->col_cell_ptr)) != RF_OK) return s;
-  if ((s = up(&d_crc, p->cell_rc)) != RF_OK) return s;
-  if ((s = up(&d_cep, p->cell_ent_ptr)) != RF_OK) return s;
+  if ((s = up(&d_cwp, p->col_warp_ptr)) != RF_OK) return s;
   if ((s = up(&d_ent, p->ent)) != RF_OK) return s;
   if ((s = up(&d_ogc, p->ongrid_chan)) != RF_OK) return s;
   std::vector<float2> tw(N);
@@ -470,9 +490,7 @@ rf_status alloc_device(rf_plan* p) {
   if ((s = up(&d_tw, tw)) != RF_OK) return s;
   p->tb.delays = d_delays;
   p->tb.dt_list = d_dt;
-  p->tb.col_cell_ptr = d_ccp;
-  p->tb.cell_rc = d_crc;
-  p->tb.cell_ent_ptr = d_cep;
+  p->tb.col_warp_ptr = d_cwp;
   p->tb.ent = d_ent;
   p->tb.ongrid_chan = d_ogc;
   p->tb.twiddle = d_tw;
@@ -849,7 +867,7 @@ rf_status rf_plan_get_info(const rf_plan* p, rf_plan_info* info) {
   info->iu_max = p->iu_max;
   info->iv_max = p->iv_max;
   info->n_offgrid = p->n_offgrid;
-  info->n_cells = (int32_t)p->cell_rc.size();
+  info->n_cells = (int32_t)p->n_cells;
   info->n_entries = (int32_t)p->ent.size();
   int mx = 0;
   for (int v : p->max_delay) mx = std::max(mx, v);

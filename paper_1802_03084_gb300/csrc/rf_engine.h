@@ -12,20 +12,21 @@ constexpr int ENT_CONJ = 1;  // contribute conj(R) (folded into the half plane)
 constexpr int ENT_NEG = 2;   // checkerboard sign (-1)^(iu + iv) is -1
 
 // One contribution of a (baseline, channel) visibility to a half-plane cell.
-// row = bc index c * nbl + b of the Stokes-I time series; cflags = (c << 2) | flags.
+// bc = row c * nbl + b of the Stokes-I time series; cflags = (c << 2) | flags;
+// row = the cell's v index iv mod N in its column.
 struct GridEntry {
   int32_t bc;
   int32_t cflags;
+  int32_t row;
+  int32_t pad;
 };
 
 // Device tables of a plan (all device pointers).
 struct DevTables {
   const int32_t* delays;        // [ndm][nchan] integrations
   const int32_t* dt_list;       // [ndt]
-  const int32_t* col_cell_ptr;  // [ncol + 1] first cell of each half-plane column
-  const int32_t* cell_rc;       // [ncells] (col << 13) | row, row = iv mod N
-  const int32_t* cell_ent_ptr;  // [ncells + 1] first entry of each cell
-  const GridEntry* ent;         // [nent]
+  const int32_t* col_warp_ptr;  // [ncol][WPC + 1] entry ranges of the warps gridding a column
+  const GridEntry* ent;         // [nent] sorted by (column, row)
   const int32_t* ongrid_chan;   // [nchan] on-grid baselines per channel
   const float2* twiddle;        // [npix] exp(+2 pi i m / N)
 };
@@ -113,6 +114,7 @@ struct ImageKernelShape {
   int cols_per_cta;       // C
   int threads_a;
   int smem_a;
+  int warps_per_col;      // WPC: warps sharing one column's gridding (pass A)
   int rows_per_cta;       // RB (pass B)
   int threads_b;
   int smem_b;

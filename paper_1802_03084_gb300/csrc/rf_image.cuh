@@ -36,6 +36,8 @@ struct ImgCfg {
   static constexpr int C = cmax(1, cmin(8, 512 / (T * B)));      // columns per CTA (pass A)
   static constexpr int XA = B * C;                               // transforms per CTA (pass A)
   static constexpr int THREADS_A = T * XA;
+  static constexpr int NW = THREADS_A / 32;                      // warps per CTA (pass A)
+  static constexpr int WPC = cmax(1, NW / C);                    // warps per column (pass A)
   static constexpr int XB = cmin(512 / T, N / 2);                // row pairs per CTA (pass B)
   static constexpr int THREADS_B = T * XB;
   static constexpr int RB = 2 * XB;                              // rows per CTA (pass B)
@@ -63,8 +65,13 @@ __device__ __forceinline__ float2 load_sample<true>(const void* __restrict__ S, 
 // checkerboarded half-plane grid in shared memory and inverse-FFT it along v.
 //   R[b,c](t') = sum_{j < dt} S[b,c][t' dt + j + delta[d][c]]    (dedisperse+resample)
 //   H[iv][iu] += (-1)^(iu+iv) R   or   conj(R) for folded entries (gridding)
-// Each thread owns whole cells (all entries of one (iu, iv)), so the sums are
-// in a fixed order and need no atomics.
+// Gridding: the entries of a column are sorted by cell and split (on the
+// host) into WPC cell-aligned ranges, one per warp.  A warp takes 32 entries
+// at a time, one per lane; each lane sums its B x dt samples, a segmented
+// shuffle scan keyed on the cell row adds up the lanes of each cell, and the
+// last lane of each cell adds the total into shared memory.  A cell belongs
+// to one warp and its partial sums are added in a fixed order, so the grid
+// is deterministic without atomics.
 template <int N, bool FP16>
 __global__ void __launch_bounds__(ImgCfg<N>::THREADS_A)
     k_grid_colfft(SegmentGeom g, DevTables tb, const void* __restrict__ S, const Group* __restrict__ groups,
@@ -72,50 +79,77 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_A)
   using K = ImgCfg<N>;
   extern __shared__ float2 sm[];
   const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
   const Group gr = groups[g_begin + blockIdx.x];
   const int col0 = blockIdx.y * K::C;
 
   for (int i = tid; i < K::XA * K::STRIDE; i += K::THREADS_A) sm[i] = make_float2(0.f, 0.f);
   __syncthreads();
 
-  const int col_end = min(col0 + K::C, g.ncol);
-  const int cb = tb.col_cell_ptr[col0];
-  const int ce = tb.col_cell_ptr[col_end];
   const int dt = tb.dt_list[gr.s];
   const int* __restrict__ dl = tb.delays + (size_t)gr.d * g.nchan;
   const int tstart = gr.t0 * dt;
-  for (int cell = cb + tid; cell < ce; cell += K::THREADS_A) {
-    const int rc = tb.cell_rc[cell];
-    const int col = rc >> 13;
-    const int row = rc & 8191;
-    float2 acc[K::B];
+  for (int unit = warp; unit < K::C * K::WPC; unit += K::NW) {
+    const int cl = unit / K::WPC;
+    const int col = col0 + cl;
+    if (col >= g.ncol) continue;  // warp-uniform
+    const int* cwp = tb.col_warp_ptr + (size_t)col * (K::WPC + 1) + (unit - cl * K::WPC);
+    const int ebeg = cwp[0];
+    const int eend = cwp[1];
+    float2* colbuf = sm + (size_t)cl * K::B * K::STRIDE;
+    for (int base = ebeg; base < eend; base += 32) {
+      const int e = base + lane;
+      const bool valid = e < eend;
+      float2 val[K::B];
 #pragma unroll
-    for (int k = 0; k < K::B; ++k) acc[k] = make_float2(0.f, 0.f);
-    const int e1 = tb.cell_ent_ptr[cell + 1];
-    for (int e = tb.cell_ent_ptr[cell]; e < e1; ++e) {
-      const GridEntry en = tb.ent[e];
-      const int c = en.cflags >> 2;
-      const int tf = tstart + __ldg(dl + c);
-      const size_t rowoff = (size_t)en.bc * g.nint_pad;
-      const float sy = (en.cflags & ENT_CONJ) ? -1.f : 1.f;
-      const float sg = (en.cflags & ENT_NEG) ? -1.f : 1.f;
+      for (int k = 0; k < K::B; ++k) val[k] = make_float2(0.f, 0.f);
+      int row = -1 - lane;  // distinct sentinel for lanes past the range
+      if (valid) {
+        const GridEntry en = tb.ent[e];
+        row = en.row;
+        const int c = en.cflags >> 2;
+        const int tf = tstart + __ldg(dl + c);
+        const size_t rowoff = (size_t)en.bc * g.nint_pad;
+        const float sy = (en.cflags & ENT_CONJ) ? -1.f : 1.f;
+        const float sg = (en.cflags & ENT_NEG) ? -1.f : 1.f;
 #pragma unroll
-      for (int k = 0; k < K::B; ++k) {
-        if (k < gr.nimg) {
-          float2 a = make_float2(0.f, 0.f);
-          const int tk = tf + k * dt;
-          for (int j = 0; j < dt; ++j) {
-            const int ti = tk + j;
-            if (ti < g.nint) a = cadd(a, load_sample<FP16>(S, rowoff + ti));
+        for (int k = 0; k < K::B; ++k) {
+          if (k < gr.nimg) {
+            float2 a = make_float2(0.f, 0.f);
+            const int tk = tf + k * dt;
+            for (int j = 0; j < dt; ++j) {
+              const int ti = tk + j;
+              if (ti < g.nint) a = cadd(a, load_sample<FP16>(S, rowoff + ti));
+            }
+            val[k] = make_float2(sg * a.x, sg * sy * a.y);
           }
-          acc[k].x += sg * a.x;
-          acc[k].y += sg * sy * a.y;
         }
       }
-    }
-    const int xbase = (col - col0) * K::B;
+      // inclusive segmented scan over lanes with equal row (rows are sorted)
 #pragma unroll
-    for (int k = 0; k < K::B; ++k) sm[(xbase + k) * K::STRIDE + pad16(row)] = acc[k];
+      for (int off = 1; off < 32; off <<= 1) {
+        const int rup = __shfl_up_sync(0xffffffffu, row, off);
+        const bool take = lane >= off && rup == row;
+#pragma unroll
+        for (int k = 0; k < K::B; ++k) {
+          const float vx = __shfl_up_sync(0xffffffffu, val[k].x, off);
+          const float vy = __shfl_up_sync(0xffffffffu, val[k].y, off);
+          if (take) {
+            val[k].x += vx;
+            val[k].y += vy;
+          }
+        }
+      }
+      const int rdown = __shfl_down_sync(0xffffffffu, row, 1);
+      const bool tail = valid && (lane == 31 || e + 1 >= eend || rdown != row);
+      if (tail) {
+        float2* cp = colbuf + pad16(row);
+#pragma unroll
+        for (int k = 0; k < K::B; ++k) cp[k * K::STRIDE] = cadd(cp[k * K::STRIDE], val[k]);
+      }
+      __syncwarp();
+    }
   }
   __syncthreads();
 
@@ -290,6 +324,7 @@ void fill_shape(ImageKernelShape* o) {
   o->cols_per_cta = K::C;
   o->threads_a = K::THREADS_A;
   o->smem_a = K::SMEM_A;
+  o->warps_per_col = K::WPC;
   o->rows_per_cta = K::RB;
   o->threads_b = K::THREADS_B;
   o->smem_b = K::SMEM_B;
