@@ -249,6 +249,43 @@ typedef struct rf_kernel_profile {
 rf_status rf_plan_set_profiling(struct rf_plan* plan, int32_t enable);
 rf_status rf_plan_get_profile(const struct rf_plan* plan, rf_kernel_profile* out, int32_t cap, int32_t* n);
 
+/*
+ * rf_image_stats_noalloc -- an entry point that allocates nothing.  The
+ * paper has no counterpart to it: it exists for callers of this library that
+ * cannot allocate device memory at the point where they image, such as code
+ * recording a CUDA graph (cudaMalloc cannot be captured), a real-time loop
+ * that cannot take the allocator's latency or failures, or a host framework
+ * that owns the device memory pool.
+ *
+ * It images one uv half plane and measures the image as the search does:
+ *   I[y][x] = (1 / 2W) sum over the Hermitian full plane of
+ *             H[v][u] exp(+2 pi i (u (x - N/2) + v (y - N/2)) / N),
+ * then peak (lowest y N + x on ties), mean, population sigma and peak/sigma.
+ * half_plane  device [npix][npix/2 + 1] complex64 (interleaved float re, im),
+ *             row v mod N, column u = 0 .. N/2.  Column 0 must hold the
+ *             whole Hermitian column (both v and -v entries); column N/2 is
+ *             ignored (treated as empty).
+ * npix        a power of two in [16, RF_NOALLOC_MAX_NPIX].  Larger images
+ *             are rejected with RF_ERR_INVALID_ARG: the scratch is a static
+ *             device array sized for RF_NOALLOC_MAX_NPIX.
+ * weight      W > 0, the normalisation of the image (samples gridded).
+ * stream      cudaStream_t (NULL = default stream); the call is asynchronous.
+ * stat        device pointer to one rf_image_stat; dm_idx, dt_idx and t_idx
+ *             are written as 0.
+ * It runs on the current CUDA device and calls no cudaMalloc or cudaFree.
+ * Its scratch (the column-FFT intermediate and row partials, about 4 MiB
+ * for RF_NOALLOC_MAX_NPIX = 1024) is one static device array per GPU, held
+ * until the process exits and shared by every call: calls whose work
+ * overlaps on the GPU (other streams, other threads) race on it, so issue
+ * them one after another on one stream.  The first call on a device does a
+ * one-time set-up (looks up the array's device address and uploads twiddle
+ * tables with a synchronous copy); make that first call before any stream
+ * capture.  Errors: RF_ERR_INVALID_ARG, RF_ERR_NO_DEVICE, RF_ERR_CUDA.
+ */
+#define RF_NOALLOC_MAX_NPIX 1024
+rf_status rf_image_stats_noalloc(const void* half_plane, int32_t npix, double weight, void* stream,
+                                 rf_image_stat* stat);
+
 /* Library version string. */
 const char* rf_version(void);
 

@@ -24,7 +24,7 @@ __all__ = [
     "lib", "make_desc", "rf_plan_create", "rf_plan_destroy", "rf_search_segment",
     "rf_search_segment_stats", "rf_render_images", "rf_plan_set_form", "rf_plan_get_info",
     "rf_plan_delays", "rf_plan_cells", "rf_count_images", "rf_last_error", "rf_version",
-    "rf_plan_set_profiling", "rf_plan_get_profile", "RfKernelProfile",
+    "rf_plan_set_profiling", "rf_plan_get_profile", "RfKernelProfile", "rf_image_stats_noalloc",
     "Plan", "CANDIDATE_DTYPE", "STAT_DTYPE", "declared_symbols",
     "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
 ]
@@ -47,6 +47,7 @@ RF_EDGE_PARTIAL = 0x2
 RF_HOST_ONLY = 0x100
 RF_FORM_BATCHED = 0
 RF_FORM_PLAIN = 1
+RF_NOALLOC_MAX_NPIX = 1024
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
                       "realfast_gb300.h")
@@ -138,6 +139,7 @@ def lib() -> ctypes.CDLL:
         "rf_plan_cells": ([P, P, P, P], ctypes.c_int),
         "rf_count_images": ([P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "rf_plan_set_profiling": ([P, ctypes.c_int32], ctypes.c_int),
+        "rf_image_stats_noalloc": ([P, ctypes.c_int32, ctypes.c_double, P, P], ctypes.c_int),
         "rf_plan_get_profile": ([P, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -301,6 +303,11 @@ def rf_plan_get_profile(plan) -> dict:
     n = ctypes.c_int32()
     _check(lib().rf_plan_get_profile(plan, arr, 16, ctypes.byref(n)))
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n.value, 16))}
+
+
+def rf_image_stats_noalloc(half_plane, npix: int, weight: float, stat, stream=None) -> None:
+    """Image one device half plane into the device rf_image_stat `stat` (no allocation)."""
+    _check(lib().rf_image_stats_noalloc(_ptr(half_plane), npix, weight, _stream(stream), _ptr(stat)))
 
 
 class Plan:

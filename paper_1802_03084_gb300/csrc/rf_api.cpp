@@ -695,6 +695,10 @@ rf_status search_impl(rf_plan* p, const void* vis, int nint, void* stream, rf_ca
 
 }  // namespace
 
+namespace rf {
+void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+}  // namespace rf
+
 extern "C" {
 
 const char* rf_last_error(void) { return g_err.c_str(); }

@@ -121,4 +121,7 @@ struct ImageKernelShape {
 };
 bool image_kernel_shape(int npix, ImageKernelShape* out);
 
+// Sets the thread-local message returned by rf_last_error().
+void set_last_error(const char* msg);
+
 }  // namespace rf
