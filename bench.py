@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--wave-images", type=int, default=0, help="images per wave (0 = engine default)")
+    ap.add_argument("--host-input", action="store_true",
+                    help="time the search from pinned host input only (small device footprint for profilers)")
     return ap.parse_args()
 
 
@@ -322,12 +325,14 @@ def main():
     spec.seed += 1000 * rank       # each rank searches its own segment
     seg = synth.make_segment(spec)
     nint = spec.nint
-    vis_dev = torch.from_numpy(seg["vis"]).cuda()
-    vis_pin = torch.from_numpy(seg["vis"]).pin_memory() if not args.no_e2e else None
+    vis_pin = torch.from_numpy(seg["vis"]).pin_memory() if (not args.no_e2e or args.host_input) else None
+    vis_dev = vis_pin if args.host_input else torch.from_numpy(seg["vis"]).cuda()
     torch.cuda.synchronize()
     plan = rf.Plan.from_spec(spec, seg["ant_uvw"], seg["freq_hz"], max_nint=nint, device=local_rank)
     if args.form == "plain":
         plan.set_form(rf.RF_FORM_PLAIN)
+    if args.wave_images:
+        plan.set_wave_images(args.wave_images)
     info = plan.info()
     n_images = plan.count_images(nint)
     fp16 = spec.store == "fp16"
@@ -369,7 +374,7 @@ def main():
     n_cand = len(cands)
 
     e2e = None
-    if vis_pin is not None:
+    if vis_pin is not None and not args.no_e2e:
         plan.search(vis_pin, nint)
         if dist:
             dist.barrier()
@@ -402,6 +407,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if not fp16 else "f16-storage/f32", "data": "synthetic",
         "config": {"workload": workload_name(spec), "images_per_step": n_images, "form": args.form,
+                   "wave_images": plan.wave_images(), "input": "pinned host" if args.host_input else "HBM",
                    "l2": f"inputs larger than L2 ({seg['vis'].nbytes / 1e9:.2f} GB segment per step)",
                    "parallelism": f"dp{world} (one segment per GPU)"},
         "visibility_gbs": world * args.steps * seg["vis"].nbytes / (ms / 1e3) / 1e9,

@@ -219,6 +219,20 @@ rf_status rf_render_images(struct rf_plan* plan, const void* vis, int32_t nint, 
 /* Select the search form: RF_FORM_BATCHED (default) or RF_FORM_PLAIN. */
 rf_status rf_plan_set_form(struct rf_plan* plan, int32_t form);
 
+/*
+ * Tuning knobs (used by the autotuner; results do not depend on them).
+ * RF_TUNE_WAVE_IMAGES  images imaged per wave.  A wave's column-FFT
+ *                      intermediate is images x (iu_max + 1) x npix x 8 bytes;
+ *                      waves small enough to stay in L2 avoid an HBM round
+ *                      trip.  Range [images_per_group, 32768].  Reallocates
+ *                      the plan's scratch.
+ * Errors: RF_ERR_INVALID_ARG (unknown key or value out of range),
+ * RF_ERR_NO_MEMORY, RF_ERR_BUSY.
+ */
+#define RF_TUNE_WAVE_IMAGES 1
+rf_status rf_plan_set_tuning(struct rf_plan* plan, int32_t key, int64_t value);
+rf_status rf_plan_get_tuning(const struct rf_plan* plan, int32_t key, int64_t* value);
+
 /* Derived facts of a plan (see rf_plan_info). */
 rf_status rf_plan_get_info(const struct rf_plan* plan, rf_plan_info* info);
 

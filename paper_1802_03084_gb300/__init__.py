@@ -24,7 +24,7 @@ __all__ = [
     "lib", "make_desc", "rf_plan_create", "rf_plan_destroy", "rf_search_segment",
     "rf_search_segment_stats", "rf_render_images", "rf_plan_set_form", "rf_plan_get_info",
     "rf_plan_delays", "rf_plan_cells", "rf_count_images", "rf_last_error", "rf_version",
-    "rf_plan_set_profiling", "rf_plan_get_profile", "RfKernelProfile", "rf_image_stats_noalloc",
+    "rf_plan_set_profiling", "rf_plan_get_profile", "RfKernelProfile", "rf_image_stats_noalloc", "rf_plan_set_tuning", "rf_plan_get_tuning",
     "Plan", "CANDIDATE_DTYPE", "STAT_DTYPE", "declared_symbols",
     "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
 ]
@@ -48,6 +48,7 @@ RF_HOST_ONLY = 0x100
 RF_FORM_BATCHED = 0
 RF_FORM_PLAIN = 1
 RF_NOALLOC_MAX_NPIX = 1024
+RF_TUNE_WAVE_IMAGES = 1
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
                       "realfast_gb300.h")
@@ -139,6 +140,8 @@ def lib() -> ctypes.CDLL:
         "rf_plan_cells": ([P, P, P, P], ctypes.c_int),
         "rf_count_images": ([P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "rf_plan_set_profiling": ([P, ctypes.c_int32], ctypes.c_int),
+        "rf_plan_set_tuning": ([P, ctypes.c_int32, ctypes.c_int64], ctypes.c_int),
+        "rf_plan_get_tuning": ([P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "rf_image_stats_noalloc": ([P, ctypes.c_int32, ctypes.c_double, P, P], ctypes.c_int),
         "rf_plan_get_profile": ([P, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     }
@@ -305,6 +308,16 @@ def rf_plan_get_profile(plan) -> dict:
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n.value, 16))}
 
 
+def rf_plan_set_tuning(plan, key: int, value: int) -> None:
+    _check(lib().rf_plan_set_tuning(plan, key, value))
+
+
+def rf_plan_get_tuning(plan, key: int) -> int:
+    v = ctypes.c_int64()
+    _check(lib().rf_plan_get_tuning(plan, key, ctypes.byref(v)))
+    return int(v.value)
+
+
 def rf_image_stats_noalloc(half_plane, npix: int, weight: float, stat, stream=None) -> None:
     """Image one device half plane into the device rf_image_stat `stat` (no allocation)."""
     _check(lib().rf_image_stats_noalloc(_ptr(half_plane), npix, weight, _stream(stream), _ptr(stat)))
@@ -361,6 +374,12 @@ class Plan:
 
     def profile(self) -> dict:
         return rf_plan_get_profile(self.handle)
+
+    def set_wave_images(self, n: int):
+        rf_plan_set_tuning(self.handle, RF_TUNE_WAVE_IMAGES, n)
+
+    def wave_images(self) -> int:
+        return rf_plan_get_tuning(self.handle, RF_TUNE_WAVE_IMAGES)
 
     def close(self):
         if self.handle:

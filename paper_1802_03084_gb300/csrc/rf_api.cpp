@@ -87,9 +87,9 @@ struct BusyGuard {
   }
 };
 
-enum KernelKind { K_H2D = 0, K_INGEST, K_WEIGHTS, K_GRID_COLFFT, K_ROWFFT_STATS, K_FINALIZE, K_NKINDS };
-const char* const kKindNames[K_NKINDS] = {"h2d_copy", "ingest", "weights", "grid_colfft", "rowfft_stats",
-                                           "finalize"};
+enum KernelKind { K_H2D = 0, K_INGEST, K_RESAMPLE, K_WEIGHTS, K_GRID_COLFFT, K_ROWFFT_STATS, K_FINALIZE, K_NKINDS };
+const char* const kKindNames[K_NKINDS] = {"h2d_copy", "ingest", "resample", "weights", "grid_colfft",
+                                           "rowfft_stats", "finalize"};
 
 // Event-pair timing of every launch a plan issues while profiling is on.
 struct Profiler {
@@ -172,9 +172,9 @@ struct rf_plan {
   std::vector<int32_t> max_delay;  // [ndm]
   std::vector<int32_t> iu, iv;     // [nbl][nchan]
   std::vector<uint8_t> ongrid;     // [nbl][nchan]
-  std::vector<int32_t> col_ent_ptr, col_warp_ptr;
+  std::vector<int32_t> col_ent_ptr, col_warp_ptr, col_cell_ptr, cell_row;
   std::vector<GridEntry> ent;
-  int n_cells = 0;
+  int n_cells = 0, max_cells = 0;
   std::vector<int32_t> ongrid_chan;
   int n_on = 0, iu_max = 0, iv_max = 0, ncol = 1, n_offgrid = 0;
   rf::ImageKernelShape shape{};
@@ -186,6 +186,8 @@ struct rf_plan {
   rf::DevTables tb{};
   void* d_S = nullptr;
   int nint_pad = 0;
+  std::vector<void*> d_sdt;     // per dt index (dt = 1: d_S)
+  std::vector<int32_t> sdt_lp;  // per dt index
   float2* d_T = nullptr;
   int slots_max = 0;
   StatPartial* d_partials = nullptr;
@@ -221,6 +223,15 @@ struct rf_plan {
     device_bytes += bytes;
     *p = static_cast<T*>(q);
     return RF_OK;
+  }
+
+  void dfree(void* q) {
+    for (size_t i = 0; i < allocs.size(); ++i)
+      if (allocs[i] == q) {
+        cudaFree(q);
+        allocs.erase(allocs.begin() + i);
+        return;
+      }
   }
 
   ~rf_plan() {
@@ -383,24 +394,33 @@ rf_status build_tables(rf_plan* p) {
   p->ent.clear();
   p->ent.reserve(es.size());
   p->col_ent_ptr.assign(p->ncol + 1, 0);
+  p->col_cell_ptr.assign(p->ncol + 1, 0);
+  p->cell_row.clear();
   p->n_cells = 0;
+  p->max_cells = 0;
   std::vector<int> cell_start;  // entry index where each cell begins
   size_t i = 0;
   for (int col = 0; col < p->ncol; ++col) {
     p->col_ent_ptr[col] = (int)p->ent.size();
+    p->col_cell_ptr[col] = p->n_cells;
     int prev_row = -1;
+    int local = -1;
     while (i < es.size() && es[i].col == col) {
       if (es[i].row != prev_row) {
         cell_start.push_back((int)p->ent.size());
         prev_row = es[i].row;
+        p->cell_row.push_back(es[i].row);
         p->n_cells++;
+        ++local;
       }
       const int c = es[i].bc / nbl;
-      p->ent.push_back({es[i].bc, (c << 2) | es[i].flags, es[i].row, 0});
+      p->ent.push_back({es[i].bc, (c << 2) | es[i].flags, es[i].row, local});
       ++i;
     }
+    p->max_cells = std::max(p->max_cells, local + 1);
   }
   p->col_ent_ptr[p->ncol] = (int)p->ent.size();
+  p->col_cell_ptr[p->ncol] = p->n_cells;
   cell_start.push_back((int)p->ent.size());
   // Split each column's entries into WPC ranges that start on cell boundaries
   // and hold about the same number of entries.
@@ -461,6 +481,31 @@ void build_lists(rf_plan* p, int nint) {
   p->cached_nint = nint;
 }
 
+// (Re)allocate the per-wave scratch for `slots` images (clamped to
+// [images_per_group, 32768]: images per wave ride on gridDim.y).
+rf_status alloc_wave_scratch(rf_plan* p, int slots) {
+  const int B = p->shape.images_per_group;
+  slots = std::max(std::min(slots, 32768), B);
+  const size_t per_slot = (size_t)p->ncol * p->npix;
+  const int nrb = p->npix / p->shape.rows_per_cta;
+  if (p->d_T) {
+    p->device_bytes -= (uint64_t)p->slots_max * per_slot * sizeof(float2);
+    p->dfree(p->d_T);
+    p->d_T = nullptr;
+  }
+  if (p->d_partials) {
+    p->device_bytes -= (uint64_t)p->slots_max * nrb * sizeof(StatPartial);
+    p->dfree(p->d_partials);
+    p->d_partials = nullptr;
+  }
+  p->slots_max = slots;
+  p->cached_nint = -1;
+  rf_status s;
+  if ((s = p->dalloc(&p->d_T, (size_t)slots * per_slot)) != RF_OK) return s;
+  if ((s = p->dalloc(&p->d_partials, (size_t)slots * nrb)) != RF_OK) return s;
+  return RF_OK;
+}
+
 rf_status alloc_device(rf_plan* p) {
   const int N = p->npix;
   auto up = [&](auto** dst, const auto& vec) -> rf_status {
@@ -472,13 +517,16 @@ rf_status alloc_device(rf_plan* p) {
     *dst = d;
     return RF_OK;
   };
-  int32_t *d_delays, *d_dt, *d_cwp, *d_ogc;
-  GridEntry* d_ent;
+  int32_t *d_delays = nullptr, *d_dt = nullptr, *d_cwp = nullptr, *d_ogc = nullptr, *d_ccp = nullptr,
+          *d_crow = nullptr;
+  GridEntry* d_ent = nullptr;
   rf_status s;
   if ((s = up(&d_delays, p->delays)) != RF_OK) return s;
   std::vector<int32_t> dtv(p->dt.begin(), p->dt.end());
   if ((s = up(&d_dt, dtv)) != RF_OK) return s;
   if ((s = up(&d_cwp, p->col_warp_ptr)) != RF_OK) return s;
+  if ((s = up(&d_ccp, p->col_cell_ptr)) != RF_OK) return s;
+  if ((s = up(&d_crow, p->cell_row)) != RF_OK) return s;
   if ((s = up(&d_ent, p->ent)) != RF_OK) return s;
   if ((s = up(&d_ogc, p->ongrid_chan)) != RF_OK) return s;
   std::vector<float2> tw(N);
@@ -486,11 +534,13 @@ rf_status alloc_device(rf_plan* p) {
     const double a = kTwoPi * (double)m / (double)N;
     tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
   }
-  float2* d_tw;
+  float2* d_tw = nullptr;
   if ((s = up(&d_tw, tw)) != RF_OK) return s;
   p->tb.delays = d_delays;
   p->tb.dt_list = d_dt;
   p->tb.col_warp_ptr = d_cwp;
+  p->tb.col_cell_ptr = d_ccp;
+  p->tb.cell_row = d_crow;
   p->tb.ent = d_ent;
   p->tb.ongrid_chan = d_ogc;
   p->tb.twiddle = d_tw;
@@ -498,15 +548,45 @@ rf_status alloc_device(rf_plan* p) {
   // Stokes-I time series S[c * nbl + b][t]
   p->nint_pad = (p->max_nint + 31) / 32 * 32;
   const size_t esz = (p->flags & RF_STORE_FP16) ? 4 : 8;
-  unsigned char* dS;
+  unsigned char* dS = nullptr;
   if ((s = p->dalloc(&dS, (size_t)p->nbl * p->nchan * p->nint_pad * esz)) != RF_OK) return s;
   p->d_S = dS;
+  // resampled series per dt (phase-split, same storage type as S)
+  p->d_sdt.assign(p->ndt, nullptr);
+  p->sdt_lp.assign(p->ndt, 0);
+  std::vector<unsigned long long> sdt_addr(p->ndt, 0);
+  for (int k = 0; k < p->ndt; ++k) {
+    const int dt = p->dt[k];
+    const int lp = (p->nint_pad + dt - 1) / dt;
+    p->sdt_lp[k] = lp;
+    if (dt == 1) {
+      p->d_sdt[k] = dS;
+    } else {
+      bool same = false;
+      for (int k2 = 0; k2 < k; ++k2)
+        if (p->dt[k2] == dt) {
+          p->d_sdt[k] = p->d_sdt[k2];
+          same = true;
+        }
+      if (!same) {
+        unsigned char* b = nullptr;
+        if ((s = p->dalloc(&b, (size_t)p->nbl * p->nchan * dt * lp * esz)) != RF_OK) return s;
+        p->d_sdt[k] = b;
+      }
+    }
+    sdt_addr[k] = (unsigned long long)(uintptr_t)p->d_sdt[k];
+  }
+  unsigned long long* d_sdt_addr = nullptr;
+  int32_t* d_sdt_lp = nullptr;
+  if ((s = up(&d_sdt_addr, sdt_addr)) != RF_OK) return s;
+  if ((s = up(&d_sdt_lp, p->sdt_lp)) != RF_OK) return s;
+  p->tb.sdt_ptr = d_sdt_addr;
+  p->tb.sdt_lp = d_sdt_lp;
 
   // image lists for the largest segment
   const int64_t nimg_max = count_images(p, p->max_nint);
   if (nimg_max > (1ll << 30)) return fail(RF_ERR_INVALID_ARG, "too many images per segment (%lld)", (long long)nimg_max);
   p->img_cap = (int)std::max<int64_t>(nimg_max, 1);
-  const int B = p->shape.images_per_group;
   p->group_cap = p->img_cap;  // at most one group per image
   if ((s = p->dalloc(&p->d_img_info, p->img_cap)) != RF_OK) return s;
   if ((s = p->dalloc(&p->d_groups, p->group_cap)) != RF_OK) return s;
@@ -517,12 +597,7 @@ rf_status alloc_device(rf_plan* p) {
   // column-FFT scratch, whole groups per wave
   const size_t per_slot = (size_t)p->ncol * N * sizeof(float2);
   int slots = (int)std::min<size_t>(kTBudgetBytes / per_slot, (size_t)p->img_cap);
-  slots = std::min(slots, 32768);  // images per wave ride on gridDim.y
-  slots = std::max(slots, B);
-  p->slots_max = slots;
-  if ((s = p->dalloc(&p->d_T, (size_t)slots * p->ncol * N)) != RF_OK) return s;
-  const int nrb = N / p->shape.rows_per_cta;
-  if ((s = p->dalloc(&p->d_partials, (size_t)slots * nrb)) != RF_OK) return s;
+  if ((s = alloc_wave_scratch(p, slots)) != RF_OK) return s;
 
   // host->device staging of raw visibilities
   const size_t per_int = (size_t)p->nbl * p->nchan * p->npol * sizeof(float2);
@@ -540,6 +615,7 @@ SegmentGeom geom(const rf_plan* p, int nint) {
   g.npix = p->npix;
   g.ncol = p->ncol;
   g.ndm = p->ndm;
+  g.max_cells = p->max_cells;
   g.fp16 = (p->flags & RF_STORE_FP16) != 0;
   return g;
 }
@@ -568,6 +644,19 @@ rf_status ingest(rf_plan* p, const void* vis, int nint, cudaStream_t st) {
     RF_TIMED(p->prof, K_H2D, st,
              cudaMemcpyAsync(p->d_stage, src + (size_t)t * per_int, (size_t)nt * per_int, cudaMemcpyHostToDevice, st));
     RF_TIMED(p->prof, K_INGEST, st, rf::launch_ingest(p->d_stage, nt, t, p->npol, g, p->d_S, st));
+  }
+  return RF_OK;
+}
+
+// Resampled series for every dt > 1 of the plan (after ingest).
+rf_status resample_all(rf_plan* p, int nint, cudaStream_t st) {
+  const SegmentGeom g = geom(p, nint);
+  for (int k = 0; k < p->ndt; ++k) {
+    if (p->dt[k] == 1 || p->d_sdt[k] == p->d_S) continue;
+    bool done = false;
+    for (int k2 = 0; k2 < k; ++k2) done = done || p->d_sdt[k2] == p->d_sdt[k];
+    if (done) continue;
+    RF_TIMED(p->prof, K_RESAMPLE, st, rf::launch_resample(g, p->d_S, p->d_sdt[k], p->dt[k], p->sdt_lp[k], st));
   }
   return RF_OK;
 }
@@ -611,6 +700,8 @@ rf_status search_impl(rf_plan* p, const void* vis, int nint, void* stream, rf_ca
   *n_out = 0;
 
   rf_status s = ingest(p, vis, nint, st);
+  if (s != RF_OK) return s;
+  s = resample_all(p, nint, st);
   if (s != RF_OK) return s;
   if (p->cached_nint != nint) {
     build_lists(p, nint);
@@ -799,6 +890,8 @@ rf_status rf_render_images(rf_plan* p, const void* vis, int32_t nint, void* stre
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   rf_status s = ingest(p, vis, nint, st);
   if (s != RF_OK) return s;
+  s = resample_all(p, nint, st);
+  if (s != RF_OK) return s;
   std::vector<int4> info(n);
   std::vector<Group> grp(n);
   for (int k = 0; k < n; ++k) {
@@ -858,6 +951,26 @@ rf_status rf_plan_get_profile(const rf_plan* plan, rf_kernel_profile* out, int32
     out[k].launches = plan->prof.launches[k];
     out[k].total_ms = plan->prof.total_ms[k];
   }
+  return RF_OK;
+}
+
+rf_status rf_plan_set_tuning(rf_plan* p, int32_t key, int64_t value) {
+  if (!p) return fail(RF_ERR_INVALID_ARG, "plan is NULL");
+  if (key != RF_TUNE_WAVE_IMAGES) return fail(RF_ERR_INVALID_ARG, "unknown tuning key %d", key);
+  if (p->host_only) return fail(RF_ERR_INVALID_ARG, "plan was created with RF_HOST_ONLY");
+  if (value < p->shape.images_per_group || value > 32768)
+    return fail(RF_ERR_INVALID_ARG, "wave images %lld out of [%d, 32768]", (long long)value,
+                p->shape.images_per_group);
+  BusyGuard bg(&p->busy);
+  if (!bg.owned) return fail(RF_ERR_BUSY, "plan is in use by another call");
+  DeviceGuard dg(p->device);
+  return alloc_wave_scratch(p, (int)value);
+}
+
+rf_status rf_plan_get_tuning(const rf_plan* p, int32_t key, int64_t* value) {
+  if (!p || !value) return fail(RF_ERR_INVALID_ARG, "NULL argument");
+  if (key != RF_TUNE_WAVE_IMAGES) return fail(RF_ERR_INVALID_ARG, "unknown tuning key %d", key);
+  *value = p->slots_max;
   return RF_OK;
 }
 

@@ -13,12 +13,13 @@ constexpr int ENT_NEG = 2;   // checkerboard sign (-1)^(iu + iv) is -1
 
 // One contribution of a (baseline, channel) visibility to a half-plane cell.
 // bc = row c * nbl + b of the Stokes-I time series; cflags = (c << 2) | flags;
-// row = the cell's v index iv mod N in its column.
+// row = the cell's v index iv mod N in its column; cell = the cell's index
+// within its column (cells numbered in row order).
 struct GridEntry {
   int32_t bc;
   int32_t cflags;
   int32_t row;
-  int32_t pad;
+  int32_t cell;
 };
 
 // Device tables of a plan (all device pointers).
@@ -26,9 +27,16 @@ struct DevTables {
   const int32_t* delays;        // [ndm][nchan] integrations
   const int32_t* dt_list;       // [ndt]
   const int32_t* col_warp_ptr;  // [ncol][WPC + 1] entry ranges of the warps gridding a column
+  const int32_t* col_cell_ptr;  // [ncol + 1] first cell of each column
+  const int32_t* cell_row;      // [ncells] row (iv mod N) of each cell
   const GridEntry* ent;         // [nent] sorted by (column, row)
   const int32_t* ongrid_chan;   // [nchan] on-grid baselines per channel
   const float2* twiddle;        // [npix] exp(+2 pi i m / N)
+  // boxcar-resampled Stokes I per dt index s, phase-split: element (row, p, i)
+  // at sdt_ptr[s] + row * dt * sdt_lp[s] + p * sdt_lp[s] + i holds
+  // sum_{j < dt, i dt + p + j < nint} S[row][i dt + p + j]
+  const unsigned long long* sdt_ptr;  // [ndt] device addresses (dt = 1: S itself)
+  const int32_t* sdt_lp;              // [ndt] phase length ceil(nint_pad / dt)
 };
 
 // Group of consecutive output integrations of one (DM, dt) trial imaged
@@ -74,6 +82,7 @@ struct SegmentGeom {
   int npix;
   int ncol;       // half-plane columns imaged: 0 .. iu_max
   int ndm;
+  int max_cells;  // largest number of occupied cells in one column
   bool fp16;      // Stokes-I stored as half2
 };
 
@@ -85,6 +94,10 @@ struct SegmentGeom {
 // time-major buffer S[c * nbl + b][t].
 cudaError_t launch_ingest(const float2* vis, int nt, int t_begin, int npol, const SegmentGeom& g, void* S,
                           cudaStream_t st);
+
+// Boxcar resampling of S into the phase-split series of width dt (see
+// DevTables::sdt_ptr) for the first nint integrations.
+cudaError_t launch_resample(const SegmentGeom& g, const void* S, void* Sdt, int dt, int lp, cudaStream_t st);
 
 // W of each listed image (img_info[i] = {d, s, t, 0}); n_on = on-grid
 // (baseline, channel) pairs.

@@ -1,16 +1,25 @@
 // rf_fft.cuh -- shared-memory Stockham FFT building blocks for the imaging
-// kernels (the 2D inverse FFT of the dirty image, Sec. 3.1 / Sec. 3.2: "the 2d
-// FFT for imaging" is the most demanding stage).
+// kernels (the 2D inverse FFT of the dirty image, Sec. 3.1 / Sec. 3.2: the
+// 2D FFT is the most demanding stage of the search).
 //
-// A length-N transform (N a power of two, 16..8192) is done by T = N/16
-// threads.  Each pass is a radix-P Stockham autosort step: thread t loads the
-// P inputs j + r*(N/P) of each of its 16/P butterflies j, applies the twiddles
+// A length-N transform (N a power of two, 16..8192) is done by T = N/E
+// threads that each hold E = 32 complex values (E = 16 for N = 16).  Each
+// pass is a radix-P Stockham autosort step: thread t loads the P inputs
+// j + r (N/P) of each of its E/P butterflies j, multiplies them by
 // exp(+2 pi i k r / (Ns P)) with k = j mod Ns, does a radix-P inverse DFT in
 // registers and stores output q at (j / Ns) Ns P + k + q Ns.  All passes are
-// radix 16 except the last, whose radix is N / 16^floor(log16 N) when N is not
-// a power of 16.  Data stay in one padded shared-memory buffer per transform;
-// a barrier separates the loads and stores of a pass, so the transform is in
-// place.  The sign is +1 (inverse DFT, no 1/N scaling).
+// radix E except the last, whose radix is N / E^floor(log_E N) when N is not
+// a power of E.  For N = 1024 that is two radix-32 passes.  The data stay in
+// one padded shared-memory buffer per transform (a spare slot every 32
+// values keeps the strided first-pass stores free of bank conflicts); a
+// barrier separates the loads and stores of a pass so the transform is in
+// place.  Transforms of at most 32 threads synchronise with __syncwarp, wider
+// ones with a named barrier of their own.  Sign +1 (inverse DFT), no 1/N.
+//
+// Twiddles: per butterfly, the powers w^(s r), r < P, are built from the
+// table values w^s, w^2s, w^4s, ... (FP64-computed, rounded to FP32) by one
+// complex product each, so every twiddle is at most four roundings away
+// from the table.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,21 +35,19 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cmul_i(float2 a) { return make_float2(-a.y, a.x); }  // i * a
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 
-// exp(2 pi i k / 16) for the constant twiddles inside the radix-8/16 kernels.
-#define RF_C16_1 0.92387953251128675613f
-#define RF_S16_1 0.38268343236508977173f
+// cos and sin of 2 pi k / 32, k = 1..7 (the others follow by symmetry).
+#define RF_C32_1 0.98078528040323044913f
+#define RF_S32_1 0.19509032201612826785f
+#define RF_C32_2 0.92387953251128675613f
+#define RF_S32_2 0.38268343236508977173f
+#define RF_C32_3 0.83146961230254523708f
+#define RF_S32_3 0.55557023301960222474f
 #define RF_R2_2 0.70710678118654752440f
 
-// Padded shared-memory index: one spare slot every 16 complex values keeps the
-// strided stores of the first pass free of bank conflicts.
-__host__ __device__ __forceinline__ constexpr int pad16(int i) { return i + (i >> 4); }
-
-// Per-transform shared-memory stride (in float2).  The extra 2 makes buffers
-// of consecutive transforms start on different bank pairs.
-template <int N>
-__host__ __device__ constexpr int fft_stride() { return N + N / 16 + 2; }
-
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
+
+// Padded shared-memory index: one spare slot every 32 complex values.
+__host__ __device__ __forceinline__ constexpr int padx(int i) { return i + (i >> 5); }
 
 // In-register inverse radix-4 on v[0], v[S], v[2S], v[3S] (natural order out).
 template <int S>
@@ -55,8 +62,7 @@ __device__ __forceinline__ void dft4(float2* v) {
   v[3 * S] = csub(t1, t3);
 }
 
-// Radix-P inverse DFT of v[0..P) in registers.  The result X[q] sits in
-// v[dft_perm<P>(q)].
+// Radix-P inverse DFT of v[0..P) in registers; X[q] ends in v[dft_perm<P>(q)].
 template <int P>
 __device__ __forceinline__ void dft(float2* v);
 
@@ -91,71 +97,132 @@ __device__ __forceinline__ void dft<8>(float2* v) {
 }
 
 // 16 = 4 x 4: r = 4 r1 + r2, q = q1 + 4 q2.  Radix-4 over r1 for each r2
-// (stride 4), twiddle w16^(r2 q1), radix-4 over r2; X[q1 + 4 q2] lands in
-// v[4 q1 + q2].
+// (stride 4) leaves Y[r2][q1] at v[r2 + 4 q1]; twiddle w16^(r2 q1); radix-4
+// over r2, i.e. over the contiguous v[4 q1 .. 4 q1 + 3]; X[q1 + 4 q2] lands
+// in v[4 q1 + q2].
 template <>
 __device__ __forceinline__ void dft<16>(float2* v) {
 #pragma unroll
   for (int r2 = 0; r2 < 4; ++r2) dft4<4>(v + r2);
-  // v[r2 + 4 q1] *= w16^(r2 q1)
-  v[5] = cmul(v[5], make_float2(RF_C16_1, RF_S16_1));   // w^1
-  v[9] = cmul(v[9], make_float2(RF_R2_2, RF_R2_2));     // w^2
-  v[13] = cmul(v[13], make_float2(RF_S16_1, RF_C16_1)); // w^3
-  v[6] = cmul(v[6], make_float2(RF_R2_2, RF_R2_2));     // w^2
-  v[10] = cmul_i(v[10]);                                // w^4
-  v[14] = cmul(v[14], make_float2(-RF_R2_2, RF_R2_2));  // w^6
-  v[7] = cmul(v[7], make_float2(RF_S16_1, RF_C16_1));   // w^3
-  v[11] = cmul(v[11], make_float2(-RF_R2_2, RF_R2_2));  // w^6
-  v[15] = cmul(v[15], make_float2(-RF_C16_1, -RF_S16_1)); // w^9
-  // Y[r2][q1] sits at v[r2 + 4 q1], so for fixed q1 the second radix-4 runs
-  // over the contiguous v[4 q1 .. 4 q1 + 3].
+  v[5] = cmul(v[5], make_float2(RF_C32_2, RF_S32_2));     // w16^1
+  v[9] = cmul(v[9], make_float2(RF_R2_2, RF_R2_2));       // w16^2
+  v[13] = cmul(v[13], make_float2(RF_S32_2, RF_C32_2));   // w16^3
+  v[6] = cmul(v[6], make_float2(RF_R2_2, RF_R2_2));       // w16^2
+  v[10] = cmul_i(v[10]);                                  // w16^4
+  v[14] = cmul(v[14], make_float2(-RF_R2_2, RF_R2_2));    // w16^6
+  v[7] = cmul(v[7], make_float2(RF_S32_2, RF_C32_2));     // w16^3
+  v[11] = cmul(v[11], make_float2(-RF_R2_2, RF_R2_2));    // w16^6
+  v[15] = cmul(v[15], make_float2(-RF_C32_2, -RF_S32_2)); // w16^9
 #pragma unroll
   for (int q1 = 0; q1 < 4; ++q1) dft4<1>(v + 4 * q1);
 }
 
+// 32 = 2 x 16: r = 16 r1 + r2, q = q1 + 2 q2.  Radix-2 over r1 for each r2
+// leaves Y[r2][q1] at v[r2 + 16 q1]; twiddle w32^(r2 q1); radix-16 over the
+// contiguous halves; X[q1 + 2 q2] lands in v[16 q1 + dft_perm<16>(q2)].
+template <>
+__device__ __forceinline__ void dft<32>(float2* v) {
+#pragma unroll
+  for (int r2 = 0; r2 < 16; ++r2) {
+    float2 a = v[r2], b = v[r2 + 16];
+    v[r2] = cadd(a, b);
+    v[r2 + 16] = csub(a, b);
+  }
+  // w32^r for r = 1..15
+  v[17] = cmul(v[17], make_float2(RF_C32_1, RF_S32_1));
+  v[18] = cmul(v[18], make_float2(RF_C32_2, RF_S32_2));
+  v[19] = cmul(v[19], make_float2(RF_C32_3, RF_S32_3));
+  v[20] = cmul(v[20], make_float2(RF_R2_2, RF_R2_2));
+  v[21] = cmul(v[21], make_float2(RF_S32_3, RF_C32_3));
+  v[22] = cmul(v[22], make_float2(RF_S32_2, RF_C32_2));
+  v[23] = cmul(v[23], make_float2(RF_S32_1, RF_C32_1));
+  v[24] = cmul_i(v[24]);
+  v[25] = cmul(v[25], make_float2(-RF_S32_1, RF_C32_1));
+  v[26] = cmul(v[26], make_float2(-RF_S32_2, RF_C32_2));
+  v[27] = cmul(v[27], make_float2(-RF_S32_3, RF_C32_3));
+  v[28] = cmul(v[28], make_float2(-RF_R2_2, RF_R2_2));
+  v[29] = cmul(v[29], make_float2(-RF_C32_3, RF_S32_3));
+  v[30] = cmul(v[30], make_float2(-RF_C32_2, RF_S32_2));
+  v[31] = cmul(v[31], make_float2(-RF_C32_1, RF_S32_1));
+  dft<16>(v);
+  dft<16>(v + 16);
+}
+
 template <int P>
 __host__ __device__ constexpr int dft_perm(int q) {
-  return P == 16 ? 4 * (q & 3) + (q >> 2) : (P == 8 ? 4 * (q & 1) + (q >> 1) : q);
+  return P == 32 ? 16 * (q & 1) + (4 * ((q >> 1) & 3) + (q >> 3))
+                 : (P == 16 ? 4 * (q & 3) + (q >> 2) : (P == 8 ? 4 * (q & 1) + (q >> 1) : q));
 }
 
 // Compile-time pass layout of a length-N transform.
 template <int N>
 struct FftShape {
-  static_assert(N >= 16 && (N & (N - 1)) == 0, "N must be a power of two >= 16");
-  static constexpr int T = N / 16;                     // threads per transform
+  static_assert(N >= 16 && N <= 8192 && (N & (N - 1)) == 0, "N must be a power of two in [16, 8192]");
+  static constexpr int E = N >= 32 ? 32 : 16;           // complex values per thread
+  static constexpr int T = N / E;                       // threads per transform
   static constexpr int LOG2N = ilog2c(N);
-  static constexpr int NFULL = LOG2N / 4;              // radix-16 passes
-  static constexpr int RL = 1 << (LOG2N % 4);          // last radix (1 = none)
+  static constexpr int LOG2E = ilog2c(E);
+  static constexpr int NFULL = LOG2N / LOG2E;           // radix-E passes
+  static constexpr int RL = 1 << (LOG2N % LOG2E);       // last radix (1 = none)
   static constexpr int NPASS = NFULL + (RL > 1 ? 1 : 0);
-  static constexpr int LAST_P = RL > 1 ? RL : 16;
-  static constexpr int LAST_NS = N / LAST_P;           // stride of the last pass
+  static constexpr int LAST_P = RL > 1 ? RL : E;
+  static constexpr int STRIDE = N + N / 32 + 2;         // float2 per transform buffer
 };
+
+template <int N>
+__host__ __device__ constexpr int fft_stride() { return FftShape<N>::STRIDE; }
+
+// Barrier among the T threads of transform `xf` of a block.
+template <int T>
+__device__ __forceinline__ void fft_sync(int xf) {
+  if (T <= 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + xf), "r"(T) : "memory");
+  }
+}
+
+// Twiddles w^(s r), r = 1 .. P-1, from the table entries w^(s 2^i).
+template <int N, int P>
+__device__ __forceinline__ void twiddle_mul(float2* v, const float2* __restrict__ tw, int s) {
+  float2 W[P];
+#pragma unroll
+  for (int p2 = 1; p2 < P; p2 <<= 1) W[p2] = __ldg(tw + s * p2);
+#pragma unroll
+  for (int r = 3; r < P; ++r) {
+    const int lb = r & -r;
+    if (r != lb) W[r] = cmul(W[r - lb], W[lb]);
+  }
+#pragma unroll
+  for (int r = 1; r < P; ++r) v[r] = cmul(v[r], W[r]);
+}
 
 // Load phase of one pass: v[m P + r] = s[j + r N/P], j = t + m T.
 template <int N, int P>
-__device__ __forceinline__ void pass_load(float2 (&v)[16], const float2* s, int t) {
-  constexpr int T = N / 16;
+__device__ __forceinline__ void pass_load(float2 (&v)[FftShape<N>::E], const float2* s, int t) {
+  constexpr int E = FftShape<N>::E;
+  constexpr int T = FftShape<N>::T;
   constexpr int J = N / P;
 #pragma unroll
-  for (int m = 0; m < 16 / P; ++m) {
+  for (int m = 0; m < E / P; ++m) {
     const int j = t + m * T;
 #pragma unroll
-    for (int r = 0; r < P; ++r) v[m * P + r] = s[pad16(j + r * J)];
+    for (int r = 0; r < P; ++r) v[m * P + r] = s[padx(j + r * J)];
   }
 }
 
 // Twiddle + radix-P DFT of each butterfly held by the thread.
 template <int N, int P>
-__device__ __forceinline__ void pass_compute(float2 (&v)[16], const float2* __restrict__ tw, int t, int Ns) {
-  constexpr int T = N / 16;
+__device__ __forceinline__ void pass_compute(float2 (&v)[FftShape<N>::E], const float2* __restrict__ tw, int t,
+                                             int Ns) {
+  constexpr int E = FftShape<N>::E;
+  constexpr int T = FftShape<N>::T;
 #pragma unroll
-  for (int m = 0; m < 16 / P; ++m) {
+  for (int m = 0; m < E / P; ++m) {
     const int j = t + m * T;
     if (Ns > 1) {
       const int k = j & (Ns - 1);
-      const int step = k * (N / (Ns * P));
-#pragma unroll
-      for (int r = 1; r < P; ++r) v[m * P + r] = cmul(v[m * P + r], __ldg(tw + step * r));
+      twiddle_mul<N, P>(v + m * P, tw, k * (N / (Ns * P)));
     }
     dft<P>(v + m * P);
   }
@@ -163,42 +230,60 @@ __device__ __forceinline__ void pass_compute(float2 (&v)[16], const float2* __re
 
 // Store phase of a non-final pass.
 template <int N, int P>
-__device__ __forceinline__ void pass_store(const float2 (&v)[16], float2* s, int t, int Ns) {
-  constexpr int T = N / 16;
+__device__ __forceinline__ void pass_store(const float2 (&v)[FftShape<N>::E], float2* s, int t, int Ns) {
+  constexpr int E = FftShape<N>::E;
+  constexpr int T = FftShape<N>::T;
 #pragma unroll
-  for (int m = 0; m < 16 / P; ++m) {
+  for (int m = 0; m < E / P; ++m) {
     const int j = t + m * T;
     const int k = j & (Ns - 1);
     const int base = (j - k) * P + k;
 #pragma unroll
-    for (int q = 0; q < P; ++q) s[pad16(base + q * Ns)] = v[m * P + dft_perm<P>(q)];
+    for (int q = 0; q < P; ++q) s[padx(base + q * Ns)] = v[m * P + dft_perm<P>(q)];
   }
 }
 
-// Runs every pass but the last on the buffer `s` (in place), then loads and
-// computes the last pass into registers.  On return the thread holds the
-// outputs X[o] for o = t + m T + q (N / LAST_P) in v[m LAST_P + dft_perm(q)]
-// (m < 16/LAST_P, q < LAST_P).  Every thread of the block must call this
-// (it contains __syncthreads); `s` must be filled before the call and
-// visible to all threads (a barrier before the call).
+// Runs the passes after the first-pass load.  On entry v holds the first
+// pass's inputs (v[r] = x[t + r T]); on return the thread holds the outputs
+// X[o] for o = t + m T + q (N / LAST_P) in v[m LAST_P + dft_perm(q)].
 template <int N>
-__device__ __forceinline__ void fft_inverse_to_regs(float2 (&v)[16], float2* s, const float2* __restrict__ tw, int t) {
+__device__ __forceinline__ void fft_inverse_from_regs(float2 (&v)[FftShape<N>::E], float2* s,
+                                                      const float2* __restrict__ tw, int t, int xf) {
   using S = FftShape<N>;
-  int Ns = 1;
+  if (S::NPASS == 1) {
+    pass_compute<N, S::LAST_P>(v, tw, t, 1);
+    return;
+  }
+  pass_compute<N, S::E>(v, tw, t, 1);
+  pass_store<N, S::E>(v, s, t, 1);
+  fft_sync<S::T>(xf);
+  int Ns = S::E;
 #pragma unroll
-  for (int p = 0; p < S::NPASS - 1; ++p) {
-    pass_load<N, 16>(v, s, t);
-    __syncthreads();
-    pass_compute<N, 16>(v, tw, t, Ns);
-    pass_store<N, 16>(v, s, t, Ns);
-    __syncthreads();
-    Ns *= 16;
+  for (int p = 1; p < S::NPASS - 1; ++p) {
+    pass_load<N, S::E>(v, s, t);
+    fft_sync<S::T>(xf);
+    pass_compute<N, S::E>(v, tw, t, Ns);
+    pass_store<N, S::E>(v, s, t, Ns);
+    fft_sync<S::T>(xf);
+    Ns *= S::E;
   }
   pass_load<N, S::LAST_P>(v, s, t);
   pass_compute<N, S::LAST_P>(v, tw, t, Ns);
 }
 
-// Output index of register (m, q) after fft_inverse_to_regs.
+// The same with the first-pass inputs read from the padded buffer `s`
+// (filled and made visible to the transform's threads by the caller).
+template <int N>
+__device__ __forceinline__ void fft_inverse_to_regs(float2 (&v)[FftShape<N>::E], float2* s,
+                                                    const float2* __restrict__ tw, int t, int xf) {
+  using S = FftShape<N>;
+  constexpr int P0 = S::NPASS == 1 ? S::LAST_P : S::E;
+  pass_load<N, P0>(v, s, t);
+  if (S::NPASS > 1) fft_sync<S::T>(xf);  // in place: all loads before the first store
+  fft_inverse_from_regs<N>(v, s, tw, t, xf);
+}
+
+// Output index of register (m, q) after the last pass.
 template <int N>
 __device__ __forceinline__ int fft_out_index(int t, int m, int q) {
   using S = FftShape<N>;

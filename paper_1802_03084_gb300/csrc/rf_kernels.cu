@@ -6,6 +6,8 @@
 #include <float.h>
 #include <limits.h>
 
+#include <algorithm>
+
 #include "rf_engine.h"
 
 namespace rf {
@@ -73,6 +75,56 @@ cudaError_t launch_ingest(const float2* vis, int nt, int t_begin, int npol, cons
     else
       k_ingest<false, 1><<<grid, block, 0, st>>>(vis, nt, t_begin, g.nbl, g.nchan, g.nint_pad, S);
   }
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- resample --
+// Boxcar resampling over dt integrations (Sec. 2.2: matched filters over
+// pulse width; Fig. 2: the loop over sampling time), computed once per
+// segment and width: out[row][p][i] = sum_{j<dt} S[row][i dt + p + j], the
+// j in order, samples at or past nint counted as absent.  The phase-split
+// layout makes the dedispersion gather of consecutive t' read consecutive
+// addresses for every dt: sample t' dt + delta lives at phase delta mod dt,
+// index t' + delta div dt.
+template <bool FP16>
+__global__ void __launch_bounds__(256) k_resample(const void* __restrict__ S, void* __restrict__ out, int nrows,
+                                                  int nint, int nint_pad, int dt, int lp) {
+  const size_t pitch = (size_t)dt * lp;
+  const size_t total = (size_t)nrows * pitch;
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < total; o += (size_t)gridDim.x * blockDim.x) {
+    const size_t row = o / pitch;
+    const int rem = (int)(o - row * pitch);
+    const int p = rem / lp;
+    const int i = rem - p * lp;
+    const int t = i * dt + p;
+    float2 a = make_float2(0.f, 0.f);
+    const size_t base = row * (size_t)nint_pad;
+    for (int j = 0; j < dt; ++j) {
+      if (t + j < nint) {
+        float2 v;
+        if (FP16)
+          v = __half22float2(reinterpret_cast<const __half2*>(S)[base + t + j]);
+        else
+          v = reinterpret_cast<const float2*>(S)[base + t + j];
+        a.x += v.x;
+        a.y += v.y;
+      }
+    }
+    if (FP16)
+      reinterpret_cast<__half2*>(out)[o] = __floats2half2_rn(a.x, a.y);
+    else
+      reinterpret_cast<float2*>(out)[o] = a;
+  }
+}
+
+cudaError_t launch_resample(const SegmentGeom& g, const void* S, void* Sdt, int dt, int lp, cudaStream_t st) {
+  const int nrows = g.nbl * g.nchan;
+  const size_t total = (size_t)nrows * dt * lp;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+  if (g.fp16)
+    k_resample<true><<<blocks, 256, 0, st>>>(S, Sdt, nrows, g.nint, g.nint_pad, dt, lp);
+  else
+    k_resample<false><<<blocks, 256, 0, st>>>(S, Sdt, nrows, g.nint, g.nint_pad, dt, lp);
   return cudaGetLastError();
 }
 

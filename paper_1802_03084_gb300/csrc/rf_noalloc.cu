@@ -96,7 +96,7 @@ rf_status ensure_setup(int dev, DeviceSetup** out) {
 // XA transforms of a CTA takes one column u < N/2, applies the
 // (-1)^(u + v) phase-centre shift and inverse-FFTs it along v.
 template <int N>
-__global__ void __launch_bounds__(ImgCfg<N>::THREADS_A)
+__global__ void __launch_bounds__(ImgCfg<N>::T * ImgCfg<N>::XA)
     k_colfft_dense(const float2* __restrict__ grid, float2* __restrict__ T, const float2* __restrict__ tw) {
   using K = ImgCfg<N>;
   constexpr int W = N / 2 + 1;
@@ -104,7 +104,8 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_A)
   extern __shared__ float2 sm[];
   const int tid = threadIdx.x;
   const int col0 = blockIdx.x * K::XA;
-  for (int i = tid; i < N * K::XA; i += K::THREADS_A) {
+  constexpr int THREADS = K::T * K::XA;
+  for (int i = tid; i < N * K::XA; i += THREADS) {
     const int c = i % K::XA;
     const int v = i / K::XA;
     const int u = col0 + c;
@@ -113,19 +114,19 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_A)
       h = __ldg(grid + (size_t)v * W + u);
       if ((u + v) & 1) h = make_float2(-h.x, -h.y);
     }
-    sm[c * K::STRIDE + pad16(v)] = h;
+    sm[c * K::STRIDE + padx(v)] = h;
   }
   __syncthreads();
   const int xf = tid / K::T;
   const int t = tid - xf * K::T;
-  float2 v[16];
-  fft_inverse_to_regs<N>(v, sm + xf * K::STRIDE, tw, t);
+  float2 v[K::E];
+  fft_inverse_to_regs<N>(v, sm + xf * K::STRIDE, tw, t, xf);
   const int u = col0 + xf;
   if (u < NC) {
     float2* dst = T + (size_t)u * N;
     constexpr int LP = FftShape<N>::LAST_P;
 #pragma unroll
-    for (int m = 0; m < 16 / LP; ++m)
+    for (int m = 0; m < K::E / LP; ++m)
 #pragma unroll
       for (int q = 0; q < LP; ++q) dst[fft_out_index<N>(t, m, q)] = v[m * LP + dft_perm<LP>(q)];
   }
@@ -173,13 +174,13 @@ cudaError_t run_noalloc(const float2* grid, double weight, const DeviceSetup& d,
                         rf_image_stat* out) {
   using K = ImgCfg<N>;
   static const cudaError_t attr =
-      cudaFuncSetAttribute(k_colfft_dense<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM_A);
+      cudaFuncSetAttribute(k_colfft_dense<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM_A_FIXED);
   if (attr != cudaSuccess) return attr;
   float2* T = reinterpret_cast<float2*>(d.scratch);
   StatPartial* partials = reinterpret_cast<StatPartial*>(d.scratch + kTBytes);
   const float2* tw = d.twiddle + twiddle_offset(N);
   constexpr int NC = N / 2;
-  k_colfft_dense<N><<<(NC + K::XA - 1) / K::XA, K::THREADS_A, K::SMEM_A, st>>>(grid, T, tw);
+  k_colfft_dense<N><<<(NC + K::XA - 1) / K::XA, K::T * K::XA, K::SMEM_A_FIXED, st>>>(grid, T, tw);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   SegmentGeom g{};
