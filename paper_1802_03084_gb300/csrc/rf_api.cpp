@@ -50,7 +50,8 @@ constexpr double kCLight = 299792458.0;   // m/s
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr uint32_t kKnownFlags = RF_STORE_FP16 | RF_EDGE_PARTIAL | RF_HOST_ONLY;
 constexpr size_t kStageBytes = 256ull << 20;   // host->device chunk of raw visibilities
-constexpr size_t kTBudgetBytes = 1024ull << 20;  // column-FFT scratch per wave
+constexpr size_t kTBudgetBytes = 4096ull << 20;  // column-FFT scratch per wave
+constexpr int kRangeEntries = 64;                // target entries per gridding warp
 
 // Round half away from zero: sign(x) floor(|x| + 1/2).
 inline double round_half_away(double x) { return x >= 0.0 ? std::floor(x + 0.5) : -std::floor(-x + 0.5); }
@@ -87,9 +88,11 @@ struct BusyGuard {
   }
 };
 
-enum KernelKind { K_H2D = 0, K_INGEST, K_RESAMPLE, K_WEIGHTS, K_GRID_COLFFT, K_ROWFFT_STATS, K_FINALIZE, K_NKINDS };
-const char* const kKindNames[K_NKINDS] = {"h2d_copy", "ingest", "resample", "weights", "grid_colfft",
-                                           "rowfft_stats", "finalize"};
+enum KernelKind {
+  K_H2D = 0, K_INGEST, K_RESAMPLE, K_WEIGHTS, K_GRID_CELLS, K_GRID_COLFFT, K_ROWFFT_STATS, K_FINALIZE, K_NKINDS
+};
+const char* const kKindNames[K_NKINDS] = {"h2d_copy", "ingest",      "resample",     "weights",
+                                           "grid_cells", "grid_colfft", "rowfft_stats", "finalize"};
 
 // Event-pair timing of every launch a plan issues while profiling is on.
 struct Profiler {
@@ -172,7 +175,8 @@ struct rf_plan {
   std::vector<int32_t> max_delay;  // [ndm]
   std::vector<int32_t> iu, iv;     // [nbl][nchan]
   std::vector<uint8_t> ongrid;     // [nbl][nchan]
-  std::vector<int32_t> col_ent_ptr, col_warp_ptr, col_cell_ptr, cell_row;
+  std::vector<int32_t> col_ent_ptr, col_cell_ptr, cell_row;
+  std::vector<int2> ranges;
   std::vector<GridEntry> ent;
   int n_cells = 0, max_cells = 0;
   std::vector<int32_t> ongrid_chan;
@@ -206,6 +210,8 @@ struct rf_plan {
   std::vector<int4> img_info;
   std::vector<Group> groups;
   std::vector<Wave> waves;
+  int gslots_max = 0;           // groups per wave (cell buffer capacity)
+  float2* d_cellbuf = nullptr;
 
   std::atomic<int> busy{0};
   Profiler prof;
@@ -414,7 +420,7 @@ rf_status build_tables(rf_plan* p) {
         ++local;
       }
       const int c = es[i].bc / nbl;
-      p->ent.push_back({es[i].bc, (c << 2) | es[i].flags, es[i].row, local});
+      p->ent.push_back({es[i].bc, (c << 2) | es[i].flags, es[i].row, p->n_cells - 1});
       ++i;
     }
     p->max_cells = std::max(p->max_cells, local + 1);
@@ -422,26 +428,19 @@ rf_status build_tables(rf_plan* p) {
   p->col_ent_ptr[p->ncol] = (int)p->ent.size();
   p->col_cell_ptr[p->ncol] = p->n_cells;
   cell_start.push_back((int)p->ent.size());
-  // Split each column's entries into WPC ranges that start on cell boundaries
-  // and hold about the same number of entries.
-  const int wpc = p->shape.warps_per_col;
-  p->col_warp_ptr.assign((size_t)p->ncol * (wpc + 1), 0);
-  size_t ci = 0;  // index into cell_start
-  for (int col = 0; col < p->ncol; ++col) {
-    const int eb = p->col_ent_ptr[col], ee = p->col_ent_ptr[col + 1];
-    int32_t* w = &p->col_warp_ptr[(size_t)col * (wpc + 1)];
-    while (ci < cell_start.size() && cell_start[ci] < eb) ++ci;
-    w[0] = eb;
-    size_t cj = ci;
-    for (int k = 1; k < wpc; ++k) {
-      const long target = eb + (long)(ee - eb) * k / wpc;
-      while (cj < cell_start.size() && cell_start[cj] < target) ++cj;
-      int b2 = (cj < cell_start.size()) ? std::min(cell_start[cj], ee) : ee;
-      w[k] = std::max(b2, w[k - 1]);
+  // Cell-aligned entry ranges of about kRangeEntries entries (a range holds
+  // whole cells; a cell with more entries is a range of its own).
+  p->ranges.clear();
+  {
+    size_t ci = 0;
+    while (ci + 1 < cell_start.size()) {
+      const int eb = cell_start[ci];
+      size_t cj = ci + 1;
+      while (cj + 1 < cell_start.size() && cell_start[cj + 1] - eb <= kRangeEntries) ++cj;
+      p->ranges.push_back(make_int2(eb, cell_start[cj]));
+      ci = cj;
     }
-    w[wpc] = ee;
   }
-  if (!rf::image_kernel_shape(N, &p->shape)) return fail(RF_ERR_INVALID_ARG, "npix %d has no kernel", N);
   return RF_OK;
 }
 
@@ -468,7 +467,7 @@ void build_lists(rf_plan* p, int nint) {
   Wave w{0, 0, 0, 0};
   for (int gi = 0; gi < (int)p->groups.size(); ++gi) {
     const Group& g = p->groups[gi];
-    if (g.img0 + g.nimg - w.img_begin > p->slots_max) {
+    if (g.img0 + g.nimg - w.img_begin > p->slots_max || gi - w.g_begin >= p->gslots_max) {
       w.g_end = gi;
       w.img_end = g.img0;
       p->waves.push_back(w);
@@ -487,7 +486,7 @@ rf_status alloc_wave_scratch(rf_plan* p, int slots) {
   const int B = p->shape.images_per_group;
   slots = std::max(std::min(slots, 32768), B);
   const size_t per_slot = (size_t)p->ncol * p->npix;
-  const int nrb = p->npix / p->shape.rows_per_cta;
+  const int nrb = p->shape.partials_per_image;
   if (p->d_T) {
     p->device_bytes -= (uint64_t)p->slots_max * per_slot * sizeof(float2);
     p->dfree(p->d_T);
@@ -498,11 +497,18 @@ rf_status alloc_wave_scratch(rf_plan* p, int slots) {
     p->dfree(p->d_partials);
     p->d_partials = nullptr;
   }
+  if (p->d_cellbuf) {
+    p->device_bytes -= (uint64_t)p->gslots_max * p->n_cells * 32 * sizeof(float2);
+    p->dfree(p->d_cellbuf);
+    p->d_cellbuf = nullptr;
+  }
   p->slots_max = slots;
+  p->gslots_max = std::max(2 * ((slots + B - 1) / B), 1);
   p->cached_nint = -1;
   rf_status s;
   if ((s = p->dalloc(&p->d_T, (size_t)slots * per_slot)) != RF_OK) return s;
   if ((s = p->dalloc(&p->d_partials, (size_t)slots * nrb)) != RF_OK) return s;
+  if ((s = p->dalloc(&p->d_cellbuf, (size_t)p->gslots_max * std::max(p->n_cells, 1) * 32)) != RF_OK) return s;
   return RF_OK;
 }
 
@@ -517,14 +523,14 @@ rf_status alloc_device(rf_plan* p) {
     *dst = d;
     return RF_OK;
   };
-  int32_t *d_delays = nullptr, *d_dt = nullptr, *d_cwp = nullptr, *d_ogc = nullptr, *d_ccp = nullptr,
-          *d_crow = nullptr;
+  int32_t *d_delays = nullptr, *d_dt = nullptr, *d_ogc = nullptr, *d_ccp = nullptr, *d_crow = nullptr;
+  int2* d_ranges = nullptr;
   GridEntry* d_ent = nullptr;
   rf_status s;
   if ((s = up(&d_delays, p->delays)) != RF_OK) return s;
   std::vector<int32_t> dtv(p->dt.begin(), p->dt.end());
   if ((s = up(&d_dt, dtv)) != RF_OK) return s;
-  if ((s = up(&d_cwp, p->col_warp_ptr)) != RF_OK) return s;
+  if ((s = up(&d_ranges, p->ranges)) != RF_OK) return s;
   if ((s = up(&d_ccp, p->col_cell_ptr)) != RF_OK) return s;
   if ((s = up(&d_crow, p->cell_row)) != RF_OK) return s;
   if ((s = up(&d_ent, p->ent)) != RF_OK) return s;
@@ -538,7 +544,7 @@ rf_status alloc_device(rf_plan* p) {
   if ((s = up(&d_tw, tw)) != RF_OK) return s;
   p->tb.delays = d_delays;
   p->tb.dt_list = d_dt;
-  p->tb.col_warp_ptr = d_cwp;
+  p->tb.ranges = d_ranges;
   p->tb.col_cell_ptr = d_ccp;
   p->tb.cell_row = d_crow;
   p->tb.ent = d_ent;
@@ -616,6 +622,8 @@ SegmentGeom geom(const rf_plan* p, int nint) {
   g.ncol = p->ncol;
   g.ndm = p->ndm;
   g.max_cells = p->max_cells;
+  g.ncells = p->n_cells;
+  g.nranges = (int)p->ranges.size();
   g.fp16 = (p->flags & RF_STORE_FP16) != 0;
   return g;
 }
@@ -671,8 +679,10 @@ rf_status run_waves(rf_plan* p, int nint, const std::vector<Wave>& waves, int ni
   for (const Wave& w : waves) {
     const int ng = w.g_end - w.g_begin;
     const int ni = w.img_end - w.img_begin;
+    RF_TIMED(p->prof, K_GRID_CELLS, st,
+             rf::launch_grid_cells(g, p->tb, p->d_groups, w.g_begin, ng, p->d_cellbuf, st));
     RF_TIMED(p->prof, K_GRID_COLFFT, st,
-             rf::launch_grid_colfft(g, p->tb, p->d_S, p->d_groups, w.g_begin, ng, w.img_begin, p->d_T, st));
+             rf::launch_colfft(g, p->tb, p->d_groups, w.g_begin, ng, w.img_begin, p->d_cellbuf, p->d_T, st));
     float* im = d_images ? d_images + (size_t)w.img_begin * p->npix * p->npix : nullptr;
     RF_TIMED(p->prof, K_ROWFFT_STATS, st,
              rf::launch_rowfft_stats(g, p->tb, p->d_T, ni, w.img_begin, p->d_weight, p->d_partials, im, st));
@@ -902,8 +912,9 @@ rf_status rf_render_images(rf_plan* p, const void* vis, int32_t nint, void* stre
   RF_CUDA(cudaMemcpyAsync(p->d_img_info, info.data(), n * sizeof(int4), cudaMemcpyHostToDevice, st));
   RF_CUDA(cudaMemcpyAsync(p->d_groups, grp.data(), n * sizeof(Group), cudaMemcpyHostToDevice, st));
   std::vector<Wave> waves;
-  for (int k = 0; k < n; k += p->slots_max) {
-    const int e = std::min(n, k + p->slots_max);
+  const int per_wave = std::min(p->slots_max, p->gslots_max);  // single-image groups
+  for (int k = 0; k < n; k += per_wave) {
+    const int e = std::min(n, k + per_wave);
     waves.push_back(Wave{k, e, k, e});
   }
   const size_t npx = (size_t)p->npix * p->npix;

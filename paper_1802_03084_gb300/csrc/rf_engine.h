@@ -13,8 +13,8 @@ constexpr int ENT_NEG = 2;   // checkerboard sign (-1)^(iu + iv) is -1
 
 // One contribution of a (baseline, channel) visibility to a half-plane cell.
 // bc = row c * nbl + b of the Stokes-I time series; cflags = (c << 2) | flags;
-// row = the cell's v index iv mod N in its column; cell = the cell's index
-// within its column (cells numbered in row order).
+// row = the cell's v index iv mod N in its column; cell = the cell's global
+// index (cells numbered by column, then row).
 struct GridEntry {
   int32_t bc;
   int32_t cflags;
@@ -26,7 +26,7 @@ struct GridEntry {
 struct DevTables {
   const int32_t* delays;        // [ndm][nchan] integrations
   const int32_t* dt_list;       // [ndt]
-  const int32_t* col_warp_ptr;  // [ncol][WPC + 1] entry ranges of the warps gridding a column
+  const int2* ranges;           // [nranges] cell-aligned entry ranges, one per gridding warp
   const int32_t* col_cell_ptr;  // [ncol + 1] first cell of each column
   const int32_t* cell_row;      // [ncells] row (iv mod N) of each cell
   const GridEntry* ent;         // [nent] sorted by (column, row)
@@ -83,6 +83,8 @@ struct SegmentGeom {
   int ncol;       // half-plane columns imaged: 0 .. iu_max
   int ndm;
   int max_cells;  // largest number of occupied cells in one column
+  int ncells;     // occupied cells of the half plane
+  int nranges;    // gridding ranges
   bool fp16;      // Stokes-I stored as half2
 };
 
@@ -104,10 +106,15 @@ cudaError_t launch_resample(const SegmentGeom& g, const void* S, void* Sdt, int 
 cudaError_t launch_weights(const int4* img_info, int nimg, bool partial, const SegmentGeom& g,
                            const DevTables& tb, double n_on, double* weight, cudaStream_t st);
 
-// Gridding + column FFT (pass A) of groups [g_begin, g_begin + ngroups).
-// Writes Tbuf[slot][col][y], slot = image index - img_base.
-cudaError_t launch_grid_colfft(const SegmentGeom& g, const DevTables& tb, const void* S, const Group* groups,
-                               int g_begin, int ngroups, int img_base, float2* Tbuf, cudaStream_t st);
+// Gridding (pass A1) of groups [g_begin, g_begin + ngroups): the cell sums
+// of every image, cellbuf[group - g_begin][cell][32 images].
+cudaError_t launch_grid_cells(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin,
+                              int ngroups, float2* cellbuf, cudaStream_t st);
+
+// Column FFTs (pass A2) of the same groups from cellbuf; writes
+// Tbuf[slot][col][y], slot = image index - img_base.
+cudaError_t launch_colfft(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin,
+                          int ngroups, int img_base, const float2* cellbuf, float2* Tbuf, cudaStream_t st);
 
 // Row C2R (pass B) + statistics of `nimg` images in slots [0, nimg) whose
 // first image index is img_base.  Optionally writes the scaled images.
@@ -129,6 +136,7 @@ struct ImageKernelShape {
   int smem_a;
   int warps_per_col;      // WPC: warps sharing one column's gridding (pass A)
   int rows_per_cta;       // RB (pass B)
+  int partials_per_image; // row-pair partials written by pass B (N / 2)
   int threads_b;
   int smem_b;
 };

@@ -182,7 +182,9 @@ __device__ __forceinline__ void fft_sync(int xf) {
   }
 }
 
-// Twiddles w^(s r), r = 1 .. P-1, from the table entries w^(s 2^i).
+// Twiddles w^(s r), r = 1 .. P-1, from the table entries w^(s 2^i): one
+// complex product per non-power-of-two r (at most four roundings from the
+// table); fewer loads and registers than reading every power.
 template <int N, int P>
 __device__ __forceinline__ void twiddle_mul(float2* v, const float2* __restrict__ tw, int s) {
   float2 W[P];

@@ -76,104 +76,38 @@ __device__ __forceinline__ float2 load_sample<true>(const void* __restrict__ S, 
   return __half22float2(h);
 }
 
-// Pass A: for a group of up to B = 32 consecutive output integrations
-// t0 .. t0+31 of trial (d, s) and one half-plane column u, build the column
-// of the checkerboarded half-plane grid and inverse-FFT it along v.
-//   R[b,c](t') = sum_{j < dt} S[b,c][t' dt + j + delta[d][c]]    (dedisperse+resample)
-//   H[iv][u] += (-1)^(u+iv) R   or   conj(R) for folded entries  (gridding)
-// Gridding: lane k of every warp is image t0 + k, so one load instruction
-// reads 32 consecutive time samples of one (b, c).  The column's entries are
-// sorted by cell and split on the host into 8 cell-aligned ranges, one per
-// warp; a warp walks its range entry by entry (metadata broadcast by
-// shuffle, samples of 8 entries in flight), summing each cell in a register
-// in a fixed order, and stores the cell's 32 values in a compact shared
-// array.  Column FFTs: each transform zeroes its buffer, scatters one
-// image's cells and runs the FFT; transforms synchronise only among their
-// own threads.
-template <int N, bool FP16>
-__global__ void __launch_bounds__(ImgCfg<N>::THREADS_A)
-    k_grid_colfft(SegmentGeom g, DevTables tb, const void* __restrict__ S, const Group* __restrict__ groups,
-                  int g_begin, int img_base, float2* __restrict__ Tbuf) {
+// Pass A2: the column FFTs of one group (up to 32 consecutive t' of a
+// trial) and one half-plane column u.  The column's cell sums for the
+// group's images (cellbuf row per cell, 32 images) are copied to shared
+// memory with cp.async (16-byte chunks XOR-swizzled by cell); then, XA
+// images at a time, each transform zeroes its buffer, scatters its image's
+// cells to rows iv mod N and inverse-FFTs the column along v.  Transforms
+// synchronise only among their own threads.
+template <int N>
+__global__ void __launch_bounds__(ImgCfg<N>::THREADS_A, 2)
+    k_colfft(SegmentGeom g, DevTables tb, const Group* __restrict__ groups, int g_begin, int img_base,
+             const float2* __restrict__ cellbuf, float2* __restrict__ Tbuf) {
   using K = ImgCfg<N>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* fbuf = reinterpret_cast<float2*>(smraw);                              // [XA][STRIDE]
-  float2* cellval = fbuf + K::XA * K::STRIDE;                                    // [max_cells][33]
-  int* crow = reinterpret_cast<int*>(cellval + (size_t)g.max_cells * K::CELL_PITCH);  // [max_cells]
-  int* sdel = crow + g.max_cells;                                                // [nchan]
+  float2* fbuf = reinterpret_cast<float2*>(smraw);                     // [XA][STRIDE]
+  float2* cellv = fbuf + K::XA * K::STRIDE;                             // [max_cells][32], swizzled
+  int* crow = reinterpret_cast<int*>(cellv + (size_t)g.max_cells * 32);  // [max_cells]
   const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const int warp = tid >> 5;
   const Group gr = groups[g_begin + blockIdx.x];
   const int col = blockIdx.y;
   const int cell0 = tb.col_cell_ptr[col];
   const int ncells = tb.col_cell_ptr[col + 1] - cell0;
+  const float2* __restrict__ src = cellbuf + ((size_t)blockIdx.x * g.ncells + cell0) * 32;
+  for (int i = tid; i < ncells * 16; i += K::THREADS_A) {
+    const int c = i >> 4;
+    const int j = i & 15;
+    cp_async16(cellv + c * 32 + 2 * (j ^ (c & 15)), src + c * 32 + 2 * j);
+  }
+  cp_async_commit();
   for (int c = tid; c < ncells; c += K::THREADS_A) crow[c] = tb.cell_row[cell0 + c];
-  {
-    const int* __restrict__ dl = tb.delays + (size_t)gr.d * g.nchan;
-    for (int c = tid; c < g.nchan; c += K::THREADS_A) sdel[c] = dl[c];
-  }
-  const int* cwp = tb.col_warp_ptr + (size_t)col * (K::WPC + 1) + warp;
-  const int ebeg = cwp[0];
-  const int eend = cwp[1];
-  GridEntry nxt = {0, 0, 0, -1};
-  if (ebeg + lane < eend) nxt = tb.ent[ebeg + lane];
+  cp_async_wait_all();
   __syncthreads();
 
-  // ---- gridding (lanes = images).  Image t' = t0 + lane reads sample
-  // t' dt + delta of the dt-resampled series: phase delta mod dt, index
-  // t' + delta div dt.
-  {
-    const int dt = tb.dt_list[gr.s];
-    const int lp = tb.sdt_lp[gr.s];
-    const unsigned char* __restrict__ Sd = reinterpret_cast<const unsigned char*>(tb.sdt_ptr[gr.s]);
-    const size_t rowpitch = (size_t)dt * lp;
-    const bool active = lane < gr.nimg;
-    const int tq = gr.t0 + lane;
-    const int lim = g.nint - tq * dt;  // the image has a sample iff delta < lim
-    float2 acc = make_float2(0.f, 0.f);
-    int cur = -1;
-    for (int base = ebeg; base < eend; base += 32) {
-      const GridEntry my = nxt;
-      const bool mine = base + lane < eend;
-      if (base + 32 + lane < eend) nxt = tb.ent[base + 32 + lane];
-      const int mydel = mine ? sdel[my.cflags >> 2] : 0;
-      const int mypart = (mydel % dt) * lp + mydel / dt;  // phase offset + index shift
-      const int n = min(32, eend - base);
-      for (int i0 = 0; i0 < n; i0 += 16) {
-        float2 a[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int i = (i0 + q) & 31;
-          const int bc = __shfl_sync(0xffffffffu, my.bc, i);
-          const int del = __shfl_sync(0xffffffffu, mydel, i);
-          const int part = __shfl_sync(0xffffffffu, mypart, i);
-          a[q] = make_float2(0.f, 0.f);
-          if (active && i0 + q < n && del < lim) a[q] = load_sample<FP16>(Sd, (size_t)bc * rowpitch + part + tq);
-        }
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int i = (i0 + q) & 31;
-          const int cf = __shfl_sync(0xffffffffu, my.cflags, i);
-          const int cell = __shfl_sync(0xffffffffu, my.cell, i);
-          if (i0 + q < n) {
-            if (cell != cur) {
-              if (cur >= 0) cellval[cur * K::CELL_PITCH + lane] = acc;
-              acc = make_float2(0.f, 0.f);
-              cur = cell;
-            }
-            const float sy = (cf & ENT_CONJ) ? -1.f : 1.f;
-            const float sg = (cf & ENT_NEG) ? -1.f : 1.f;
-            acc.x += sg * a[q].x;
-            acc.y += sg * sy * a[q].y;
-          }
-        }
-      }
-    }
-    if (cur >= 0) cellval[cur * K::CELL_PITCH + lane] = acc;
-  }
-  __syncthreads();
-
-  // ---- column FFTs, XA images per round
   const int xf = tid / K::T;
   const int t = tid - xf * K::T;
   if (xf < K::XA) {
@@ -183,8 +117,11 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_A)
       const int k = rd * K::XA + xf;
       for (int i = t; i < K::STRIDE; i += K::T) buf[i] = make_float2(0.f, 0.f);
       fft_sync<K::T>(xf);
-      if (k < gr.nimg)
-        for (int c = t; c < ncells; c += K::T) buf[padx(crow[c])] = cellval[c * K::CELL_PITCH + k];
+      if (k < gr.nimg) {
+        const int kc = k >> 1;
+        const int ko = k & 1;
+        for (int c = t; c < ncells; c += K::T) buf[padx(crow[c])] = cellv[c * 32 + 2 * (kc ^ (c & 15)) + ko];
+      }
       fft_sync<K::T>(xf);
       float2 v[K::E];
       fft_inverse_to_regs<N>(v, buf, tb.twiddle, t, xf);
@@ -214,10 +151,10 @@ __device__ __forceinline__ void max_merge(float& m, int& i, float m2, int i2) {
 // tile T[slot][u][y0 .. y0+RB) of the next item is copied to shared memory
 // with cp.async (16-byte chunks, XOR-swizzled per row so the strided reads
 // are free of bank conflicts) while the current item is transformed.  Each
-// item writes one StatPartial: pixel sum and sum of squares over its RB rows
-// (FP32: per thread, pairwise within warps, then across the block's warps;
-// the items of an image are added in FP64 by the finalisation) and the max
-// pixel with its lowest index.
+// row pair writes one StatPartial: pixel sum and sum of squares of its two
+// rows (FP32 per thread and pairwise across the transform's threads; the
+// N/2 partials of an image are added in FP64 by the finalisation) and the
+// max pixel with its lowest index.
 template <int N>
 __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     k_rowfft_stats(SegmentGeom g, DevTables tb, const float2* __restrict__ Tbuf, int nimg, int img_base,
@@ -230,7 +167,7 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
   float4* tile = reinterpret_cast<float4*>(fbuf + K::XB * K::STRIDE);  // [ncol][CH]
   __shared__ float w_sum[32], w_sq[32];
   __shared__ float w_max[32];
-  __shared__ int s_idx;
+  __shared__ int w_idx[32];
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int wid = tid >> 5;
@@ -288,6 +225,9 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     }
     fft_inverse_from_regs<N>(v, fbuf + xf * K::STRIDE, tb.twiddle, t, xf);
 
+    // per-row-pair statistics: pixel sum and sum of squares (FP32 per
+    // thread, then a pairwise warp reduction), the max pixel and its lowest
+    // index; one StatPartial per row pair, no block-wide barrier
     const int y = y0 + 2 * xf;
     float lmax = -FLT_MAX;
     float lsum = 0.f, lsq = 0.f;
@@ -314,10 +254,10 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
         }
       }
     }
-    // FP32 warp sums and max, FP64 across warps; the index of the block
-    // maximum is searched only by the threads that hold it.
-    constexpr int WL = K::THREADS_B < 32 ? K::THREADS_B : 32;
-    constexpr unsigned MASK = WL == 32 ? 0xffffffffu : ((1u << WL) - 1u);
+    // reduce over the transform's T threads (a warp, a part of one, or
+    // several warps joined through shared memory)
+    constexpr int WL = K::T < 32 ? K::T : 32;
+    constexpr unsigned MASK = 0xffffffffu;
     float wmax = lmax;
 #pragma unroll
     for (int off = WL / 2; off > 0; off >>= 1) {
@@ -325,44 +265,58 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
       lsq += __shfl_xor_sync(MASK, lsq, off);
       wmax = fmaxf(wmax, __shfl_xor_sync(MASK, wmax, off));
     }
-    if (lane == 0) {
-      w_sum[wid] = lsum;
-      w_sq[wid] = lsq;
-      w_max[wid] = wmax;
-    }
-    if (tid == 0) s_idx = INT_MAX;
-    __syncthreads();
-    float bmax = w_max[0];
-#pragma unroll
-    for (int w = 1; w < NWB; ++w) bmax = fmaxf(bmax, w_max[w]);
-    if (lmax == bmax) {
-      int best = INT_MAX;
+    int best = INT_MAX;
+    if (lmax == wmax) {
 #pragma unroll
       for (int m = 0; m < K::E / LP; ++m) {
 #pragma unroll
         for (int q = 0; q < LP; ++q) {
           const float2 z = v[m * LP + dft_perm<LP>(q)];
           const int o = fft_out_index<N>(t, m, q);
-          if (z.x == bmax) best = min(best, y * N + o);
-          if (z.y == bmax) best = min(best, (y + 1) * N + o);
+          if (z.x == wmax) best = min(best, y * N + o);
+          if (z.y == wmax) best = min(best, (y + 1) * N + o);
         }
       }
-      atomicMin(&s_idx, best);
     }
-    __syncthreads();
-    if (tid == 0) {
-      float s = 0.f, q2 = 0.f;
-      for (int w = 0; w < NWB; ++w) {
-        s += w_sum[w];
-        q2 += w_sq[w];
+#pragma unroll
+    for (int off = WL / 2; off > 0; off >>= 1) best = min(best, __shfl_xor_sync(MASK, best, off));
+    if (K::T > 32) {
+      // wide transforms: combine the warps of one transform in shared memory
+      constexpr int WPT = K::T / 32;
+      const int wi = t >> 5;
+      if (lane == 0) {
+        w_sum[wid] = lsum;
+        w_sq[wid] = lsq;
+        w_max[wid] = wmax;
+        w_idx[wid] = best;
       }
+      fft_sync<K::T>(xf);
+      if (t == 0) {
+        const int w0 = wid - wi;
+        float s2 = 0.f, q2 = 0.f, mx = -FLT_MAX;
+        int mi = INT_MAX;
+        for (int w = 0; w < WPT; ++w) {
+          s2 += w_sum[w0 + w];
+          q2 += w_sq[w0 + w];
+          max_merge(mx, mi, w_max[w0 + w], w_idx[w0 + w]);
+        }
+        StatPartial sp;
+        sp.sum = (double)s2;
+        sp.sumsq = (double)q2;
+        sp.max = mx;
+        sp.idx = mi;
+        sp.pad[0] = sp.pad[1] = 0;
+        partials[(size_t)slot * (N / 2) + (y0 >> 1) + xf] = sp;
+      }
+      fft_sync<K::T>(xf);
+    } else if (t == 0) {
       StatPartial sp;
-      sp.sum = (double)s;
-      sp.sumsq = (double)q2;
-      sp.max = bmax;
-      sp.idx = s_idx;
+      sp.sum = (double)lsum;
+      sp.sumsq = (double)lsq;
+      sp.max = wmax;
+      sp.idx = best;
       sp.pad[0] = sp.pad[1] = 0;
-      partials[(size_t)item] = sp;
+      partials[(size_t)slot * (N / 2) + (y0 >> 1) + xf] = sp;
     }
   }
 }
@@ -377,20 +331,20 @@ inline int sm_count() {
   return n;
 }
 
-template <int N, bool FP16>
-cudaError_t run_grid_colfft(const SegmentGeom& g, const DevTables& tb, const void* S, const Group* groups,
-                            int g_begin, int ngroups, int img_base, float2* Tbuf, cudaStream_t st) {
+template <int N>
+cudaError_t run_colfft(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin, int ngroups,
+                       int img_base, const float2* cellbuf, float2* Tbuf, cudaStream_t st) {
   using K = ImgCfg<N>;
-  const int smem = K::SMEM_A_FIXED + g.max_cells * (K::CELL_PITCH * 8 + 4) + g.nchan * 4;
+  const int smem = K::SMEM_A_FIXED + g.max_cells * (32 * 8 + 4);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_grid_colfft<N, FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_colfft<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_grid_colfft<N, FP16>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  e = cudaFuncSetAttribute(k_colfft<N>, cudaFuncAttributePreferredSharedMemoryCarveout,
                            cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   if (ngroups <= 0) return cudaSuccess;
   dim3 grid(ngroups, g.ncol);
-  k_grid_colfft<N, FP16><<<grid, K::THREADS_A, smem, st>>>(g, tb, S, groups, g_begin, img_base, Tbuf);
+  k_colfft<N><<<grid, K::THREADS_A, smem, st>>>(g, tb, groups, g_begin, img_base, cellbuf, Tbuf);
   return cudaGetLastError();
 }
 
@@ -423,17 +377,16 @@ void fill_shape(ImageKernelShape* o) {
   o->cols_per_cta = 1;
   o->threads_a = K::THREADS_A;
   o->smem_a = K::SMEM_A_FIXED;
-  o->warps_per_col = K::WPC;
+  o->warps_per_col = 0;
   o->rows_per_cta = K::RB;
+  o->partials_per_image = N / 2;
   o->threads_b = K::THREADS_B;
   o->smem_b = K::SMEM_B_FIXED;
 }
 
 #define RF_INSTANTIATE_IMAGE(N)                                                                              \
-  template cudaError_t run_grid_colfft<N, false>(const SegmentGeom&, const DevTables&, const void*,          \
-                                                 const Group*, int, int, int, float2*, cudaStream_t);       \
-  template cudaError_t run_grid_colfft<N, true>(const SegmentGeom&, const DevTables&, const void*,           \
-                                                const Group*, int, int, int, float2*, cudaStream_t);        \
+  template cudaError_t run_colfft<N>(const SegmentGeom&, const DevTables&, const Group*, int, int, int,      \
+                                     const float2*, float2*, cudaStream_t);                                 \
   template cudaError_t run_rowfft_stats<N>(const SegmentGeom&, const DevTables&, const float2*, int, int,    \
                                            const double*, StatPartial*, float*, cudaStream_t);              \
   template void fill_shape<N>(ImageKernelShape*);

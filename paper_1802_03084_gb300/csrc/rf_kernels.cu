@@ -128,6 +128,104 @@ cudaError_t launch_resample(const SegmentGeom& g, const void* S, void* Sdt, int 
   return cudaGetLastError();
 }
 
+// --------------------------------------------------------------- gridding --
+// Dedispersion + resampling + nearest-neighbour gridding (Sec. 2.2, 3.1) of
+// a group of up to 32 consecutive output integrations t0 .. t0+31 of one
+// (DM, dt) trial.  Lane k of every warp is image t0 + k: it reads sample
+// t' dt + delta[d][c] of the dt-resampled series (phase delta mod dt, index
+// t' + delta div dt), so one load instruction reads 32 consecutive samples.
+// Each warp walks one host-made, cell-aligned range of gridding entries
+// (sorted by cell), entry metadata broadcast by shuffle and 16 sample loads
+// in flight per lane, sums every cell in registers in a fixed order
+//   H[cell] = sum_entries (-1)^(iu+iv) R  (or conj R for folded entries)
+// and writes the cell's 32 values to cellbuf[group][cell][k] (one 256-byte
+// row).  No atomics: the grid is bitwise reproducible.
+template <bool FP16>
+__device__ __forceinline__ float2 load_s(const unsigned char* __restrict__ S, size_t i) {
+  if (FP16) return __half22float2(__ldg(reinterpret_cast<const __half2*>(S) + i));
+  return __ldg(reinterpret_cast<const float2*>(S) + i);
+}
+
+template <bool FP16>
+__global__ void __launch_bounds__(256, 3) k_grid_cells(SegmentGeom g, DevTables tb, const Group* __restrict__ groups,
+                                                    int g_begin, float2* __restrict__ cellbuf) {
+  extern __shared__ int sdel[];  // [nchan] delays of this group's DM
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const Group gr = groups[g_begin + blockIdx.x];
+  {
+    const int* __restrict__ dl = tb.delays + (size_t)gr.d * g.nchan;
+    for (int c = tid; c < g.nchan; c += blockDim.x) sdel[c] = dl[c];
+  }
+  __syncthreads();
+  const int r = blockIdx.y * (blockDim.x >> 5) + (tid >> 5);
+  if (r >= g.nranges) return;
+  const int2 rg = tb.ranges[r];
+  const int ebeg = rg.x, eend = rg.y;
+  const int dt = tb.dt_list[gr.s];
+  const int lp = tb.sdt_lp[gr.s];
+  const unsigned char* __restrict__ Sd = reinterpret_cast<const unsigned char*>(tb.sdt_ptr[gr.s]);
+  const size_t rowpitch = (size_t)dt * lp;
+  const bool active = lane < gr.nimg;
+  const int tq = gr.t0 + lane;
+  const int lim = g.nint - tq * dt;  // the image has a sample iff delta < lim
+  float2* __restrict__ out = cellbuf + (size_t)blockIdx.x * g.ncells * 32 + lane;
+  float2 acc = make_float2(0.f, 0.f);
+  int cur = -1;
+  GridEntry nxt = {0, 0, 0, -1};
+  if (ebeg + lane < eend) nxt = tb.ent[ebeg + lane];
+  for (int base = ebeg; base < eend; base += 32) {
+    const GridEntry my = nxt;
+    const bool mine = base + lane < eend;
+    if (base + 32 + lane < eend) nxt = tb.ent[base + 32 + lane];
+    const int mydel = mine ? sdel[my.cflags >> 2] : 0;
+    const int mypart = (mydel % dt) * lp + mydel / dt;
+    const int n = min(32, eend - base);
+    for (int i0 = 0; i0 < n; i0 += 16) {
+      float2 a[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int i = (i0 + q) & 31;
+        const int bc = __shfl_sync(0xffffffffu, my.bc, i);
+        const int del = __shfl_sync(0xffffffffu, mydel, i);
+        const int part = __shfl_sync(0xffffffffu, mypart, i);
+        a[q] = make_float2(0.f, 0.f);
+        if (active && i0 + q < n && del < lim) a[q] = load_s<FP16>(Sd, (size_t)bc * rowpitch + part + tq);
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int i = (i0 + q) & 31;
+        const int cf = __shfl_sync(0xffffffffu, my.cflags, i);
+        const int cell = __shfl_sync(0xffffffffu, my.cell, i);
+        if (i0 + q < n) {
+          if (cell != cur) {
+            if (cur >= 0) out[(size_t)cur * 32] = acc;
+            acc = make_float2(0.f, 0.f);
+            cur = cell;
+          }
+          const float sy = (cf & ENT_CONJ) ? -1.f : 1.f;
+          const float sg = (cf & ENT_NEG) ? -1.f : 1.f;
+          acc.x += sg * a[q].x;
+          acc.y += sg * sy * a[q].y;
+        }
+      }
+    }
+  }
+  if (cur >= 0) out[(size_t)cur * 32] = acc;
+}
+
+cudaError_t launch_grid_cells(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin,
+                              int ngroups, float2* cellbuf, cudaStream_t st) {
+  if (ngroups <= 0 || g.nranges <= 0) return cudaSuccess;
+  dim3 grid(ngroups, (g.nranges + 7) / 8);
+  const int smem = g.nchan * 4;
+  if (g.fp16)
+    k_grid_cells<true><<<grid, 256, smem, st>>>(g, tb, groups, g_begin, cellbuf);
+  else
+    k_grid_cells<false><<<grid, 256, smem, st>>>(g, tb, groups, g_begin, cellbuf);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- weights --
 // W = sum over on-grid (b, c) of the samples summed into R[b, c].  Under the
 // FULL edge rule every channel sums dt samples; under PARTIAL channel c sums
@@ -179,19 +277,31 @@ __global__ void k_finalize(int npix, int nrb, const StatPartial* __restrict__ pa
                            const int4* __restrict__ img_info, const double* __restrict__ weight, int nimg,
                            int img_base, double threshold, DevCand* __restrict__ cands, int* __restrict__ ncand,
                            int cand_cap, DevStat* __restrict__ stats) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per image; lanes stride over the row-block partials, then an
+  // xor-tree (fixed order) combines them
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (i >= nimg) return;
   const int img = img_base + i;
   const StatPartial* pp = partials + (size_t)i * nrb;
   double sum = 0.0, sq = 0.0;
   float mx = -FLT_MAX;
   int mi = INT_MAX;
-  for (int r = 0; r < nrb; ++r) {
+  for (int r = lane; r < nrb; r += 32) {
     const StatPartial p = pp[r];
     sum += p.sum;
     sq += p.sumsq;
     fmax_merge(mx, mi, p.max, p.idx);
   }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    sq += __shfl_xor_sync(0xffffffffu, sq, off);
+    const float om = __shfl_xor_sync(0xffffffffu, mx, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, mi, off);
+    fmax_merge(mx, mi, om, oi);
+  }
+  if (lane != 0) return;
   const double W = weight[img];
   const int4 info = img_info[img];
   DevStat ds;
@@ -247,16 +357,16 @@ cudaError_t launch_finalize(const SegmentGeom& g, const StatPartial* partials, c
   if (nimg <= 0) return cudaSuccess;
   ImageKernelShape sh;
   if (!image_kernel_shape(g.npix, &sh)) return cudaErrorInvalidValue;
-  const int nrb = g.npix / sh.rows_per_cta;
-  k_finalize<<<(nimg + 127) / 128, 128, 0, st>>>(g.npix, nrb, partials, img_info, weight, nimg, img_base,
+  const int nrb = sh.partials_per_image;
+  k_finalize<<<(nimg + 7) / 8, 256, 0, st>>>(g.npix, nrb, partials, img_info, weight, nimg, img_base,
                                                   threshold, cands, ncand, cand_cap, stats);
   return cudaGetLastError();
 }
 
 // --------------------------------------------------------------- dispatch --
-template <int N, bool FP16>
-cudaError_t run_grid_colfft(const SegmentGeom&, const DevTables&, const void*, const Group*, int, int, int,
-                            float2*, cudaStream_t);
+template <int N>
+cudaError_t run_colfft(const SegmentGeom&, const DevTables&, const Group*, int, int, int, const float2*, float2*,
+                       cudaStream_t);
 template <int N>
 cudaError_t run_rowfft_stats(const SegmentGeom&, const DevTables&, const float2*, int, int, const double*,
                              StatPartial*, float*, cudaStream_t);
@@ -265,13 +375,12 @@ void fill_shape(ImageKernelShape*);
 
 #define RF_FOR_EACH_N(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
 
-cudaError_t launch_grid_colfft(const SegmentGeom& g, const DevTables& tb, const void* S, const Group* groups,
-                               int g_begin, int ngroups, int img_base, float2* Tbuf, cudaStream_t st) {
+cudaError_t launch_colfft(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin,
+                          int ngroups, int img_base, const float2* cellbuf, float2* Tbuf, cudaStream_t st) {
   switch (g.npix) {
-#define RF_CASE(N)                                                                               \
-  case N:                                                                                        \
-    return g.fp16 ? run_grid_colfft<N, true>(g, tb, S, groups, g_begin, ngroups, img_base, Tbuf, st) \
-                  : run_grid_colfft<N, false>(g, tb, S, groups, g_begin, ngroups, img_base, Tbuf, st);
+#define RF_CASE(N) \
+  case N:          \
+    return run_colfft<N>(g, tb, groups, g_begin, ngroups, img_base, cellbuf, Tbuf, st);
     RF_FOR_EACH_N(RF_CASE)
 #undef RF_CASE
     default:

@@ -190,7 +190,7 @@ cudaError_t run_noalloc(const float2* grid, double weight, const DeviceSetup& d,
   tb.twiddle = tw;
   e = launch_rowfft_stats(g, tb, T, 1, 0, nullptr, partials, nullptr, st);
   if (e != cudaSuccess) return e;
-  k_noalloc_finalize<<<1, 32, 0, st>>>(partials, N / K::RB, N, weight, out);
+  k_noalloc_finalize<<<1, 32, 0, st>>>(partials, N / 2, N, weight, out);
   return cudaGetLastError();
 }
 
