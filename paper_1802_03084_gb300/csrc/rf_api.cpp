@@ -212,6 +212,8 @@ struct rf_plan {
   std::vector<Wave> waves;
   int gslots_max = 0;           // groups per wave (cell buffer capacity)
   float2* d_cellbuf = nullptr;
+  float* d_colsq = nullptr;     // [slots][ncol] Parseval sums
+  float* d_mean0 = nullptr;     // [slots] Re H(0, 0)
 
   std::atomic<int> busy{0};
   Profiler prof;
@@ -502,6 +504,12 @@ rf_status alloc_wave_scratch(rf_plan* p, int slots) {
     p->dfree(p->d_cellbuf);
     p->d_cellbuf = nullptr;
   }
+  if (p->d_colsq) {
+    p->device_bytes -= (uint64_t)p->slots_max * (p->ncol + 1) * sizeof(float);
+    p->dfree(p->d_colsq);
+    p->dfree(p->d_mean0);
+    p->d_colsq = p->d_mean0 = nullptr;
+  }
   p->slots_max = slots;
   p->gslots_max = std::max(2 * ((slots + B - 1) / B), 1);
   p->cached_nint = -1;
@@ -509,6 +517,8 @@ rf_status alloc_wave_scratch(rf_plan* p, int slots) {
   if ((s = p->dalloc(&p->d_T, (size_t)slots * per_slot)) != RF_OK) return s;
   if ((s = p->dalloc(&p->d_partials, (size_t)slots * nrb)) != RF_OK) return s;
   if ((s = p->dalloc(&p->d_cellbuf, (size_t)p->gslots_max * std::max(p->n_cells, 1) * 32)) != RF_OK) return s;
+  if ((s = p->dalloc(&p->d_colsq, (size_t)slots * p->ncol)) != RF_OK) return s;
+  if ((s = p->dalloc(&p->d_mean0, (size_t)slots)) != RF_OK) return s;
   return RF_OK;
 }
 
@@ -682,12 +692,14 @@ rf_status run_waves(rf_plan* p, int nint, const std::vector<Wave>& waves, int ni
     RF_TIMED(p->prof, K_GRID_CELLS, st,
              rf::launch_grid_cells(g, p->tb, p->d_groups, w.g_begin, ng, p->d_cellbuf, st));
     RF_TIMED(p->prof, K_GRID_COLFFT, st,
-             rf::launch_colfft(g, p->tb, p->d_groups, w.g_begin, ng, w.img_begin, p->d_cellbuf, p->d_T, st));
+             rf::launch_colfft(g, p->tb, p->d_groups, w.g_begin, ng, w.img_begin, p->d_cellbuf, p->d_T,
+                               p->d_colsq, p->d_mean0, st));
     float* im = d_images ? d_images + (size_t)w.img_begin * p->npix * p->npix : nullptr;
     RF_TIMED(p->prof, K_ROWFFT_STATS, st,
              rf::launch_rowfft_stats(g, p->tb, p->d_T, ni, w.img_begin, p->d_weight, p->d_partials, im, st));
     RF_TIMED(p->prof, K_FINALIZE, st,
-             rf::launch_finalize(g, p->d_partials, p->d_img_info, p->d_weight, ni, w.img_begin, p->threshold,
+             rf::launch_finalize(g, p->d_partials, p->d_colsq, p->d_mean0, p->d_img_info, p->d_weight, ni,
+                                 w.img_begin, p->threshold,
                                  p->d_cands, p->d_ncand, p->img_cap, d_stats, st));
   }
   return RF_OK;

@@ -112,9 +112,12 @@ cudaError_t launch_grid_cells(const SegmentGeom& g, const DevTables& tb, const G
                               int ngroups, float2* cellbuf, cudaStream_t st);
 
 // Column FFTs (pass A2) of the same groups from cellbuf; writes
-// Tbuf[slot][col][y], slot = image index - img_base.
+// Tbuf[slot][col][y], slot = image index - img_base, the Parseval sums
+// colsq[slot][col] (weighted sum of |H|^2 over the column) and
+// mean0[slot] = Re H(u = 0, v = 0).
 cudaError_t launch_colfft(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin,
-                          int ngroups, int img_base, const float2* cellbuf, float2* Tbuf, cudaStream_t st);
+                          int ngroups, int img_base, const float2* cellbuf, float2* Tbuf, float* colsq,
+                          float* mean0, cudaStream_t st);
 
 // Row C2R (pass B) + statistics of `nimg` images in slots [0, nimg) whose
 // first image index is img_base.  Optionally writes the scaled images.
@@ -124,9 +127,10 @@ cudaError_t launch_rowfft_stats(const SegmentGeom& g, const DevTables& tb, const
 
 // Reduce row-block partials, compute sigma / snr, append candidates and
 // (optionally) per-image stats for images [img_base, img_base + nimg).
-cudaError_t launch_finalize(const SegmentGeom& g, const StatPartial* partials, const int4* img_info,
-                            const double* weight, int nimg, int img_base, double threshold, DevCand* cands,
-                            int* ncand, int cand_cap, DevStat* stats, cudaStream_t st);
+cudaError_t launch_finalize(const SegmentGeom& g, const StatPartial* partials, const float* colsq,
+                            const float* mean0, const int4* img_info, const double* weight, int nimg, int img_base,
+                            double threshold, DevCand* cands, int* ncand, int cand_cap, DevStat* stats,
+                            cudaStream_t st);
 
 // Compile-time layout facts per image size, for host-side sizing.
 struct ImageKernelShape {

@@ -86,7 +86,8 @@ __device__ __forceinline__ float2 load_sample<true>(const void* __restrict__ S, 
 template <int N>
 __global__ void __launch_bounds__(ImgCfg<N>::THREADS_A, 2)
     k_colfft(SegmentGeom g, DevTables tb, const Group* __restrict__ groups, int g_begin, int img_base,
-             const float2* __restrict__ cellbuf, float2* __restrict__ Tbuf) {
+             const float2* __restrict__ cellbuf, float2* __restrict__ Tbuf, float* __restrict__ colsq,
+             float* __restrict__ mean0) {
   using K = ImgCfg<N>;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* fbuf = reinterpret_cast<float2*>(smraw);                     // [XA][STRIDE]
@@ -107,6 +108,31 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_A, 2)
   for (int c = tid; c < ncells; c += K::THREADS_A) crow[c] = tb.cell_row[cell0 + c];
   cp_async_wait_all();
   __syncthreads();
+
+  // Parseval: the image's sum of squares is N^2 / (4 W^2) times the sum of
+  // |G|^2 over the full Hermitian plane, which counts this column twice
+  // unless u = 0; its mean is G(0, 0) / (2 W).  Each warp sums |H|^2 of the
+  // column's cells for some of the images (FP32, fixed order).
+  {
+    const int lane = tid & 31;
+    const float wcol = col == 0 ? 1.f : 2.f;
+    for (int k = tid >> 5; k < gr.nimg; k += K::THREADS_A / 32) {
+      const int kc = k >> 1;
+      const int ko = k & 1;
+      float acc = 0.f;
+      for (int c = lane; c < ncells; c += 32) {
+        const float2 h = cellv[c * 32 + 2 * (kc ^ (c & 15)) + ko];
+        acc = fmaf(h.x, h.x, fmaf(h.y, h.y, acc));
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (lane == 0) {
+        const size_t slot = (size_t)(gr.img0 + k - img_base);
+        colsq[slot * g.ncol + col] = wcol * acc;
+        if (col == 0) mean0[slot] = (ncells > 0 && crow[0] == 0) ? cellv[k].x : 0.f;  // cell 0 is unswizzled
+      }
+    }
+  }
 
   const int xf = tid / K::T;
   const int t = tid - xf * K::T;
@@ -165,7 +191,6 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* fbuf = reinterpret_cast<float2*>(smraw);                  // [XB][STRIDE]
   float4* tile = reinterpret_cast<float4*>(fbuf + K::XB * K::STRIDE);  // [ncol][CH]
-  __shared__ float w_sum[32], w_sq[32];
   __shared__ float w_max[32];
   __shared__ int w_idx[32];
   const int tid = threadIdx.x;
@@ -195,21 +220,42 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     const int y0 = (item - slot * nrb) * K::RB;
     // first-pass inputs Z[u], u = t + r T: a + i b for 0 < u < ncol, the
     // Hermitian mirror conj(a) + i conj(b) for N - u < ncol, real parts at
-    // u = 0, zero elsewhere (columns beyond iu_max are empty)
+    // u = 0, zero elsewhere (columns beyond iu_max are empty).  N/2 = 16 T,
+    // so r < 16 can only be a direct column and r >= 16 only a mirror.
     float2 v[K::E];
+    if constexpr (K::E == 32 && K::T % K::CH == 0) {
+      // the swizzle term depends on u mod CH = t mod CH only
+      const int rd_end = ncol > t ? (ncol - t + K::T - 1) / K::T : 0;
+      const int rm_beg = (N - ncol - t) / K::T + 1;
+      const float4* pd = tile + t * K::CH + (xf ^ (t & (K::CH - 1)));
+      const float4* pm = tile + (size_t)(N - t) * K::CH + (xf ^ ((N - t) & (K::CH - 1)));
 #pragma unroll
-    for (int r = 0; r < K::E; ++r) {
-      const int u = t + r * K::T;
-      float2 z = make_float2(0.f, 0.f);
-      if (u < ncol) {
-        const float4 ab = tile[u * K::CH + (xf ^ (u & (K::CH - 1)))];
-        z = (u == 0) ? make_float2(ab.x, ab.z) : make_float2(ab.x - ab.w, ab.y + ab.z);
-      } else if (N - u < ncol) {
-        const int uu = N - u;
-        const float4 ab = tile[uu * K::CH + (xf ^ (uu & (K::CH - 1)))];
-        z = make_float2(ab.x + ab.w, ab.z - ab.y);
+      for (int r = 0; r < 16; ++r) {
+        float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < rd_end) ab = pd[r * K::T * K::CH];
+        v[r] = (r == 0 && t == 0) ? make_float2(ab.x, ab.z) : make_float2(ab.x - ab.w, ab.y + ab.z);
       }
-      v[r] = z;
+#pragma unroll
+      for (int r = 16; r < 32; ++r) {
+        float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r >= rm_beg) ab = pm[-r * K::T * K::CH];
+        v[r] = make_float2(ab.x + ab.w, ab.z - ab.y);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < K::E; ++r) {
+        const int u = t + r * K::T;
+        float2 z = make_float2(0.f, 0.f);
+        if (u < ncol) {
+          const float4 ab = tile[u * K::CH + (xf ^ (u & (K::CH - 1)))];
+          z = (u == 0) ? make_float2(ab.x, ab.z) : make_float2(ab.x - ab.w, ab.y + ab.z);
+        } else if (N - u < ncol) {
+          const int uu = N - u;
+          const float4 ab = tile[uu * K::CH + (xf ^ (uu & (K::CH - 1)))];
+          z = make_float2(ab.x + ab.w, ab.z - ab.y);
+        }
+        v[r] = z;
+      }
     }
     __syncthreads();  // tile consumed: prefetch the next item
     const int next = item + gridDim.x;
@@ -225,12 +271,10 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     }
     fft_inverse_from_regs<N>(v, fbuf + xf * K::STRIDE, tb.twiddle, t, xf);
 
-    // per-row-pair statistics: pixel sum and sum of squares (FP32 per
-    // thread, then a pairwise warp reduction), the max pixel and its lowest
-    // index; one StatPartial per row pair, no block-wide barrier
+    // per-row-pair statistics: the max pixel and its lowest index (the
+    // noise comes from the grid by Parseval's identity, see k_colfft)
     const int y = y0 + 2 * xf;
     float lmax = -FLT_MAX;
-    float lsum = 0.f, lsq = 0.f;
     constexpr int LP = FftShape<N>::LAST_P;
     float scale = 0.f;
     if (images != nullptr) {
@@ -243,9 +287,6 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
       for (int q = 0; q < LP; ++q) {
         const float2 z = v[m * LP + dft_perm<LP>(q)];
         lmax = fmaxf(lmax, fmaxf(z.x, z.y));
-        lsum += z.x + z.y;
-        lsq = fmaf(z.x, z.x, lsq);
-        lsq = fmaf(z.y, z.y, lsq);
         if (images != nullptr) {
           const int o = fft_out_index<N>(t, m, q);
           float* im = images + ((size_t)slot * N + y) * N;
@@ -260,11 +301,7 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     constexpr unsigned MASK = 0xffffffffu;
     float wmax = lmax;
 #pragma unroll
-    for (int off = WL / 2; off > 0; off >>= 1) {
-      lsum += __shfl_xor_sync(MASK, lsum, off);
-      lsq += __shfl_xor_sync(MASK, lsq, off);
-      wmax = fmaxf(wmax, __shfl_xor_sync(MASK, wmax, off));
-    }
+    for (int off = WL / 2; off > 0; off >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(MASK, wmax, off));
     int best = INT_MAX;
     if (lmax == wmax) {
 #pragma unroll
@@ -285,24 +322,18 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
       constexpr int WPT = K::T / 32;
       const int wi = t >> 5;
       if (lane == 0) {
-        w_sum[wid] = lsum;
-        w_sq[wid] = lsq;
         w_max[wid] = wmax;
         w_idx[wid] = best;
       }
       fft_sync<K::T>(xf);
       if (t == 0) {
         const int w0 = wid - wi;
-        float s2 = 0.f, q2 = 0.f, mx = -FLT_MAX;
+        float mx = -FLT_MAX;
         int mi = INT_MAX;
-        for (int w = 0; w < WPT; ++w) {
-          s2 += w_sum[w0 + w];
-          q2 += w_sq[w0 + w];
-          max_merge(mx, mi, w_max[w0 + w], w_idx[w0 + w]);
-        }
+        for (int w = 0; w < WPT; ++w) max_merge(mx, mi, w_max[w0 + w], w_idx[w0 + w]);
         StatPartial sp;
-        sp.sum = (double)s2;
-        sp.sumsq = (double)q2;
+        sp.sum = 0.0;
+        sp.sumsq = 0.0;
         sp.max = mx;
         sp.idx = mi;
         sp.pad[0] = sp.pad[1] = 0;
@@ -311,8 +342,8 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
       fft_sync<K::T>(xf);
     } else if (t == 0) {
       StatPartial sp;
-      sp.sum = (double)lsum;
-      sp.sumsq = (double)lsq;
+      sp.sum = 0.0;
+      sp.sumsq = 0.0;
       sp.max = wmax;
       sp.idx = best;
       sp.pad[0] = sp.pad[1] = 0;
@@ -333,7 +364,8 @@ inline int sm_count() {
 
 template <int N>
 cudaError_t run_colfft(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin, int ngroups,
-                       int img_base, const float2* cellbuf, float2* Tbuf, cudaStream_t st) {
+                       int img_base, const float2* cellbuf, float2* Tbuf, float* colsq, float* mean0,
+                       cudaStream_t st) {
   using K = ImgCfg<N>;
   const int smem = K::SMEM_A_FIXED + g.max_cells * (32 * 8 + 4);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
@@ -344,7 +376,7 @@ cudaError_t run_colfft(const SegmentGeom& g, const DevTables& tb, const Group* g
   if (e != cudaSuccess) return e;
   if (ngroups <= 0) return cudaSuccess;
   dim3 grid(ngroups, g.ncol);
-  k_colfft<N><<<grid, K::THREADS_A, smem, st>>>(g, tb, groups, g_begin, img_base, cellbuf, Tbuf);
+  k_colfft<N><<<grid, K::THREADS_A, smem, st>>>(g, tb, groups, g_begin, img_base, cellbuf, Tbuf, colsq, mean0);
   return cudaGetLastError();
 }
 
@@ -386,7 +418,7 @@ void fill_shape(ImageKernelShape* o) {
 
 #define RF_INSTANTIATE_IMAGE(N)                                                                              \
   template cudaError_t run_colfft<N>(const SegmentGeom&, const DevTables&, const Group*, int, int, int,      \
-                                     const float2*, float2*, cudaStream_t);                                 \
+                                     const float2*, float2*, float*, float*, cudaStream_t);                 \
   template cudaError_t run_rowfft_stats<N>(const SegmentGeom&, const DevTables&, const float2*, int, int,    \
                                            const double*, StatPartial*, float*, cudaStream_t);              \
   template void fill_shape<N>(ImageKernelShape*);

@@ -273,29 +273,30 @@ __device__ __forceinline__ void fmax_merge(float& m, int& i, float m2, int i2) {
   }
 }
 
-__global__ void k_finalize(int npix, int nrb, const StatPartial* __restrict__ partials,
+__global__ void k_finalize(int npix, int nrb, int ncol, const StatPartial* __restrict__ partials,
+                           const float* __restrict__ colsq, const float* __restrict__ mean0,
                            const int4* __restrict__ img_info, const double* __restrict__ weight, int nimg,
                            int img_base, double threshold, DevCand* __restrict__ cands, int* __restrict__ ncand,
                            int cand_cap, DevStat* __restrict__ stats) {
-  // one warp per image; lanes stride over the row-block partials, then an
-  // xor-tree (fixed order) combines them
+  // one warp per image; lanes stride over the row-pair partials (peak) and
+  // the per-column Parseval sums (FP64), then an xor-tree (fixed order)
+  // combines them
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= nimg) return;
   const int img = img_base + i;
   const StatPartial* pp = partials + (size_t)i * nrb;
-  double sum = 0.0, sq = 0.0;
+  const float* cs = colsq + (size_t)i * ncol;
+  double sq = 0.0;
   float mx = -FLT_MAX;
   int mi = INT_MAX;
   for (int r = lane; r < nrb; r += 32) {
     const StatPartial p = pp[r];
-    sum += p.sum;
-    sq += p.sumsq;
     fmax_merge(mx, mi, p.max, p.idx);
   }
+  for (int c = lane; c < ncol; c += 32) sq += (double)cs[c];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    sum += __shfl_xor_sync(0xffffffffu, sum, off);
     sq += __shfl_xor_sync(0xffffffffu, sq, off);
     const float om = __shfl_xor_sync(0xffffffffu, mx, off);
     const int oi = __shfl_xor_sync(0xffffffffu, mi, off);
@@ -317,10 +318,10 @@ __global__ void k_finalize(int npix, int nrb, const StatPartial* __restrict__ pa
     if (stats) stats[img] = ds;
     return;
   }
+  // mean = G(0,0) / 2W; mean of I^2 = sum_full |G|^2 / 4W^2 (Parseval)
   const double inv = 0.5 / W;
-  const double n2 = (double)npix * (double)npix;
-  const double mean = sum * inv / n2;
-  double var = sq * inv * inv / n2 - mean * mean;
+  const double mean = (double)mean0[i] * inv;
+  double var = sq * inv * inv - mean * mean;
   var = var > 0.0 ? var : 0.0;
   const double sigma = sqrt(var);
   const double peak = (double)mx * inv;
@@ -351,14 +352,16 @@ __global__ void k_finalize(int npix, int nrb, const StatPartial* __restrict__ pa
   }
 }
 
-cudaError_t launch_finalize(const SegmentGeom& g, const StatPartial* partials, const int4* img_info,
-                            const double* weight, int nimg, int img_base, double threshold, DevCand* cands,
-                            int* ncand, int cand_cap, DevStat* stats, cudaStream_t st) {
+cudaError_t launch_finalize(const SegmentGeom& g, const StatPartial* partials, const float* colsq,
+                            const float* mean0, const int4* img_info, const double* weight, int nimg, int img_base,
+                            double threshold, DevCand* cands, int* ncand, int cand_cap, DevStat* stats,
+                            cudaStream_t st) {
   if (nimg <= 0) return cudaSuccess;
   ImageKernelShape sh;
   if (!image_kernel_shape(g.npix, &sh)) return cudaErrorInvalidValue;
   const int nrb = sh.partials_per_image;
-  k_finalize<<<(nimg + 7) / 8, 256, 0, st>>>(g.npix, nrb, partials, img_info, weight, nimg, img_base,
+  k_finalize<<<(nimg + 7) / 8, 256, 0, st>>>(g.npix, nrb, g.ncol, partials, colsq, mean0, img_info, weight, nimg,
+                                              img_base,
                                                   threshold, cands, ncand, cand_cap, stats);
   return cudaGetLastError();
 }
@@ -366,7 +369,7 @@ cudaError_t launch_finalize(const SegmentGeom& g, const StatPartial* partials, c
 // --------------------------------------------------------------- dispatch --
 template <int N>
 cudaError_t run_colfft(const SegmentGeom&, const DevTables&, const Group*, int, int, int, const float2*, float2*,
-                       cudaStream_t);
+                       float*, float*, cudaStream_t);
 template <int N>
 cudaError_t run_rowfft_stats(const SegmentGeom&, const DevTables&, const float2*, int, int, const double*,
                              StatPartial*, float*, cudaStream_t);
@@ -376,11 +379,12 @@ void fill_shape(ImageKernelShape*);
 #define RF_FOR_EACH_N(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
 
 cudaError_t launch_colfft(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin,
-                          int ngroups, int img_base, const float2* cellbuf, float2* Tbuf, cudaStream_t st) {
+                          int ngroups, int img_base, const float2* cellbuf, float2* Tbuf, float* colsq,
+                          float* mean0, cudaStream_t st) {
   switch (g.npix) {
 #define RF_CASE(N) \
   case N:          \
-    return run_colfft<N>(g, tb, groups, g_begin, ngroups, img_base, cellbuf, Tbuf, st);
+    return run_colfft<N>(g, tb, groups, g_begin, ngroups, img_base, cellbuf, Tbuf, colsq, mean0, st);
     RF_FOR_EACH_N(RF_CASE)
 #undef RF_CASE
     default:

@@ -28,12 +28,13 @@ namespace {
 constexpr int kMaxN = RF_NOALLOC_MAX_NPIX;
 constexpr int kMaxDevices = 64;
 
-// Scratch: column-FFT output T[u][y] (u < N/2) followed by the row-block
-// partials of the statistics kernel.  Every byte a call reads is written by
+// Scratch: column-FFT output T[u][y] (u < N/2), the row-pair partials of
+// the statistics kernel, the per-column Parseval sums and the (0, 0) term.  Every byte a call reads is written by
 // the same call first, so nothing has to start at zero.
 constexpr size_t kTBytes = (size_t)kMaxN * (kMaxN / 2) * sizeof(float2);
 constexpr size_t kPartialBytes = 4096 * sizeof(StatPartial);
-static __device__ __align__(256) unsigned char g_noalloc_scratch[kTBytes + kPartialBytes];
+constexpr size_t kColsqBytes = (kMaxN / 2 + 64) * sizeof(float);  // Parseval column sums + mean term
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kTBytes + kPartialBytes + kColsqBytes];
 
 // Twiddle tables exp(+2 pi i m / N), m < N, for N = 16, 32, ..., kMaxN, back
 // to back (constants written once per device at set-up, not scratch).
@@ -97,7 +98,8 @@ rf_status ensure_setup(int dev, DeviceSetup** out) {
 // (-1)^(u + v) phase-centre shift and inverse-FFTs it along v.
 template <int N>
 __global__ void __launch_bounds__(ImgCfg<N>::T * ImgCfg<N>::XA)
-    k_colfft_dense(const float2* __restrict__ grid, float2* __restrict__ T, const float2* __restrict__ tw) {
+    k_colfft_dense(const float2* __restrict__ grid, float2* __restrict__ T, const float2* __restrict__ tw,
+                   float* __restrict__ colsq, float* __restrict__ mean0) {
   using K = ImgCfg<N>;
   constexpr int W = N / 2 + 1;
   constexpr int NC = N / 2;
@@ -119,9 +121,24 @@ __global__ void __launch_bounds__(ImgCfg<N>::T * ImgCfg<N>::XA)
   __syncthreads();
   const int xf = tid / K::T;
   const int t = tid - xf * K::T;
+  const int u = col0 + xf;
+  {
+    // Parseval: weighted sum of |H|^2 down the column (twice for u > 0)
+    float acc = 0.f;
+    for (int v = t; v < N; v += K::T) {
+      const float2 h = sm[xf * K::STRIDE + padx(v)];
+      acc = fmaf(h.x, h.x, fmaf(h.y, h.y, acc));
+    }
+    constexpr int WL = K::T < 32 ? K::T : 32;
+#pragma unroll
+    for (int off = WL / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (t == 0 && u < NC) {
+      colsq[u] = (u == 0 ? 1.f : 2.f) * acc;
+      if (u == 0) *mean0 = sm[xf * K::STRIDE].x;
+    }
+  }
   float2 v[K::E];
   fft_inverse_to_regs<N>(v, sm + xf * K::STRIDE, tw, t, xf);
-  const int u = col0 + xf;
   if (u < NC) {
     float2* dst = T + (size_t)u * N;
     constexpr int LP = FftShape<N>::LAST_P;
@@ -133,25 +150,25 @@ __global__ void __launch_bounds__(ImgCfg<N>::T * ImgCfg<N>::XA)
 }
 
 // Reduce the row-block partials of one image into an rf_image_stat.
-__global__ void k_noalloc_finalize(const StatPartial* __restrict__ partials, int nrb, int npix, double weight,
+__global__ void k_noalloc_finalize(const StatPartial* __restrict__ partials, int nrb, const float* __restrict__ colsq,
+                                   const float* __restrict__ mean0, int npix, double weight,
                                    rf_image_stat* __restrict__ out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double sum = 0.0, sq = 0.0;
+  double sq = 0.0;
   float mx = -FLT_MAX;
   int mi = INT_MAX;
   for (int r = 0; r < nrb; ++r) {
     const StatPartial p = partials[r];
-    sum += p.sum;
-    sq += p.sumsq;
     if (p.max > mx || (p.max == mx && p.idx < mi)) {
       mx = p.max;
       mi = p.idx;
     }
   }
+  for (int c = 0; c < npix / 2; ++c) sq += (double)colsq[c];
+  // mean = G(0,0) / 2W; mean of I^2 = sum_full |G|^2 / 4W^2 (Parseval)
   const double inv = 0.5 / weight;
-  const double n2 = (double)npix * (double)npix;
-  const double mean = sum * inv / n2;
-  double var = sq * inv * inv / n2 - mean * mean;
+  const double mean = (double)*mean0 * inv;
+  double var = sq * inv * inv - mean * mean;
   var = var > 0.0 ? var : 0.0;
   const double sigma = sqrt(var);
   const double peak = (double)mx * inv;
@@ -178,9 +195,11 @@ cudaError_t run_noalloc(const float2* grid, double weight, const DeviceSetup& d,
   if (attr != cudaSuccess) return attr;
   float2* T = reinterpret_cast<float2*>(d.scratch);
   StatPartial* partials = reinterpret_cast<StatPartial*>(d.scratch + kTBytes);
+  float* colsq = reinterpret_cast<float*>(d.scratch + kTBytes + kPartialBytes);
+  float* mean0 = colsq + kMaxN / 2;
   const float2* tw = d.twiddle + twiddle_offset(N);
   constexpr int NC = N / 2;
-  k_colfft_dense<N><<<(NC + K::XA - 1) / K::XA, K::T * K::XA, K::SMEM_A_FIXED, st>>>(grid, T, tw);
+  k_colfft_dense<N><<<(NC + K::XA - 1) / K::XA, K::T * K::XA, K::SMEM_A_FIXED, st>>>(grid, T, tw, colsq, mean0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   SegmentGeom g{};
@@ -190,7 +209,7 @@ cudaError_t run_noalloc(const float2* grid, double weight, const DeviceSetup& d,
   tb.twiddle = tw;
   e = launch_rowfft_stats(g, tb, T, 1, 0, nullptr, partials, nullptr, st);
   if (e != cudaSuccess) return e;
-  k_noalloc_finalize<<<1, 32, 0, st>>>(partials, N / 2, N, weight, out);
+  k_noalloc_finalize<<<1, 32, 0, st>>>(partials, N / 2, colsq, mean0, N, weight, out);
   return cudaGetLastError();
 }
 
