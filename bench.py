@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--wave-images", type=int, default=0, help="images per wave (0 = engine default)")
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain per-trial form")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the engine's default tuning")
+    ap.add_argument("--tune-cache", default=os.path.expanduser("~/.cache/realfast_gb300/tune.json"))
     ap.add_argument("--host-input", action="store_true",
                     help="time the search from pinned host input only (small device footprint for profilers)")
     return ap.parse_args()
@@ -200,59 +203,86 @@ def cpu_baseline(spec, seg, seconds):
 
 # ------------------------------------------------------------ work counts --
 def work_per_image(spec, info, fp16):
-    """Algorithmic bytes and flops per image for each imaging kernel."""
+    """Algorithmic bytes and flops per image of each imaging kernel.
+
+    grid_cells: one resampled sample per gridding entry (8 B FP32, 4 B FP16)
+    read and one 8-byte cell value written per occupied cell.
+    grid_colfft (the column FFTs): cells read, column FFT output
+    (8 N ncol B) written; ncol length-N FFTs.
+    rowfft_stats: the column FFT output read once; N/2 length-N FFTs (two
+    image rows per complex transform).  FFTs count 5 N log2 N flops.
+    """
     N = spec.npix
     ncol = info.iu_max + 1
-    nbl, nchan = info.nbl, info.nchan
-    mean_dt = None
+    esz = 4 if fp16 else 8
+    fft = 5.0 * N * math.log2(N)
     return {
-        "grid_colfft": {
-            # visibility gather (per sample) + column-FFT output written once
-            "bytes_per_sample": (4 if fp16 else 8) * info.n_entries,
-            "bytes_fixed": 8 * N * ncol,
-            "flops": ncol * 5.0 * N * math.log2(N),
-        },
-        "rowfft_stats": {
-            "bytes_fixed": 8 * N * ncol,   # column-FFT output read once
-            "bytes_per_sample": 0,
-            "flops": (N / 2) * 5.0 * N * math.log2(N),
-        },
+        "grid_cells": {"bytes": esz * info.n_entries + 8 * info.n_cells, "flops": 0.0, "bound": "hbm"},
+        "grid_colfft": {"bytes": 8 * info.n_cells + 8 * N * ncol, "flops": ncol * fft, "bound": "alu"},
+        "rowfft_stats": {"bytes": 8 * N * ncol, "flops": (N / 2) * fft, "bound": "alu"},
     }
 
 
-def roofline(prof, spec, info, n_images, samples_per_step, steps, fp16, hbm_peak, peak_kind, clock_mhz):
+FP32_PEAK_TFLOPS = GB300_SMS * FP32_LANES_PER_SM * 2 * GB300_MAX_SM_MHZ * 1e6 / 1e12
+
+
+def load_traffic(kernel, images_per_launch):
+    """DRAM bytes per launch from the committed ncu summary, scaled to this
+    launch's images; None if the summary is missing or was taken from other
+    kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    k = t.get("kernels", {}).get(kernel)
+    if not k or t.get("source_hash") != source_hash():
+        return None
+    return k["dram_bytes_per_image"] * images_per_launch
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1802_03084_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def roofline(prof, spec, info, n_images, steps, fp16, hbm_peak, peak_kind):
     work = work_per_image(spec, info, fp16)
     per = {}
     for name, w in work.items():
         launches, ms = prof.get(name, (0, 0.0))
         if launches == 0:
             continue
-        imgs_per_launch = n_images * steps / launches
-        samples_per_launch = samples_per_step * steps / launches
-        bytes_per_launch = w["bytes_fixed"] * imgs_per_launch + w["bytes_per_sample"] * samples_per_launch
-        flops_per_launch = w["flops"] * imgs_per_launch
+        imgs = n_images * steps / launches
         avg_s = ms / launches / 1e3
-        per[name] = dict(launches=launches, total_ms=ms, avg_us=avg_s * 1e6, images_per_launch=imgs_per_launch,
-                         gbs=bytes_per_launch / avg_s / 1e9, tflops=flops_per_launch / avg_s / 1e12)
+        per[name] = dict(launches=launches, total_ms=ms, avg_us=avg_s * 1e6, images_per_launch=imgs,
+                         gbs=w["bytes"] * imgs / avg_s / 1e9, tflops=w["flops"] * imgs / avg_s / 1e12,
+                         bound=w["bound"])
     if not per:
         return None, per
     dom = max(per, key=lambda k: per[k]["total_ms"])
     d = per[dom]
-    fp32_peak = GB300_SMS * FP32_LANES_PER_SM * 2 * GB300_MAX_SM_MHZ * 1e6 / 1e12
-    hbm_frac = d["gbs"] / hbm_peak
-    alu_frac = d["tflops"] / fp32_peak
-    if alu_frac >= hbm_frac:
-        r = {"bound": "alu", "achieved": round(d["tflops"], 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-             "frac": round(alu_frac, 4), "traffic": None, "kernel": dom,
-             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz max SM clock",
+    traffic = load_traffic(dom, d["images_per_launch"])
+    if d["bound"] == "alu":
+        r = {"bound": "alu", "achieved": round(d["tflops"], 3), "peak": round(FP32_PEAK_TFLOPS, 2),
+             "unit": "TFLOP/s", "frac": round(d["tflops"] / FP32_PEAK_TFLOPS, 4), "traffic": traffic,
+             "kernel": dom,
+             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz max SM clock",
              "flops_model": "5 N log2 N per length-N complex FFT",
-             "hbm_achieved_gbs": round(d["gbs"], 1), "hbm_frac": round(hbm_frac, 4),
-             "hbm_peak": hbm_peak, "hbm_peak_source": peak_kind}
+             "hbm_achieved_gbs": round(d["gbs"], 1), "hbm_frac_of_measured": round(d["gbs"] / hbm_peak, 4)}
     else:
         r = {"bound": "hbm", "achieved": round(d["gbs"], 1), "peak": hbm_peak, "unit": "GB/s",
-             "frac": round(hbm_frac, 4), "traffic": None, "kernel": dom, "peak_source": peak_kind,
-             "alu_tflops": round(d["tflops"], 3), "alu_frac": round(alu_frac, 4)}
+             "frac": round(d["gbs"] / hbm_peak, 4), "traffic": traffic, "kernel": dom,
+             "peak_source": peak_kind}
     r["avg_launch_us"] = round(d["avg_us"], 2)
+    r["images_per_launch"] = round(d["images_per_launch"], 1)
     return r, per
 
 
@@ -331,20 +361,14 @@ def main():
     plan = rf.Plan.from_spec(spec, seg["ant_uvw"], seg["freq_hz"], max_nint=nint, device=local_rank)
     if args.form == "plain":
         plan.set_form(rf.RF_FORM_PLAIN)
+    tuning = None
     if args.wave_images:
         plan.set_wave_images(args.wave_images)
+    elif not args.no_autotune and args.form == "batched":
+        tuning = plan.autotune(vis_dev, nint, cache_path=args.tune_cache)
     info = plan.info()
     n_images = plan.count_images(nint)
     fp16 = spec.store == "fp16"
-    # samples gathered per step: sum over images of dt (each image sums dt samples per entry)
-    d_max = plan.delays().max(axis=1)
-    samples_per_step = 0
-    for d in range(len(spec.dm_list)):
-        for dt in spec.dt_list:
-            span = nint - int(d_max[d])
-            nt = max(span // dt, 0) if span > 0 else 0
-            samples_per_step += nt * dt
-
     for _ in range(max(args.warmup, 0)):
         cands = plan.search(vis_dev, nint)
     plan.set_profiling(True)
@@ -396,9 +420,35 @@ def main():
                "d2h_bytes_per_step": int(4 + len(c2) * rf.CANDIDATE_DTYPE.itemsize),
                "ms_per_step": ems / args.steps}
 
+    # the same segment without per-kernel events (graph replay), and the
+    # plain one-launch-set-per-trial form on the same GPU
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    plan.search(vis_dev, nint)
+    g0.record()
+    for _ in range(args.steps):
+        plan.search(vis_dev, nint)
+    g1.record()
+    torch.cuda.synchronize()
+    graph_value = world * args.steps * n_images / (g0.elapsed_time(g1) / 1e3)
+    plain = None
+    if not args.no_plain and args.form == "batched":
+        plan.set_form(rf.RF_FORM_PLAIN)
+        plan.search(vis_dev, nint)
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record()
+        plan.search(vis_dev, nint)
+        p1.record()
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1)
+        plain = {"value": n_images / (pms / 1e3), "unit": UNIT, "ms_per_step": pms, "steps": 1,
+                 "form": "one unfused launch set per (DM, dt) trial, intermediates in HBM"}
+        plan.set_form(rf.RF_FORM_BATCHED)
+
     hbm_peak, peak_kind = peaks()
-    roof, per_kernel = roofline(prof, spec, info, n_images, samples_per_step, args.steps, fp16, hbm_peak,
-                                peak_kind, clk.get("sm_mhz"))
+    roof, per_kernel = roofline(prof, spec, info, n_images, args.steps, fp16, hbm_peak, peak_kind)
     launches = sum(v[0] for k, v in prof.items() if k != "h2d_copy")
     value = world * args.steps * n_images / (ms / 1e3)
     seg_s = nint * spec.inttime_s
@@ -408,6 +458,7 @@ def main():
         "vs_baseline": None, "dtype": "f32" if not fp16 else "f16-storage/f32", "data": "synthetic",
         "config": {"workload": workload_name(spec), "images_per_step": n_images, "form": args.form,
                    "wave_images": plan.wave_images(), "input": "pinned host" if args.host_input else "HBM",
+                   "autotune": tuning,
                    "l2": f"inputs larger than L2 ({seg['vis'].nbytes / 1e9:.2f} GB segment per step)",
                    "parallelism": f"dp{world} (one segment per GPU)"},
         "visibility_gbs": world * args.steps * seg["vis"].nbytes / (ms / 1e3) / 1e9,
@@ -418,7 +469,11 @@ def main():
         "roofline": roof,
         "kernels": {k: {kk: (round(vv, 3) if isinstance(vv, float) else vv) for kk, vv in v.items()}
                     for k, v in per_kernel.items()},
+        "kernel_source_hash": source_hash(),
         "e2e": e2e,
+        "graph_replay_value": graph_value,
+        "plain_form": plain,
+        "batched_over_plain": (value / plain["value"]) if plain else None,
         "gpu_launches": int(launches),
         "clocks": clk,
     }

@@ -230,8 +230,32 @@ rf_status rf_plan_set_form(struct rf_plan* plan, int32_t form);
  * RF_ERR_NO_MEMORY, RF_ERR_BUSY.
  */
 #define RF_TUNE_WAVE_IMAGES 1
+/* RF_TUNE_GRAPHS       1 (default): the batched form records its per-wave
+ *                      launches once per segment length as a CUDA graph and
+ *                      replays it; 0: direct launches. */
+#define RF_TUNE_GRAPHS 2
 rf_status rf_plan_set_tuning(struct rf_plan* plan, int32_t key, int64_t value);
 rf_status rf_plan_get_tuning(const struct rf_plan* plan, int32_t key, int64_t* value);
+
+/*
+ * rf_plan_autotune: pick the tuning (RF_TUNE_WAVE_IMAGES from a ladder of
+ * wave sizes that fit in half the free device memory, RF_TUNE_GRAPHS on or
+ * off) that searches `vis` fastest, timing one full search per candidate
+ * with CUDA events on `stream` after one warm-up, and apply it.  vis and
+ * nint as for rf_search_segment.  `report` (may be NULL) receives what was
+ * tried.  Results of the search do not depend on the tuning.
+ * Errors: as rf_search_segment.
+ */
+typedef struct rf_tune_report {
+  int32_t best_wave_images;
+  int32_t best_graphs;
+  int32_t ntried;
+  int32_t tried_wave_images[16];
+  int32_t tried_graphs[16];
+  float tried_ms[16];
+} rf_tune_report;
+rf_status rf_plan_autotune(struct rf_plan* plan, const void* vis, int32_t nint, void* stream,
+                           rf_tune_report* report);
 
 /* Derived facts of a plan (see rf_plan_info). */
 rf_status rf_plan_get_info(const struct rf_plan* plan, rf_plan_info* info);

@@ -24,7 +24,8 @@ __all__ = [
     "lib", "make_desc", "rf_plan_create", "rf_plan_destroy", "rf_search_segment",
     "rf_search_segment_stats", "rf_render_images", "rf_plan_set_form", "rf_plan_get_info",
     "rf_plan_delays", "rf_plan_cells", "rf_count_images", "rf_last_error", "rf_version",
-    "rf_plan_set_profiling", "rf_plan_get_profile", "RfKernelProfile", "rf_image_stats_noalloc", "rf_plan_set_tuning", "rf_plan_get_tuning",
+    "rf_plan_set_profiling", "rf_plan_get_profile", "RfKernelProfile", "rf_image_stats_noalloc", "rf_plan_set_tuning", "rf_plan_get_tuning", "rf_plan_autotune",
+    "RfTuneReport",
     "Plan", "CANDIDATE_DTYPE", "STAT_DTYPE", "declared_symbols",
     "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
 ]
@@ -49,6 +50,7 @@ RF_FORM_BATCHED = 0
 RF_FORM_PLAIN = 1
 RF_NOALLOC_MAX_NPIX = 1024
 RF_TUNE_WAVE_IMAGES = 1
+RF_TUNE_GRAPHS = 2
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
                       "realfast_gb300.h")
@@ -94,6 +96,12 @@ class RfPlanInfo(ctypes.Structure):
                 ("iv_max", ctypes.c_int32), ("n_offgrid", ctypes.c_int32), ("n_cells", ctypes.c_int32),
                 ("n_entries", ctypes.c_int32), ("max_delay", ctypes.c_int32),
                 ("images_per_group", ctypes.c_int32), ("device_bytes", ctypes.c_uint64)]
+
+
+class RfTuneReport(ctypes.Structure):
+    _fields_ = [("best_wave_images", ctypes.c_int32), ("best_graphs", ctypes.c_int32), ("ntried", ctypes.c_int32),
+                ("tried_wave_images", ctypes.c_int32 * 16), ("tried_graphs", ctypes.c_int32 * 16),
+                ("tried_ms", ctypes.c_float * 16)]
 
 
 class RfKernelProfile(ctypes.Structure):
@@ -143,6 +151,7 @@ def lib() -> ctypes.CDLL:
         "rf_plan_set_tuning": ([P, ctypes.c_int32, ctypes.c_int64], ctypes.c_int),
         "rf_plan_get_tuning": ([P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "rf_image_stats_noalloc": ([P, ctypes.c_int32, ctypes.c_double, P, P], ctypes.c_int),
+        "rf_plan_autotune": ([P, P, ctypes.c_int32, P, ctypes.POINTER(RfTuneReport)], ctypes.c_int),
         "rf_plan_get_profile": ([P, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -318,6 +327,15 @@ def rf_plan_get_tuning(plan, key: int) -> int:
     return int(v.value)
 
 
+def rf_plan_autotune(plan, vis, nint: int, stream=None) -> dict:
+    """Time the tuning ladder on this segment, apply the fastest, return what was tried."""
+    rep = RfTuneReport()
+    _check(lib().rf_plan_autotune(plan, _ptr(vis), nint, _stream(stream), ctypes.byref(rep)))
+    return {"wave_images": rep.best_wave_images, "graphs": rep.best_graphs,
+            "tried": [(rep.tried_wave_images[i], rep.tried_graphs[i], float(rep.tried_ms[i]))
+                      for i in range(rep.ntried)]}
+
+
 def rf_image_stats_noalloc(half_plane, npix: int, weight: float, stat, stream=None) -> None:
     """Image one device half plane into the device rf_image_stat `stat` (no allocation)."""
     _check(lib().rf_image_stats_noalloc(_ptr(half_plane), npix, weight, _stream(stream), _ptr(stat)))
@@ -380,6 +398,44 @@ class Plan:
 
     def wave_images(self) -> int:
         return rf_plan_get_tuning(self.handle, RF_TUNE_WAVE_IMAGES)
+
+    def set_graphs(self, enable: bool):
+        rf_plan_set_tuning(self.handle, RF_TUNE_GRAPHS, 1 if enable else 0)
+
+    def autotune(self, vis, nint=None, stream=None, cache_path=None, key_extra=""):
+        """Apply a cached tuning for this shape, or run the autotuner and cache it.
+
+        The cache is a JSON file mapping a shape key (image size, channels,
+        baselines, trials, segment length, flags, device name) to the chosen
+        wave size and graph mode.
+        """
+        import json
+        n = nint if nint is not None else len(vis)
+        info = self.info()
+        try:
+            import torch
+            dev = torch.cuda.get_device_name(self.desc.device)
+        except Exception:
+            dev = "cuda"
+        key = f"{info.npix}/{info.nchan}/{info.nbl}/{info.ndm}/{info.ndt}/{n}/{self.desc.flags}/{dev}{key_extra}"
+        cache = {}
+        if cache_path and os.path.exists(cache_path):
+            try:
+                with open(cache_path) as f:
+                    cache = json.load(f)
+            except (OSError, ValueError):
+                cache = {}
+        if key in cache:
+            rf_plan_set_tuning(self.handle, RF_TUNE_WAVE_IMAGES, int(cache[key]["wave_images"]))
+            rf_plan_set_tuning(self.handle, RF_TUNE_GRAPHS, int(cache[key]["graphs"]))
+            return dict(cache[key], cached=True)
+        res = rf_plan_autotune(self.handle, vis, n, stream)
+        if cache_path:
+            cache[key] = {"wave_images": res["wave_images"], "graphs": res["graphs"]}
+            os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
+            with open(cache_path, "w") as f:
+                json.dump(cache, f, indent=1)
+        return dict(res, cached=False)
 
     def close(self):
         if self.handle:

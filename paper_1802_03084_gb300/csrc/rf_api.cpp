@@ -52,6 +52,7 @@ constexpr uint32_t kKnownFlags = RF_STORE_FP16 | RF_EDGE_PARTIAL | RF_HOST_ONLY;
 constexpr size_t kStageBytes = 256ull << 20;   // host->device chunk of raw visibilities
 constexpr size_t kTBudgetBytes = 4096ull << 20;  // column-FFT scratch per wave
 constexpr int kRangeEntries = 64;                // target entries per gridding warp
+constexpr size_t kPlainBudgetBytes = 4096ull << 20;  // plain form: intermediates of one chunk
 
 // Round half away from zero: sign(x) floor(|x| + 1/2).
 inline double round_half_away(double x) { return x >= 0.0 ? std::floor(x + 0.5) : -std::floor(-x + 0.5); }
@@ -89,10 +90,11 @@ struct BusyGuard {
 };
 
 enum KernelKind {
-  K_H2D = 0, K_INGEST, K_RESAMPLE, K_WEIGHTS, K_GRID_CELLS, K_GRID_COLFFT, K_ROWFFT_STATS, K_FINALIZE, K_NKINDS
+  K_H2D = 0, K_INGEST, K_RESAMPLE, K_WEIGHTS, K_GRID_CELLS, K_GRID_COLFFT, K_ROWFFT_STATS, K_FINALIZE,
+  K_PLAIN_TRIAL, K_NKINDS
 };
-const char* const kKindNames[K_NKINDS] = {"h2d_copy", "ingest",      "resample",     "weights",
-                                           "grid_cells", "grid_colfft", "rowfft_stats", "finalize"};
+const char* const kKindNames[K_NKINDS] = {"h2d_copy",   "ingest",      "resample",     "weights",    "grid_cells",
+                                           "grid_colfft", "rowfft_stats", "finalize", "plain_trial_chunk"};
 
 // Event-pair timing of every launch a plan issues while profiling is on.
 struct Profiler {
@@ -133,6 +135,29 @@ struct Profiler {
       }
     }
     used = 0;
+  }
+  // Hands the pairs [from, used) over to the caller (a captured graph) and
+  // removes them from the pool.
+  void take(size_t from, std::vector<cudaEvent_t>* evs, std::vector<int>* kinds) {
+    for (size_t i = from; i < used; ++i) {
+      evs->push_back(ev[2 * i]);
+      evs->push_back(ev[2 * i + 1]);
+      kinds->push_back(kind[i]);
+    }
+    ev.resize(2 * from);
+    kind.resize(from);
+    used = from;
+  }
+  void add_pairs(const std::vector<cudaEvent_t>& evs, const std::vector<int>& kinds) {
+    for (size_t i = 0; i < kinds.size(); ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, evs[2 * i], evs[2 * i + 1]) == cudaSuccess) {
+        launches[kinds[i]]++;
+        total_ms[kinds[i]] += ms;
+      } else {
+        cudaGetLastError();
+      }
+    }
   }
   void reset() {
     used = 0;
@@ -177,6 +202,7 @@ struct rf_plan {
   std::vector<uint8_t> ongrid;     // [nbl][nchan]
   std::vector<int32_t> col_ent_ptr, col_cell_ptr, cell_row;
   std::vector<int2> ranges;
+  std::vector<int4> plain_ent;  // {bc, col, row, flags} for the plain form
   std::vector<GridEntry> ent;
   int n_cells = 0, max_cells = 0;
   std::vector<int32_t> ongrid_chan;
@@ -214,6 +240,28 @@ struct rf_plan {
   float2* d_cellbuf = nullptr;
   float* d_colsq = nullptr;     // [slots][ncol] Parseval sums
   float* d_mean0 = nullptr;     // [slots] Re H(0, 0)
+  rf::PlainBuffers plain{};     // allocated on the first plain-form search
+
+  // CUDA graph of the batched wave loop for the current image list
+  bool use_graphs = true;
+  bool graph_pending = false;  // a replay with profiling events awaits collection
+  struct GraphCache {
+    bool valid = false;
+    int nint = -1;
+    bool stats = false;
+    bool prof = false;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> ev;  // profiler event pairs captured in the graph
+    std::vector<int> kind;
+  } graph;
+  cudaStream_t gstream = nullptr;  // private stream: capture and replay
+  cudaEvent_t join[2] = {nullptr, nullptr};
+
+  void drop_graph() {
+    if (graph.exec) cudaGraphExecDestroy(graph.exec);
+    for (cudaEvent_t e : graph.ev) cudaEventDestroy(e);
+    graph = GraphCache();
+  }
 
   std::atomic<int> busy{0};
   Profiler prof;
@@ -243,8 +291,12 @@ struct rf_plan {
   }
 
   ~rf_plan() {
-    if (!allocs.empty() || !prof.ev.empty()) {
+    if (!allocs.empty() || !prof.ev.empty() || gstream) {
       DeviceGuard dg(device);
+      drop_graph();
+      if (gstream) cudaStreamDestroy(gstream);
+      for (cudaEvent_t e : join)
+        if (e) cudaEventDestroy(e);
       for (void* p : allocs) cudaFree(p);
       prof.destroy();
     }
@@ -399,6 +451,9 @@ rf_status build_tables(rf_plan* p) {
   });
   p->ncol = p->n_on > 0 ? p->iu_max + 1 : 1;
   if (!rf::image_kernel_shape(N, &p->shape)) return fail(RF_ERR_INVALID_ARG, "npix %d has no kernel", N);
+  p->plain_ent.clear();
+  p->plain_ent.reserve(es.size());
+  for (const E& e : es) p->plain_ent.push_back(make_int4(e.bc, e.col, e.row, e.flags));
   p->ent.clear();
   p->ent.reserve(es.size());
   p->col_ent_ptr.assign(p->ncol + 1, 0);
@@ -480,6 +535,7 @@ void build_lists(rf_plan* p, int nint) {
   w.img_end = (int)p->img_info.size();
   if (w.img_end > w.img_begin) p->waves.push_back(w);
   p->cached_nint = nint;
+  p->drop_graph();
 }
 
 // (Re)allocate the per-wave scratch for `slots` images (clamped to
@@ -513,6 +569,7 @@ rf_status alloc_wave_scratch(rf_plan* p, int slots) {
   p->slots_max = slots;
   p->gslots_max = std::max(2 * ((slots + B - 1) / B), 1);
   p->cached_nint = -1;
+  p->drop_graph();
   rf_status s;
   if ((s = p->dalloc(&p->d_T, (size_t)slots * per_slot)) != RF_OK) return s;
   if ((s = p->dalloc(&p->d_partials, (size_t)slots * nrb)) != RF_OK) return s;
@@ -705,6 +762,102 @@ rf_status run_waves(rf_plan* p, int nint, const std::vector<Wave>& waves, int ni
   return RF_OK;
 }
 
+// The batched wave loop through a CUDA graph: captured on the plan's
+// private stream the first time an image list is searched (per nint and
+// stats output) and replayed afterwards.  With profiling on, searches use
+// direct launches instead (events in a graph do not time its kernels).  The private
+// stream is ordered after the caller's stream and the caller's stream after
+// the replay, so the call behaves like direct launches on `st`.
+rf_status run_waves_graph(rf_plan* p, int nint, int nimg, DevStat* d_stats, cudaStream_t st) {
+  if (!p->gstream) {
+    RF_CUDA(cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));
+    RF_CUDA(cudaEventCreateWithFlags(&p->join[0], cudaEventDisableTiming));
+    RF_CUDA(cudaEventCreateWithFlags(&p->join[1], cudaEventDisableTiming));
+  }
+  auto& gc = p->graph;
+  const bool want_stats = d_stats != nullptr;
+  if (!(gc.valid && gc.nint == nint && gc.stats == want_stats && gc.prof == p->prof.on)) {
+    p->drop_graph();
+    const size_t u0 = p->prof.used;
+    RF_CUDA(cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal));
+    rf_status s = run_waves(p, nint, p->waves, nimg, d_stats, nullptr, p->gstream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(p->gstream, &g);
+    if (s != RF_OK) {
+      if (g) cudaGraphDestroy(g);
+      p->prof.take(u0, &gc.ev, &gc.kind);
+      p->drop_graph();
+      return s;
+    }
+    if (ec != cudaSuccess) return fail(RF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ec));
+    const cudaError_t ei = cudaGraphInstantiate(&gc.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return fail(RF_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+    p->prof.take(u0, &gc.ev, &gc.kind);
+    gc.valid = true;
+    gc.nint = nint;
+    gc.stats = want_stats;
+    gc.prof = p->prof.on;
+  }
+  RF_CUDA(cudaEventRecord(p->join[0], st));
+  RF_CUDA(cudaStreamWaitEvent(p->gstream, p->join[0], 0));
+  RF_CUDA(cudaGraphLaunch(gc.exec, p->gstream));
+  RF_CUDA(cudaEventRecord(p->join[1], p->gstream));
+  RF_CUDA(cudaStreamWaitEvent(st, p->join[1], 0));
+  p->graph_pending = gc.prof;
+  return RF_OK;
+}
+
+// Plain form buffers, sized for chunks of up to `cap` images within the budget.
+rf_status alloc_plain(rf_plan* p) {
+  if (p->plain.cap > 0) return RF_OK;
+  const size_t N = p->npix;
+  const size_t per = (size_t)p->nbl * p->nchan * sizeof(float2) + N * (N / 2 + 1) * sizeof(float2) +
+                     (N / 2) * N * sizeof(float2) + N * N * sizeof(float) + (N / 2) * sizeof(StatPartial);
+  const int cap = (int)std::max<size_t>(1, std::min<size_t>(kPlainBudgetBytes / per, 4096));
+  rf_status s;
+  rf::PlainBuffers& b = p->plain;
+  if ((s = p->dalloc(&b.R, (size_t)p->nbl * p->nchan * cap)) != RF_OK) return s;
+  if ((s = p->dalloc(&b.grid, (size_t)cap * N * (N / 2 + 1))) != RF_OK) return s;
+  if ((s = p->dalloc(&b.T, (size_t)cap * (N / 2) * N)) != RF_OK) return s;
+  if ((s = p->dalloc(&b.images, (size_t)cap * N * N)) != RF_OK) return s;
+  if ((s = p->dalloc(&b.partials, (size_t)cap * (N / 2))) != RF_OK) return s;
+  int4* d_ent = nullptr;
+  if ((s = p->dalloc(&d_ent, p->plain_ent.size())) != RF_OK) return s;
+  if (!p->plain_ent.empty())
+    RF_CUDA(cudaMemcpy(d_ent, p->plain_ent.data(), p->plain_ent.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  b.S = p->d_S;
+  b.ent = d_ent;
+  b.nent = (int)p->plain_ent.size();
+  b.cap = cap;
+  return RF_OK;
+}
+
+// The plain form: for each (DM, dt) trial, chunks of its images through the
+// unfused launch set.
+rf_status run_plain(rf_plan* p, int nint, DevStat* d_stats, cudaStream_t st) {
+  rf_status s = alloc_plain(p);
+  if (s != RF_OK) return s;
+  const SegmentGeom g = geom(p, nint);
+  const int nimg_total = (int)p->img_info.size();
+  RF_TIMED(p->prof, K_WEIGHTS, st,
+           rf::launch_weights(p->d_img_info, nimg_total, (p->flags & RF_EDGE_PARTIAL) != 0, g, p->tb,
+                              (double)p->n_on, p->d_weight, st));
+  int img0 = 0;
+  for (int d = 0; d < p->ndm; ++d)
+    for (int sdt = 0; sdt < p->ndt; ++sdt) {
+      const int nt = n_times(p, nint, d, sdt);
+      for (int t0 = 0; t0 < nt; t0 += p->plain.cap) {
+        const int nk = std::min(p->plain.cap, nt - t0);
+        RF_TIMED(p->prof, K_PLAIN_TRIAL, st,
+                 rf::launch_plain_chunk(g, p->tb, p->plain, d, sdt, t0, nk, img0, p->d_img_info, p->d_weight,
+                                        p->threshold, p->d_cands, p->d_ncand, p->img_cap, d_stats, st));
+        img0 += nk;
+      }
+    }
+  return RF_OK;
+}
+
 rf_status search_impl(rf_plan* p, const void* vis, int nint, void* stream, rf_candidate* out, size_t cap,
                       size_t* n_out, bool want_stats, rf_image_stat* stats, size_t stats_cap, size_t* n_stats) {
   if (!p) return fail(RF_ERR_INVALID_ARG, "plan is NULL");
@@ -713,7 +866,6 @@ rf_status search_impl(rf_plan* p, const void* vis, int nint, void* stream, rf_ca
   if (!n_out) return fail(RF_ERR_INVALID_ARG, "n_out is NULL");
   if (cap > 0 && !out) return fail(RF_ERR_INVALID_ARG, "out is NULL with cap > 0");
   if (nint < 1 || nint > p->max_nint) return fail(RF_ERR_SHAPE, "nint %d out of [1, %d]", nint, p->max_nint);
-  if (p->form != RF_FORM_BATCHED) return fail(RF_ERR_INVALID_ARG, "search form %d not available", p->form);
   BusyGuard bg(&p->busy);
   if (!bg.owned) return fail(RF_ERR_BUSY, "plan is in use by another call");
   DeviceGuard dg(p->device);
@@ -745,7 +897,12 @@ rf_status search_impl(rf_plan* p, const void* vis, int nint, void* stream, rf_ca
   }
   RF_CUDA(cudaMemsetAsync(p->d_ncand, 0, sizeof(int), st));
   if (nimg > 0) {
-    s = run_waves(p, nint, p->waves, nimg, d_stats, nullptr, st);
+    if (p->form == RF_FORM_PLAIN)
+      s = run_plain(p, nint, d_stats, st);
+    else if (p->use_graphs && !p->prof.on)  // per-kernel event timing needs direct launches
+      s = run_waves_graph(p, nint, nimg, d_stats, st);
+    else
+      s = run_waves(p, nint, p->waves, nimg, d_stats, nullptr, st);
     if (s != RF_OK) return s;
   }
   int ncand = 0;
@@ -762,6 +919,10 @@ rf_status search_impl(rf_plan* p, const void* vis, int nint, void* stream, rf_ca
   }
   RF_CUDA(cudaStreamSynchronize(st));
   p->prof.collect();
+  if (p->graph_pending) {
+    p->prof.add_pairs(p->graph.ev, p->graph.kind);
+    p->graph_pending = false;
+  }
   std::sort(dc.begin(), dc.end(), [](const DevCand& a, const DevCand& b) {
     if (a.d != b.d) return a.d < b.d;
     if (a.s != b.s) return a.s < b.s;
@@ -921,6 +1082,7 @@ rf_status rf_render_images(rf_plan* p, const void* vis, int32_t nint, void* stre
     grp[k] = Group{trials[3 * k], trials[3 * k + 1], trials[3 * k + 2], 1, k, {0, 0, 0}};
   }
   p->cached_nint = -1;  // the lists below replace the cached search lists
+  p->drop_graph();
   RF_CUDA(cudaMemcpyAsync(p->d_img_info, info.data(), n * sizeof(int4), cudaMemcpyHostToDevice, st));
   RF_CUDA(cudaMemcpyAsync(p->d_groups, grp.data(), n * sizeof(Group), cudaMemcpyHostToDevice, st));
   std::vector<Wave> waves;
@@ -979,6 +1141,15 @@ rf_status rf_plan_get_profile(const rf_plan* plan, rf_kernel_profile* out, int32
 
 rf_status rf_plan_set_tuning(rf_plan* p, int32_t key, int64_t value) {
   if (!p) return fail(RF_ERR_INVALID_ARG, "plan is NULL");
+  if (key == RF_TUNE_GRAPHS) {
+    if (value != 0 && value != 1) return fail(RF_ERR_INVALID_ARG, "RF_TUNE_GRAPHS takes 0 or 1");
+    BusyGuard bg(&p->busy);
+    if (!bg.owned) return fail(RF_ERR_BUSY, "plan is in use by another call");
+    DeviceGuard dg(p->device);
+    p->use_graphs = value != 0;
+    p->drop_graph();
+    return RF_OK;
+  }
   if (key != RF_TUNE_WAVE_IMAGES) return fail(RF_ERR_INVALID_ARG, "unknown tuning key %d", key);
   if (p->host_only) return fail(RF_ERR_INVALID_ARG, "plan was created with RF_HOST_ONLY");
   if (value < p->shape.images_per_group || value > 32768)
@@ -990,8 +1161,106 @@ rf_status rf_plan_set_tuning(rf_plan* p, int32_t key, int64_t value) {
   return alloc_wave_scratch(p, (int)value);
 }
 
+rf_status rf_plan_autotune(rf_plan* p, const void* vis, int32_t nint, void* stream, rf_tune_report* report) {
+  if (!p) return fail(RF_ERR_INVALID_ARG, "plan is NULL");
+  if (p->host_only) return fail(RF_ERR_INVALID_ARG, "plan was created with RF_HOST_ONLY");
+  if (!vis) return fail(RF_ERR_INVALID_ARG, "vis is NULL");
+  if (nint < 1 || nint > p->max_nint) return fail(RF_ERR_SHAPE, "nint %d out of [1, %d]", nint, p->max_nint);
+  DeviceGuard dg(p->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t nimg = count_images(p, nint);
+  const int B = p->shape.images_per_group;
+  const size_t per_slot = (size_t)p->ncol * p->npix * sizeof(float2);
+  size_t free_b = 0, total_b = 0;
+  RF_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const size_t have = free_b / 2 + (size_t)p->slots_max * per_slot;  // the current scratch is reusable
+  std::vector<int> ladder;
+  for (int w : {256, 512, 1024, 2048, 4096, 8192}) {
+    const int wc = std::max(w, B);
+    if ((size_t)wc * per_slot > have) continue;
+    if (!ladder.empty() && ladder.back() >= nimg) break;
+    ladder.push_back(wc);
+  }
+  if (ladder.empty()) ladder.push_back(p->slots_max);
+  const bool prof_was = p->prof.on;
+  p->prof.on = false;
+  cudaEvent_t e0, e1;
+  RF_CUDA(cudaEventCreate(&e0));
+  RF_CUDA(cudaEventCreate(&e1));
+  std::vector<rf_candidate> scratch_out(1);
+  float best_ms = 1e30f;
+  int best_w = p->slots_max, best_g = p->use_graphs ? 1 : 0, ntried = 0;
+  rf_status s = RF_OK;
+  for (int w : ladder) {
+    for (int gmode = 1; gmode >= 0 && s == RF_OK; --gmode) {
+      {
+        BusyGuard bg(&p->busy);
+        if (!bg.owned) {
+          s = fail(RF_ERR_BUSY, "plan is in use by another call");
+          break;
+        }
+        if (p->slots_max != w) s = alloc_wave_scratch(p, w);
+        p->use_graphs = gmode != 0;
+        p->drop_graph();
+      }
+      if (s != RF_OK) break;
+      size_t n_out = 0;
+      rf_status r = search_impl(p, vis, nint, stream, scratch_out.data(), 0, &n_out, false, nullptr, 0, nullptr);
+      if (r != RF_OK && r != RF_ERR_CAPACITY) {
+        s = r;
+        break;
+      }
+      cudaEventRecord(e0, st);
+      r = search_impl(p, vis, nint, stream, scratch_out.data(), 0, &n_out, false, nullptr, 0, nullptr);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      if (r != RF_OK && r != RF_ERR_CAPACITY) {
+        s = r;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ntried < 16 && report) {
+        report->tried_wave_images[ntried] = w;
+        report->tried_graphs[ntried] = gmode;
+        report->tried_ms[ntried] = ms;
+      }
+      ++ntried;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_w = w;
+        best_g = gmode;
+      }
+    }
+    if (s != RF_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->prof.on = prof_was;
+  if (s != RF_OK) return s;
+  {
+    BusyGuard bg(&p->busy);
+    if (p->slots_max != best_w) {
+      s = alloc_wave_scratch(p, best_w);
+      if (s != RF_OK) return s;
+    }
+    p->use_graphs = best_g != 0;
+    p->drop_graph();
+  }
+  if (report) {
+    report->best_wave_images = best_w;
+    report->best_graphs = best_g;
+    report->ntried = std::min(ntried, 16);
+  }
+  return RF_OK;
+}
+
 rf_status rf_plan_get_tuning(const rf_plan* p, int32_t key, int64_t* value) {
   if (!p || !value) return fail(RF_ERR_INVALID_ARG, "NULL argument");
+  if (key == RF_TUNE_GRAPHS) {
+    *value = p->use_graphs ? 1 : 0;
+    return RF_OK;
+  }
   if (key != RF_TUNE_WAVE_IMAGES) return fail(RF_ERR_INVALID_ARG, "unknown tuning key %d", key);
   *value = p->slots_max;
   return RF_OK;

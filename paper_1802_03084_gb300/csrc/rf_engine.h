@@ -132,6 +132,27 @@ cudaError_t launch_finalize(const SegmentGeom& g, const StatPartial* partials, c
                             double threshold, DevCand* cands, int* ncand, int cand_cap, DevStat* stats,
                             cudaStream_t st);
 
+// Buffers of the plain per-trial form (chunks of up to `cap` images).
+struct PlainBuffers {
+  const void* S;          // Stokes-I time series (as for the batched form)
+  float2* R;              // [nbl * nchan][cap] dedispersed, resampled
+  float2* grid;           // [cap][N][N/2 + 1] dense half planes
+  float2* T;              // [cap][N/2][N] column-FFT output
+  float* images;          // [cap][N][N]
+  StatPartial* partials;  // [cap][N/2] (row pass output, unused)
+  const int4* ent;        // [nent] {bc, col, row, flags}
+  int nent;
+  int cap;
+};
+
+// One unfused launch set for images [img0, img0 + nk) = t' t0 .. t0+nk-1 of
+// trial (d, s): dedisperse, grid (atomics), column FFTs, row FFTs writing the
+// images, image statistics read back from HBM.
+cudaError_t launch_plain_chunk(const SegmentGeom& g, const DevTables& tb, const PlainBuffers& pb, int d, int s,
+                               int t0, int nk, int img0, const int4* img_info, const double* weight,
+                               double threshold, DevCand* cands, int* ncand, int cand_cap, DevStat* stats,
+                               cudaStream_t st);
+
 // Compile-time layout facts per image size, for host-side sizing.
 struct ImageKernelShape {
   int images_per_group;   // B

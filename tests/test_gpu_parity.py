@@ -169,3 +169,68 @@ def test_single_channel_single_integration():
         oc, ost = oracle.search_segment(op, seg["vis"], with_stats=True)
         compare_stats(gst, ost, oracle_images(op, seg["vis"], list(ost)))
         compare_candidates(gc, oc, spec.threshold, ost)
+
+
+def _disagreeing(gst, ost):
+    return [(int(r["dm_idx"]), int(r["dt_idx"]), int(r["t_idx"])) for r in gst
+            if (int(r["x"]), int(r["y"])) != (ost[(int(r["dm_idx"]), int(r["dt_idx"]), int(r["t_idx"]))].x,
+                                               ost[(int(r["dm_idx"]), int(r["dt_idx"]), int(r["t_idx"]))].y)]
+
+
+def test_plain_form_matches_oracle(tiny):
+    spec, seg, _, op, ocands, ost = tiny
+    gp, _ = plans_for(spec, seg)
+    with gp:
+        gp.set_form(rf.RF_FORM_PLAIN)
+        gc, gst = gp.search_stats(seg["vis"])
+        dis = _disagreeing(gst, ost)
+        compare_stats(gst, ost, oracle_images(op, seg["vis"], dis) if dis else None)
+        compare_candidates(gc, ocands, spec.threshold, ost)
+
+
+def test_plain_form_random_shape():
+    rng = np.random.default_rng(77)
+    seg = small_random_segment(rng, 7, 9, 37, 128)
+    umax = 600.0 * seg["freq_hz"].max() / oracle.C_LIGHT
+    spec = synth.SegmentSpec(name="rand", nchan=9, f_lo_hz=1e9, bw_hz=1e9, nint=37, inttime_s=2e-3, npix=128,
+                             dm_list=np.linspace(0, 30.0, 4), dt_list=[1, 3], threshold=3.0, nant=7,
+                             cell_rad=0.45 / umax, edge="partial")
+    gp, op = plans_for(spec, seg)
+    with gp:
+        gp.set_form(rf.RF_FORM_PLAIN)
+        gc, gst = gp.search_stats(seg["vis"])
+        oc, ost = oracle.search_segment(op, seg["vis"], with_stats=True)
+        gst = gst[gst["weight"] > 0]
+        compare_stats(gst, ost, oracle_images(op, seg["vis"], list(ost)))
+        compare_candidates(gc, oc, spec.threshold, ost)
+
+
+def test_graph_replay_equals_direct_launches(tiny):
+    spec, seg, _, op, _, _ = tiny
+    gp, _ = plans_for(spec, seg)
+    with gp:
+        c_graph, s_graph = gp.search_stats(seg["vis"])
+        c_graph2, s_graph2 = gp.search_stats(seg["vis"])        # replay
+        _, s_short = gp.search_stats(seg["vis"][:64].copy())     # new image list: re-captured
+        c_graph3, s_graph3 = gp.search_stats(seg["vis"])
+        gp.set_graphs(False)
+        c_direct, s_direct = gp.search_stats(seg["vis"])
+        for s_ in (s_graph2, s_graph3, s_direct):
+            assert np.array_equal(s_graph, s_)
+        for c_ in (c_graph2, c_graph3, c_direct):
+            assert np.array_equal(c_graph, c_)
+        assert len(s_short) == 8 * 64
+
+
+def test_autotune_keeps_results(tiny, tmp_path):
+    spec, seg, _, op, _, _ = tiny
+    gp, _ = plans_for(spec, seg)
+    with gp:
+        c0, s0 = gp.search_stats(seg["vis"])
+        cache = str(tmp_path / "tune.json")
+        res = gp.autotune(seg["vis"], cache_path=cache)
+        assert res["cached"] is False and res["wave_images"] >= 32 and len(res["tried"]) >= 2
+        c1, s1 = gp.search_stats(seg["vis"])
+        assert np.array_equal(s0, s1) and np.array_equal(c0, c1)
+        again = gp.autotune(seg["vis"], cache_path=cache)
+        assert again["cached"] is True and again["wave_images"] == res["wave_images"]
