@@ -170,6 +170,14 @@ typedef struct rf_plan_info {
  */
 rf_status rf_plan_create(const rf_plan_desc* desc, struct rf_plan** out);
 
+/*
+ * rf_plan_estimate_bytes: the device memory rf_plan_create(desc) would
+ * allocate, with column-FFT scratch for `wave_images` images per wave
+ * (0 = the default), without touching the device.  Used for admission by
+ * memory.  Errors: as rf_plan_create's validation.
+ */
+rf_status rf_plan_estimate_bytes(const rf_plan_desc* desc, int64_t wave_images, uint64_t* bytes);
+
 /* rf_plan_destroy: free everything the plan owns.  NULL is accepted.  The
  * caller must not have work in flight on the plan. */
 rf_status rf_plan_destroy(struct rf_plan* plan);
@@ -323,6 +331,60 @@ rf_status rf_plan_get_profile(const struct rf_plan* plan, rf_kernel_profile* out
 #define RF_NOALLOC_MAX_NPIX 1024
 rf_status rf_image_stats_noalloc(const void* half_plane, int32_t npix, double weight, void* stream,
                                  rf_image_stat* stat);
+
+/* ---- serving --------------------------------------------------------
+ * A server keeps plans resident on one device and searches segments as they
+ * arrive (Sec. 3.2: segments are independent and are processed as they are
+ * read; the state of each is fixed by its metadata and preferences).  Each
+ * of `slots` workers runs one segment at a time on its own CUDA stream, so
+ * segments admitted together overlap on the device.  Admission is in
+ * arrival order: the oldest waiting segment starts when a worker is free and
+ * its plan is resident and idle, or a new plan for it fits in the HBM budget
+ * (idle resident plans are evicted least-recently-used first).
+ */
+typedef struct rf_server_desc {
+  int32_t device;            /* CUDA device ordinal                          */
+  int32_t slots;             /* segments in flight at once, 1 .. 16          */
+  uint64_t hbm_budget_bytes; /* device memory the server's plans may hold     */
+  int64_t wave_images;       /* RF_TUNE_WAVE_IMAGES for its plans (0 = default) */
+} rf_server_desc;
+
+/* Outcome and timing of one request; times in seconds since the server
+ * was created (steady clock). */
+typedef struct rf_request_info {
+  int32_t status;     /* rf_status of the search (valid once done)          */
+  int32_t done;       /* 1 when the search has finished                     */
+  double submit_s;    /* when rf_server_submit accepted it                  */
+  double start_s;     /* when a worker started it                           */
+  double done_s;      /* when its candidates were on the host               */
+  int64_t n_images;   /* images searched                                    */
+  uint64_t n_candidates;
+  int32_t plan_reused; /* 1 if a resident plan was used                     */
+} rf_request_info;
+
+rf_status rf_server_create(const rf_server_desc* desc, struct rf_server** out);
+
+/* Queue one segment.  `desc` is copied (max_nint is taken as the plan's);
+ * `vis` (host or device, layout as for rf_search_segment) must stay valid
+ * and unchanged until the request is done.  *ticket identifies it.
+ * Errors: RF_ERR_INVALID_ARG, RF_ERR_SHAPE (nint > desc->max_nint),
+ * RF_ERR_NO_MEMORY (the plan cannot fit in the budget at all). */
+rf_status rf_server_submit(struct rf_server* server, const rf_plan_desc* desc, const void* vis, int32_t nint,
+                           int64_t* ticket);
+
+/* Wait up to timeout_ms (negative: no limit) for the request to finish and
+ * fill `info`.  Returns RF_ERR_TIMEOUT if it is still running (info then
+ * has done = 0), RF_ERR_INVALID_ARG for an unknown ticket. */
+rf_status rf_server_wait(struct rf_server* server, int64_t ticket, int32_t timeout_ms, rf_request_info* info);
+
+/* Copy the candidates of a finished request (sorted as rf_search_segment)
+ * and forget the request.  If n_out > cap the first cap are written and
+ * RF_ERR_CAPACITY is returned (the request is kept). */
+rf_status rf_server_results(struct rf_server* server, int64_t ticket, rf_candidate* out, size_t cap,
+                            size_t* n_out);
+
+/* Finish all queued work, then free the server and its plans. */
+rf_status rf_server_destroy(struct rf_server* server);
 
 /* Library version string. */
 const char* rf_version(void);

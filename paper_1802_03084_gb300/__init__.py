@@ -25,7 +25,7 @@ __all__ = [
     "rf_search_segment_stats", "rf_render_images", "rf_plan_set_form", "rf_plan_get_info",
     "rf_plan_delays", "rf_plan_cells", "rf_count_images", "rf_last_error", "rf_version",
     "rf_plan_set_profiling", "rf_plan_get_profile", "RfKernelProfile", "rf_image_stats_noalloc", "rf_plan_set_tuning", "rf_plan_get_tuning", "rf_plan_autotune",
-    "RfTuneReport",
+    "RfTuneReport", "Server", "RfServerDesc", "RfRequestInfo", "rf_plan_estimate_bytes",
     "Plan", "CANDIDATE_DTYPE", "STAT_DTYPE", "declared_symbols",
     "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
 ]
@@ -104,6 +104,17 @@ class RfTuneReport(ctypes.Structure):
                 ("tried_ms", ctypes.c_float * 16)]
 
 
+class RfServerDesc(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("slots", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_uint64),
+                ("wave_images", ctypes.c_int64)]
+
+
+class RfRequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("done", ctypes.c_int32), ("submit_s", ctypes.c_double),
+                ("start_s", ctypes.c_double), ("done_s", ctypes.c_double), ("n_images", ctypes.c_int64),
+                ("n_candidates", ctypes.c_uint64), ("plan_reused", ctypes.c_int32)]
+
+
 class RfKernelProfile(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -152,6 +163,14 @@ def lib() -> ctypes.CDLL:
         "rf_plan_get_tuning": ([P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "rf_image_stats_noalloc": ([P, ctypes.c_int32, ctypes.c_double, P, P], ctypes.c_int),
         "rf_plan_autotune": ([P, P, ctypes.c_int32, P, ctypes.POINTER(RfTuneReport)], ctypes.c_int),
+        "rf_plan_estimate_bytes": ([ctypes.POINTER(RfPlanDesc), ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)],
+                                   ctypes.c_int),
+        "rf_server_create": ([ctypes.POINTER(RfServerDesc), ctypes.POINTER(P)], ctypes.c_int),
+        "rf_server_submit": ([P, ctypes.POINTER(RfPlanDesc), P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)],
+                             ctypes.c_int),
+        "rf_server_wait": ([P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(RfRequestInfo)], ctypes.c_int),
+        "rf_server_results": ([P, ctypes.c_int64, P, S, ctypes.POINTER(S)], ctypes.c_int),
+        "rf_server_destroy": ([P], ctypes.c_int),
         "rf_plan_get_profile": ([P, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -339,6 +358,59 @@ def rf_plan_autotune(plan, vis, nint: int, stream=None) -> dict:
 def rf_image_stats_noalloc(half_plane, npix: int, weight: float, stat, stream=None) -> None:
     """Image one device half plane into the device rf_image_stat `stat` (no allocation)."""
     _check(lib().rf_image_stats_noalloc(_ptr(half_plane), npix, weight, _stream(stream), _ptr(stat)))
+
+
+def rf_plan_estimate_bytes(desc: RfPlanDesc, wave_images: int = 0) -> int:
+    b = ctypes.c_uint64()
+    _check(lib().rf_plan_estimate_bytes(ctypes.byref(desc), wave_images, ctypes.byref(b)))
+    return int(b.value)
+
+
+class Server:
+    """Serving runtime: resident plans, admission by HBM budget, `slots`
+    segments in flight on their own streams (rf_server_* in the C ABI)."""
+
+    def __init__(self, device=0, slots=2, hbm_budget_bytes=64 << 30, wave_images=0):
+        self.desc = RfServerDesc(device=device, slots=slots, hbm_budget_bytes=hbm_budget_bytes,
+                                 wave_images=wave_images)
+        self.handle = ctypes.c_void_p()
+        _check(lib().rf_server_create(ctypes.byref(self.desc), ctypes.byref(self.handle)))
+        self._keep = {}
+
+    def submit(self, desc: RfPlanDesc, vis, nint: int) -> int:
+        """Queue a segment; `vis` (and `desc`'s arrays) are kept alive until results() is called."""
+        t = ctypes.c_int64()
+        _check(lib().rf_server_submit(self.handle, ctypes.byref(desc), _ptr(vis), nint, ctypes.byref(t)))
+        self._keep[t.value] = (desc, vis)
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> dict:
+        info = RfRequestInfo()
+        st = lib().rf_server_wait(self.handle, ticket, timeout_ms, ctypes.byref(info))
+        if st not in (RF_OK, RF_ERR_TIMEOUT):
+            raise RfError(st, rf_last_error())
+        return {f: getattr(info, f) for f, _ in RfRequestInfo._fields_}
+
+    def results(self, ticket: int) -> np.ndarray:
+        info = self.wait(ticket)
+        cap = max(int(info["n_candidates"]), 1)
+        out = np.zeros(cap, dtype=CANDIDATE_DTYPE)
+        n = ctypes.c_size_t()
+        _check(lib().rf_server_results(self.handle, ticket, out.ctypes.data, cap, ctypes.byref(n)))
+        self._keep.pop(ticket, None)
+        return out[:n.value]
+
+    def close(self):
+        if self.handle:
+            _check(lib().rf_server_destroy(self.handle))
+            self.handle = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Plan:

@@ -579,6 +579,42 @@ rf_status alloc_wave_scratch(rf_plan* p, int slots) {
   return RF_OK;
 }
 
+// Device bytes alloc_device will allocate for a plan whose host tables are
+// built, with column-FFT scratch for `slots` images (0 = the default
+// budget).  Mirrors alloc_device and alloc_wave_scratch.
+uint64_t estimate_device_bytes(const rf_plan* p, int slots) {
+  const size_t N = p->npix;
+  auto r = [](size_t n, size_t sz) { return (uint64_t)std::max<size_t>(n, 1) * sz; };
+  uint64_t b = 0;
+  b += r(p->delays.size(), 4) + r(p->dt.size(), 4) + r(p->ranges.size(), 8) + r(p->col_cell_ptr.size(), 4) +
+       r(p->cell_row.size(), 4) + r(p->ent.size(), sizeof(GridEntry)) + r(p->ongrid_chan.size(), 4) + r(N, 8);
+  const size_t nint_pad = (p->max_nint + 31) / 32 * 32;
+  const size_t esz = (p->flags & RF_STORE_FP16) ? 4 : 8;
+  const size_t rows = (size_t)p->nbl * p->nchan;
+  b += r(rows * nint_pad, esz);
+  std::vector<int> seen;
+  for (int dt : p->dt) {
+    if (dt == 1 || std::find(seen.begin(), seen.end(), dt) != seen.end()) continue;
+    seen.push_back(dt);
+    b += r(rows * dt * ((nint_pad + dt - 1) / dt), esz);
+  }
+  b += r(p->dt.size(), 8) + r(p->dt.size(), 4);
+  const int64_t img_cap = std::max<int64_t>(count_images(p, p->max_nint), 1);
+  b += r(img_cap, sizeof(int4)) + r(img_cap, sizeof(Group)) + r(img_cap, 8) + r(img_cap, sizeof(DevCand)) + 4;
+  const size_t per_slot = (size_t)p->ncol * N * sizeof(float2);
+  if (slots <= 0) slots = (int)std::min<size_t>(kTBudgetBytes / per_slot, (size_t)img_cap);
+  const int B = p->shape.images_per_group;
+  slots = std::max(std::min(slots, 32768), B);
+  const int gslots = std::max(2 * ((slots + B - 1) / B), 1);
+  b += r((size_t)slots * per_slot, 1) + r((size_t)slots * p->shape.partials_per_image, sizeof(StatPartial)) +
+       r((size_t)gslots * std::max(p->n_cells, 1) * 32, sizeof(float2)) + r((size_t)slots * p->ncol, 4) +
+       r(slots, 4);
+  const size_t per_int = rows * p->npol * sizeof(float2);
+  const size_t stage_nint = std::max<size_t>(1, std::min<size_t>(kStageBytes / per_int, (size_t)p->max_nint));
+  b += r(stage_nint * per_int, 1);
+  return b;
+}
+
 rf_status alloc_device(rf_plan* p) {
   const int N = p->npix;
   auto up = [&](auto** dst, const auto& vec) -> rf_status {
@@ -1033,6 +1069,31 @@ rf_status rf_plan_create(const rf_plan_desc* desc, rf_plan** out) {
     }
   }
   *out = p;
+  return RF_OK;
+}
+
+rf_status rf_plan_estimate_bytes(const rf_plan_desc* desc, int64_t wave_images, uint64_t* bytes) {
+  if (!bytes) return fail(RF_ERR_INVALID_ARG, "bytes is NULL");
+  rf_status s = validate(desc);
+  if (s != RF_OK) return s;
+  rf_plan tmp;
+  tmp.nant = desc->nant;
+  tmp.nchan = desc->nchan;
+  tmp.npol = desc->npol;
+  tmp.npix = desc->npix;
+  tmp.ndm = desc->ndm;
+  tmp.ndt = desc->ndt;
+  tmp.max_nint = desc->max_nint;
+  tmp.flags = desc->flags;
+  tmp.inttime = desc->inttime_s;
+  tmp.cell = desc->cell_rad;
+  tmp.ant_uvw.assign(desc->ant_uvw_m, desc->ant_uvw_m + 3 * desc->nant);
+  tmp.freq.assign(desc->freq_hz, desc->freq_hz + desc->nchan);
+  tmp.dm.assign(desc->dm_list, desc->dm_list + desc->ndm);
+  tmp.dt.assign(desc->dt_list, desc->dt_list + desc->ndt);
+  s = build_tables(&tmp);
+  if (s != RF_OK) return s;
+  *bytes = estimate_device_bytes(&tmp, (int)std::min<int64_t>(std::max<int64_t>(wave_images, 0), 32768));
   return RF_OK;
 }
 

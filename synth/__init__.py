@@ -16,5 +16,6 @@ from .segments import (  # noqa: F401
     dm_grid_linear,
     dm_grid_smearing,
     make_segment,
+    serving_shapes,
     CONFIG_NAMES,
 )

@@ -137,3 +137,14 @@ def test_zero_images_when_segment_shorter_than_sweep(L):
         d = p.delays().max(axis=1)
         n = sum(max(0, (300 - m) // dt) if 300 - m > 0 else 0 for m in d for dt in spec.dt_list)
         assert p.count_images(300) == n
+
+
+def test_estimate_bytes_without_device(L):
+    spec = synth.config("realtime")
+    kw = _desc_kwargs(spec)
+    kw["flags"] = 0
+    b = rf.rf_plan_estimate_bytes(rf.make_desc(**kw))
+    # Stokes I (FP32) alone is 351 x 256 x 1024 x 8 bytes
+    assert b > 351 * 256 * 1024 * 8
+    b_small = rf.rf_plan_estimate_bytes(rf.make_desc(**kw), wave_images=64)
+    assert b_small < b
