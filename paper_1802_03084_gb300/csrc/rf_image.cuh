@@ -43,6 +43,7 @@ struct ImgCfg {
   static constexpr int B = 32;                                   // images per group
   static constexpr int XA = cmin(THREADS_A / T, B);              // transforms per round
   static constexpr int CELL_PITCH = 33;                          // cell values per cell row (32 + pad)
+  static constexpr int PART_IMAGES = N >= 2048 ? 16 : 32;        // images whose cells are staged at once
   static constexpr int SMEM_A_FIXED = XA * fft_stride<N>() * 8;
   // pass B: XB row pairs (RB rows) per work item; the column-FFT tile of the
   // next item is prefetched while the current one is transformed
@@ -89,78 +90,82 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_A, 2)
              const float2* __restrict__ cellbuf, float2* __restrict__ Tbuf, float* __restrict__ colsq,
              float* __restrict__ mean0) {
   using K = ImgCfg<N>;
+  constexpr int PI = K::PART_IMAGES;  // images staged at a time
+  constexpr int CPC = PI / 2;         // 16-byte chunks per cell row
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* fbuf = reinterpret_cast<float2*>(smraw);                     // [XA][STRIDE]
-  float2* cellv = fbuf + K::XA * K::STRIDE;                             // [max_cells][32], swizzled
-  int* crow = reinterpret_cast<int*>(cellv + (size_t)g.max_cells * 32);  // [max_cells]
+  float2* cellv = fbuf + K::XA * K::STRIDE;                             // [max_cells][PI], swizzled
+  int* crow = reinterpret_cast<int*>(cellv + (size_t)g.max_cells * PI);  // [max_cells]
   const int tid = threadIdx.x;
+  const int lane = tid & 31;
   const Group gr = groups[g_begin + blockIdx.x];
   const int col = blockIdx.y;
   const int cell0 = tb.col_cell_ptr[col];
   const int ncells = tb.col_cell_ptr[col + 1] - cell0;
   const float2* __restrict__ src = cellbuf + ((size_t)blockIdx.x * g.ncells + cell0) * 32;
-  for (int i = tid; i < ncells * 16; i += K::THREADS_A) {
-    const int c = i >> 4;
-    const int j = i & 15;
-    cp_async16(cellv + c * 32 + 2 * (j ^ (c & 15)), src + c * 32 + 2 * j);
-  }
-  cp_async_commit();
   for (int c = tid; c < ncells; c += K::THREADS_A) crow[c] = tb.cell_row[cell0 + c];
-  cp_async_wait_all();
-  __syncthreads();
-
-  // Parseval: the image's sum of squares is N^2 / (4 W^2) times the sum of
-  // |G|^2 over the full Hermitian plane, which counts this column twice
-  // unless u = 0; its mean is G(0, 0) / (2 W).  Each warp sums |H|^2 of the
-  // column's cells for some of the images (FP32, fixed order).
-  {
-    const int lane = tid & 31;
-    const float wcol = col == 0 ? 1.f : 2.f;
-    for (int k = tid >> 5; k < gr.nimg; k += K::THREADS_A / 32) {
-      const int kc = k >> 1;
-      const int ko = k & 1;
-      float acc = 0.f;
-      for (int c = lane; c < ncells; c += 32) {
-        const float2 h = cellv[c * 32 + 2 * (kc ^ (c & 15)) + ko];
-        acc = fmaf(h.x, h.x, fmaf(h.y, h.y, acc));
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-      if (lane == 0) {
-        const size_t slot = (size_t)(gr.img0 + k - img_base);
-        colsq[slot * g.ncol + col] = wcol * acc;
-        if (col == 0) mean0[slot] = (ncells > 0 && crow[0] == 0) ? cellv[k].x : 0.f;  // cell 0 is unswizzled
-      }
-    }
-  }
-
   const int xf = tid / K::T;
   const int t = tid - xf * K::T;
-  if (xf < K::XA) {
-    float2* buf = fbuf + xf * K::STRIDE;
-    const int nrounds = (gr.nimg + K::XA - 1) / K::XA;
-    for (int rd = 0; rd < nrounds; ++rd) {
-      const int k = rd * K::XA + xf;
-      for (int i = t; i < K::STRIDE; i += K::T) buf[i] = make_float2(0.f, 0.f);
-      fft_sync<K::T>(xf);
-      if (k < gr.nimg) {
-        const int kc = k >> 1;
-        const int ko = k & 1;
-        for (int c = t; c < ncells; c += K::T) buf[padx(crow[c])] = cellv[c * 32 + 2 * (kc ^ (c & 15)) + ko];
-      }
-      fft_sync<K::T>(xf);
-      float2 v[K::E];
-      fft_inverse_to_regs<N>(v, buf, tb.twiddle, t, xf);
-      if (k < gr.nimg) {
-        const size_t slot = (size_t)(gr.img0 + k - img_base);
-        float2* dst = Tbuf + (slot * g.ncol + col) * N;
-        constexpr int LP = FftShape<N>::LAST_P;
+  float2* buf = fbuf + xf * K::STRIDE;
+  for (int kbase = 0; kbase < gr.nimg; kbase += PI) {
+    if (kbase > 0) __syncthreads();  // the previous part's cells are consumed
+    for (int i = tid; i < ncells * CPC; i += K::THREADS_A) {
+      const int c = i / CPC;
+      const int j = i - c * CPC;
+      cp_async16(cellv + c * PI + 2 * (j ^ (c & (CPC - 1))), src + c * 32 + kbase + 2 * j);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    const int nk = min(PI, gr.nimg - kbase);
+
+    // Parseval: the image's sum of squares is N^2 / (4 W^2) times the sum
+    // of |G|^2 over the full Hermitian plane, which counts this column
+    // twice unless u = 0; its mean is G(0, 0) / (2 W).  Each warp sums
+    // |H|^2 of the column's cells for some of the images (FP32, fixed order).
+    {
+      const float wcol = col == 0 ? 1.f : 2.f;
+      for (int kl = tid >> 5; kl < nk; kl += K::THREADS_A / 32) {
+        float acc = 0.f;
+        for (int c = lane; c < ncells; c += 32) {
+          const float2 h = cellv[c * PI + 2 * ((kl >> 1) ^ (c & (CPC - 1))) + (kl & 1)];
+          acc = fmaf(h.x, h.x, fmaf(h.y, h.y, acc));
+        }
 #pragma unroll
-        for (int m = 0; m < K::E / LP; ++m)
-#pragma unroll
-          for (int q = 0; q < LP; ++q) dst[fft_out_index<N>(t, m, q)] = v[m * LP + dft_perm<LP>(q)];
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) {
+          const size_t slot = (size_t)(gr.img0 + kbase + kl - img_base);
+          colsq[slot * g.ncol + col] = wcol * acc;
+          if (col == 0) mean0[slot] = (ncells > 0 && crow[0] == 0) ? cellv[kl].x : 0.f;  // cell 0 unswizzled
+        }
       }
-      fft_sync<K::T>(xf);
+    }
+
+    if (xf < K::XA) {
+      const int nrounds = (nk + K::XA - 1) / K::XA;
+      for (int rd = 0; rd < nrounds; ++rd) {
+        const int kl = rd * K::XA + xf;
+        for (int i = t; i < K::STRIDE; i += K::T) buf[i] = make_float2(0.f, 0.f);
+        fft_sync<K::T>(xf);
+        if (kl < nk) {
+          const int kc = kl >> 1;
+          const int ko = kl & 1;
+          for (int c = t; c < ncells; c += K::T) buf[padx(crow[c])] = cellv[c * PI + 2 * (kc ^ (c & (CPC - 1))) + ko];
+        }
+        fft_sync<K::T>(xf);
+        float2 v[K::E];
+        fft_inverse_to_regs<N>(v, buf, tb.twiddle, t, xf);
+        if (kl < nk) {
+          const size_t slot = (size_t)(gr.img0 + kbase + kl - img_base);
+          float2* dst = Tbuf + (slot * g.ncol + col) * N;
+          constexpr int LP = FftShape<N>::LAST_P;
+#pragma unroll
+          for (int m = 0; m < K::E / LP; ++m)
+#pragma unroll
+            for (int q = 0; q < LP; ++q) dst[fft_out_index<N>(t, m, q)] = v[m * LP + dft_perm<LP>(q)];
+        }
+        fft_sync<K::T>(xf);
+      }
     }
   }
 }
@@ -367,7 +372,7 @@ cudaError_t run_colfft(const SegmentGeom& g, const DevTables& tb, const Group* g
                        int img_base, const float2* cellbuf, float2* Tbuf, float* colsq, float* mean0,
                        cudaStream_t st) {
   using K = ImgCfg<N>;
-  const int smem = K::SMEM_A_FIXED + g.max_cells * (32 * 8 + 4);
+  const int smem = K::SMEM_A_FIXED + g.max_cells * (K::PART_IMAGES * 8 + 4);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_colfft<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
