@@ -24,4 +24,5 @@ from .realfast_oracle import (  # noqa: F401
     round_half_away,
     search_segment,
     stokes_i,
+    subtract_mean,
 )

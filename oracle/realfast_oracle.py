@@ -129,6 +129,15 @@ def stokes_i(vis: np.ndarray) -> np.ndarray:
     return v.astype(np.complex128).mean(axis=3)
 
 
+def subtract_mean(S: np.ndarray, nint: Optional[int] = None) -> np.ndarray:
+    """Mean-visibility subtraction (Sec. 3.1): the mean over the segment's
+    integrations of every (baseline, channel) is removed, so sources that
+    are constant over the segment (shorter than the fringe-rate time scale,
+    Sec. 3.2) vanish.  S: [nint, nbl, nchan]; returns a new array."""
+    n = S.shape[0] if nint is None else nint
+    return S - S[:n].mean(axis=0, keepdims=True)
+
+
 def dedisperse_resample(S: np.ndarray, delays_d: np.ndarray, dt: int, t: int, nint: Optional[int] = None):
     """R[b,c] = sum_{j<dt} S[t*dt + j + delta[c]][b, c] and n[c] = samples present.
 
@@ -245,6 +254,7 @@ class OraclePlan:
     threshold: float
     edge: str = EDGE_FULL
     npol: int = 2
+    mean_subtract: bool = False
 
     def __post_init__(self):
         self.bl_uvw = baseline_uvw(self.ant_uvw)
@@ -275,6 +285,12 @@ class OraclePlan:
         """W = sum over on-grid (b, c) of the samples summed into R[b, c]."""
         return float((self.ongrid.sum(axis=0) * n).sum())
 
+    def stokes(self, vis: np.ndarray, nint: Optional[int] = None) -> np.ndarray:
+        """Stokes I of the segment, mean-subtracted if the plan says so."""
+        n = vis.shape[0] if nint is None else nint
+        S = stokes_i(vis[:n])
+        return subtract_mean(S, n) if self.mean_subtract else S
+
     def image(self, S: np.ndarray, d: int, s: int, t: int, nint: Optional[int] = None, method: str = "fft"):
         """Dirty image of trial (d, s, t') and its weight W (None if W = 0)."""
         R, n = dedisperse_resample(S, self.delays[d], int(self.dt_list[s]), t, nint)
@@ -301,7 +317,7 @@ def search_segment(plan: OraclePlan, vis: np.ndarray, nint: Optional[int] = None
     ``with_stats``, a dict (d, s, t) -> ImageStats for every imaged trial.
     """
     n = vis.shape[0] if nint is None else nint
-    S = stokes_i(vis[:n])
+    S = plan.stokes(vis, n)
     todo = plan.image_list(n) if images is None else list(images)
     cands, stats = [], {}
     for (d, s, t) in todo:

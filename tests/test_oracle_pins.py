@@ -361,3 +361,28 @@ def test_noise_only_image_statistics():
     assert 0.8 < st.sigma / expect < 1.2
     assert abs(st.mean) < 1e-12          # no visibility on the (0,0) cell
     assert st.snr < 6.0
+
+
+def test_mean_subtraction_removes_a_constant_source_and_keeps_a_pulse():
+    # Sec. 3.1: a source constant over the segment vanishes; a pulse keeps all
+    # but 1/nint of its amplitude per sample it occupies.
+    spec = synth.config("tiny")
+    spec.pulses = []
+    spec.continuum = [dict(amp=5.0, x=100, y=150)]
+    seg = synth.make_segment(spec, nint=16)
+    ant = seg["ant_uvw"]
+    op = oracle.OraclePlan(ant, seg["freq_hz"], spec.inttime_s, spec.npix, spec.cell_rad, spec.dm_list,
+                           spec.dt_list, spec.threshold, edge="partial", mean_subtract=True)
+    S = op.stokes(seg["vis"], 16)
+    np.testing.assert_allclose(S.mean(axis=0), 0, atol=1e-12)
+    I, _ = op.image(S, 0, 0, 3, 16)
+    st = oracle.image_stats(I)
+    assert st.peak < 0.3          # the 5.0 continuum is gone, noise-level image remains
+    raw = oracle.stokes_i(seg["vis"])
+    I_raw, _ = op.image(raw, 0, 0, 3, 16)
+    assert oracle.image_stats(I_raw).peak > 4.0
+    # an impulse at one integration keeps (1 - 1/nint) of its height
+    X = np.zeros((16, 3, 2), dtype=np.complex128)
+    X[5] = 1.0
+    np.testing.assert_allclose(oracle.subtract_mean(X)[5], 1.0 - 1.0 / 16)
+    np.testing.assert_allclose(oracle.subtract_mean(X)[4], -1.0 / 16)
