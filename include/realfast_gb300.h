@@ -55,6 +55,11 @@ typedef enum rf_status {
  * the end of the segment get weight 0.  Default (FULL): only t' whose whole
  * dispersed sweep lies in the segment, t' < floor((nint - max_c delay)/dt). */
 #define RF_EDGE_PARTIAL 0x2u
+/* Mean-visibility subtraction (Sec. 3.1): before dedispersion, every
+ * (baseline, channel) loses its mean over the segment's nint integrations,
+ * which removes sources that are constant over the segment.  The mean is
+ * summed in FP64 over the stored Stokes-I values. */
+#define RF_MEAN_SUBTRACT 0x4u
 /* Build the host tables only; no device memory is touched.  Such a plan
  * answers the table queries (rf_plan_info, rf_plan_delays, rf_plan_cells,
  * rf_count_images) and rejects searches with RF_ERR_INVALID_ARG. */
@@ -82,7 +87,7 @@ typedef enum rf_status {
  * dm_list    [ndm] dispersion measures in pc cm^-3, each >= 0.
  * dt_list    [ndt] boxcar widths in integrations, each in [1, 1024].
  * threshold_sigma  candidate threshold on peak / sigma (> 0).
- * flags      RF_STORE_FP16 | RF_EDGE_PARTIAL | RF_HOST_ONLY.
+ * flags      RF_STORE_FP16 | RF_EDGE_PARTIAL | RF_MEAN_SUBTRACT | RF_HOST_ONLY.
  * max_nint   largest segment length (integrations) this plan will search;
  *            sizes the device buffers.
  * device     CUDA device ordinal the plan lives on.

@@ -27,7 +27,7 @@ __all__ = [
     "rf_plan_set_profiling", "rf_plan_get_profile", "RfKernelProfile", "rf_image_stats_noalloc", "rf_plan_set_tuning", "rf_plan_get_tuning", "rf_plan_autotune",
     "RfTuneReport", "Server", "RfServerDesc", "RfRequestInfo", "rf_plan_estimate_bytes",
     "Plan", "CANDIDATE_DTYPE", "STAT_DTYPE", "declared_symbols",
-    "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
+    "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_MEAN_SUBTRACT", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
 ]
 
 RF_OK = 0
@@ -45,6 +45,7 @@ STATUS_NAMES = {0: "RF_OK", 1: "RF_ERR_INVALID_ARG", 2: "RF_ERR_NO_MEMORY", 3: "
 
 RF_STORE_FP16 = 0x1
 RF_EDGE_PARTIAL = 0x2
+RF_MEAN_SUBTRACT = 0x4
 RF_HOST_ONLY = 0x100
 RF_FORM_BATCHED = 0
 RF_FORM_PLAIN = 1
@@ -432,6 +433,8 @@ class Plan:
                 flags |= RF_EDGE_PARTIAL
             if getattr(spec, "store", "fp32") == "fp16":
                 flags |= RF_STORE_FP16
+            if getattr(spec, "mean_subtract", False):
+                flags |= RF_MEAN_SUBTRACT
         return cls(ant_uvw, freq_hz, spec.inttime_s, spec.npix, spec.cell_rad, spec.dm_list, spec.dt_list,
                    spec.threshold, npol=spec.npol, flags=flags, max_nint=max_nint or spec.nint, device=device)
 

@@ -48,7 +48,7 @@ rf_status fail(rf_status s, const char* fmt, ...) {
 constexpr double kDispConst = 4.1488e-3;  // s GHz^2 per pc cm^-3 (Sec. 2.1 footnote)
 constexpr double kCLight = 299792458.0;   // m/s
 constexpr double kTwoPi = 6.283185307179586476925286766559;
-constexpr uint32_t kKnownFlags = RF_STORE_FP16 | RF_EDGE_PARTIAL | RF_HOST_ONLY;
+constexpr uint32_t kKnownFlags = RF_STORE_FP16 | RF_EDGE_PARTIAL | RF_MEAN_SUBTRACT | RF_HOST_ONLY;
 constexpr size_t kStageBytes = 256ull << 20;   // host->device chunk of raw visibilities
 constexpr size_t kTBudgetBytes = 4096ull << 20;  // column-FFT scratch per wave
 constexpr int kRangeEntries = 64;                // target entries per gridding warp
@@ -91,10 +91,12 @@ struct BusyGuard {
 
 enum KernelKind {
   K_H2D = 0, K_INGEST, K_RESAMPLE, K_WEIGHTS, K_GRID_CELLS, K_GRID_COLFFT, K_ROWFFT_STATS, K_FINALIZE,
-  K_PLAIN_TRIAL, K_NKINDS
+  K_PLAIN_TRIAL, K_MEAN_SUBTRACT, K_NKINDS
 };
-const char* const kKindNames[K_NKINDS] = {"h2d_copy",   "ingest",      "resample",     "weights",    "grid_cells",
-                                           "grid_colfft", "rowfft_stats", "finalize", "plain_trial_chunk"};
+const char* const kKindNames[K_NKINDS] = {"h2d_copy",    "ingest",       "resample",
+                                           "weights",     "grid_cells",   "grid_colfft",
+                                           "rowfft_stats", "finalize",    "plain_trial_chunk",
+                                           "mean_subtract"};
 
 // Event-pair timing of every launch a plan issues while profiling is on.
 struct Profiler {
@@ -746,16 +748,18 @@ rf_status ingest(rf_plan* p, const void* vis, int nint, cudaStream_t st) {
   if (on_device) {
     if ((uintptr_t)vis % 16 != 0) return fail(RF_ERR_INVALID_ARG, "device vis must be 16-byte aligned");
     RF_TIMED(p->prof, K_INGEST, st, rf::launch_ingest(static_cast<const float2*>(vis), nint, 0, p->npol, g, p->d_S, st));
-    return RF_OK;
+  } else {
+    const size_t per_int = (size_t)p->nbl * p->nchan * p->npol * sizeof(float2);
+    const unsigned char* src = static_cast<const unsigned char*>(vis);
+    for (int t = 0; t < nint; t += p->stage_nint) {
+      const int nt = std::min(p->stage_nint, nint - t);
+      RF_TIMED(p->prof, K_H2D, st,
+               cudaMemcpyAsync(p->d_stage, src + (size_t)t * per_int, (size_t)nt * per_int, cudaMemcpyHostToDevice,
+                               st));
+      RF_TIMED(p->prof, K_INGEST, st, rf::launch_ingest(p->d_stage, nt, t, p->npol, g, p->d_S, st));
+    }
   }
-  const size_t per_int = (size_t)p->nbl * p->nchan * p->npol * sizeof(float2);
-  const unsigned char* src = static_cast<const unsigned char*>(vis);
-  for (int t = 0; t < nint; t += p->stage_nint) {
-    const int nt = std::min(p->stage_nint, nint - t);
-    RF_TIMED(p->prof, K_H2D, st,
-             cudaMemcpyAsync(p->d_stage, src + (size_t)t * per_int, (size_t)nt * per_int, cudaMemcpyHostToDevice, st));
-    RF_TIMED(p->prof, K_INGEST, st, rf::launch_ingest(p->d_stage, nt, t, p->npol, g, p->d_S, st));
-  }
+  if (p->flags & RF_MEAN_SUBTRACT) RF_TIMED(p->prof, K_MEAN_SUBTRACT, st, rf::launch_mean_subtract(g, p->d_S, st));
   return RF_OK;
 }
 

@@ -97,6 +97,9 @@ struct SegmentGeom {
 cudaError_t launch_ingest(const float2* vis, int nt, int t_begin, int npol, const SegmentGeom& g, void* S,
                           cudaStream_t st);
 
+// Subtract from every row of S its mean over the first nint integrations.
+cudaError_t launch_mean_subtract(const SegmentGeom& g, void* S, cudaStream_t st);
+
 // Boxcar resampling of S into the phase-split series of width dt (see
 // DevTables::sdt_ptr) for the first nint integrations.
 cudaError_t launch_resample(const SegmentGeom& g, const void* S, void* Sdt, int dt, int lp, cudaStream_t st);

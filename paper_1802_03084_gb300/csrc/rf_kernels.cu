@@ -78,6 +78,59 @@ cudaError_t launch_ingest(const float2* vis, int nt, int t_begin, int npol, cons
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------- mean subtract --
+// Mean-visibility subtraction over the segment (Sec. 3.1): every row of S
+// (one baseline and channel) loses its mean over t < nint, which removes
+// sources that are constant over the segment.  One warp per row; lane l sums
+// t = l, l + 32, ... in FP64 and a fixed xor-shuffle tree combines the lanes,
+// so the mean does not depend on scheduling.  The difference is formed in
+// FP32 and stored back in the storage precision.
+template <bool FP16>
+__global__ void __launch_bounds__(256) k_mean_subtract(void* __restrict__ S, int nrows, int nint, int nint_pad) {
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= nrows) return;
+  const size_t base = (size_t)row * nint_pad;
+  double sr = 0.0, si = 0.0;
+  for (int t = lane; t < nint; t += 32) {
+    float2 v;
+    if (FP16)
+      v = __half22float2(reinterpret_cast<const __half2*>(S)[base + t]);
+    else
+      v = reinterpret_cast<const float2*>(S)[base + t];
+    sr += (double)v.x;
+    si += (double)v.y;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  const float mr = (float)(sr / (double)nint);
+  const float mi = (float)(si / (double)nint);
+  for (int t = lane; t < nint; t += 32) {
+    if (FP16) {
+      __half2* q = reinterpret_cast<__half2*>(S) + base + t;
+      const float2 v = __half22float2(*q);
+      *q = __floats2half2_rn(v.x - mr, v.y - mi);
+    } else {
+      float2* q = reinterpret_cast<float2*>(S) + base + t;
+      const float2 v = *q;
+      *q = make_float2(v.x - mr, v.y - mi);
+    }
+  }
+}
+
+cudaError_t launch_mean_subtract(const SegmentGeom& g, void* S, cudaStream_t st) {
+  const int nrows = g.nbl * g.nchan;
+  if (nrows <= 0 || g.nint <= 0) return cudaSuccess;
+  if (g.fp16)
+    k_mean_subtract<true><<<(nrows + 7) / 8, 256, 0, st>>>(S, nrows, g.nint, g.nint_pad);
+  else
+    k_mean_subtract<false><<<(nrows + 7) / 8, 256, 0, st>>>(S, nrows, g.nint, g.nint_pad);
+  return cudaGetLastError();
+}
+
 // --------------------------------------------------------------- resample --
 // Boxcar resampling over dt integrations (Sec. 2.2: matched filters over
 // pulse width; Fig. 2: the loop over sampling time), computed once per

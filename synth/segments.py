@@ -67,6 +67,7 @@ class SegmentSpec:
     cell_rad: float = 10.0 * ARCSEC
     edge: str = "full"            # "full" or "partial"
     store: str = "fp32"           # "fp32" or "fp16"
+    mean_subtract: bool = False   # remove the per-(baseline, channel) segment mean first
     pulses: List[Dict] = dataclasses.field(default_factory=list)
     continuum: List[Dict] = dataclasses.field(default_factory=list)
     seed: int = 0

@@ -22,13 +22,16 @@ def rel_rms(a, b):
 def plans_for(spec, seg, flags=None, max_nint=None, dt_list=None):
     dts = spec.dt_list if dt_list is None else dt_list
     edge = spec.edge
+    mean = bool(getattr(spec, "mean_subtract", False))
     if flags is not None:
         edge = "partial" if flags & rf.RF_EDGE_PARTIAL else "full"
+        mean = bool(flags & rf.RF_MEAN_SUBTRACT)
     op = oracle.OraclePlan(seg["ant_uvw"], seg["freq_hz"], spec.inttime_s, spec.npix, spec.cell_rad,
-                           spec.dm_list, dts, spec.threshold, edge=edge, npol=spec.npol)
+                           spec.dm_list, dts, spec.threshold, edge=edge, npol=spec.npol, mean_subtract=mean)
     if flags is None:
         flags = (rf.RF_EDGE_PARTIAL if spec.edge == "partial" else 0) | \
-                (rf.RF_STORE_FP16 if spec.store == "fp16" else 0)
+                (rf.RF_STORE_FP16 if spec.store == "fp16" else 0) | \
+                (rf.RF_MEAN_SUBTRACT if mean else 0)
     gp = rf.Plan(seg["ant_uvw"], seg["freq_hz"], spec.inttime_s, spec.npix, spec.cell_rad, spec.dm_list, dts,
                  spec.threshold, npol=spec.npol, flags=flags, max_nint=max_nint or seg["vis"].shape[0])
     return gp, op
@@ -77,7 +80,7 @@ def compare_candidates(gc, oc, threshold, ost=None, guard=SNR_GUARD):
 
 
 def oracle_images(op, vis, keys, nint=None):
-    S = oracle.stokes_i(vis[: (nint or vis.shape[0])])
+    S = op.stokes(vis, nint or vis.shape[0])
     out = {}
     for k in keys:
         I, W = op.image(S, *k, nint=nint or vis.shape[0])
