@@ -23,6 +23,8 @@ from .realfast_oracle import (  # noqa: F401
     n_valid_times,
     round_half_away,
     search_segment,
+    search_stream,
+    stream_overlap,
     stokes_i,
     subtract_mean,
 )

@@ -331,3 +331,57 @@ def search_segment(plan: OraclePlan, vis: np.ndarray, nint: Optional[int] = None
             cands.append(plan.candidate(d, s, t, st))
     cands.sort(key=lambda c: (c["dm_idx"], c["dt_idx"], c["t_idx"]))
     return (cands, stats) if with_stats else cands
+
+
+def stream_overlap(plan: OraclePlan) -> int:
+    """Integrations shared by consecutive segments of a stream: the longest
+    dispersion sweep of the plan, max over DM trials and channels of delta
+    (Sec. 3.2: segments overlap by the maximum sweep so that every pulse lies
+    whole inside one segment)."""
+    return int(np.max(plan.delays)) if plan.delays.size else 0
+
+
+def search_stream(plan: OraclePlan, vis: np.ndarray, stride: int, with_stats: bool = False):
+    """Search a continuous run of integrations cut into overlapping segments (Sec. 3.2).
+
+    Segment k covers integrations [k stride, k stride + stride + overlap).
+    Every DM trial and width dt (stride a multiple of every dt) searches
+    t' < stride / dt there, so each sweep lies inside the segment and each
+    start time k stride + t' dt is searched by exactly one segment.  Once
+    fewer than stride + overlap integrations remain, the rest (from the
+    next segment start to the end) is searched as one last segment under
+    the plan's own edge rule.  Mean subtraction, if on, takes each segment's
+    own mean.  t_idx in the output counts from the start of the run:
+    k stride / dt + t'.
+    """
+    dts = [int(x) for x in plan.dt_list]
+    for dt in dts:
+        if stride % dt:
+            raise ValueError("stride must be a multiple of every dt")
+    overlap = stream_overlap(plan)
+    nseg = stride + overlap
+    total = vis.shape[0]
+    windows = []
+    k = 0
+    while k * stride + nseg <= total:
+        keys = [(d, s, t) for d in range(len(plan.dm_list)) for s, dt in enumerate(dts) for t in range(stride // dt)]
+        windows.append((k * stride, nseg, keys))
+        k += 1
+    rest = total - k * stride
+    if rest > 0:
+        windows.append((k * stride, rest, plan.image_list(rest)))
+    cands, stats = [], {}
+    for start, n, keys in windows:
+        S = plan.stokes(vis[start:start + n], n)
+        for (d, s, t) in keys:
+            I, W = plan.image(S, d, s, t, n)
+            if I is None:
+                continue
+            st = image_stats(I)
+            key = (d, s, start // dts[s] + t)
+            if with_stats:
+                stats[key] = st
+            if st.sigma > 0 and st.snr >= plan.threshold:
+                cands.append(plan.candidate(*key, st))
+    cands.sort(key=lambda c: (c["dm_idx"], c["dt_idx"], c["t_idx"]))
+    return (cands, stats) if with_stats else cands
