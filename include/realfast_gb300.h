@@ -391,6 +391,69 @@ rf_status rf_server_results(struct rf_server* server, int64_t ticket, rf_candida
 /* Finish all queued work, then free the server and its plans. */
 rf_status rf_server_destroy(struct rf_server* server);
 
+/* ---- continuous search over overlapping segments ----------------------
+ * A stream cuts an unbounded run of integrations into segments that overlap
+ * by the plan's longest dispersion sweep (Sec. 3.2: consecutive segments
+ * overlap by the maximum sweep so that every pulse lies whole inside one of
+ * them).  Segment k holds integrations [k stride, k stride + stride + overlap)
+ * with overlap = max over DM trials and channels of the delay; every
+ * (DM, dt) searches t' < stride / dt in it, so each start time
+ * k stride + t' dt is searched by exactly one segment and its whole sweep is
+ * inside that segment.  rf_stream_flush searches what is left (from the next
+ * segment start to the last integration pushed) under the plan's edge rule.
+ * Without RF_MEAN_SUBTRACT the union of a stream's images is exactly the
+ * image set of one rf_search_segment over the whole run; with it, each
+ * segment subtracts its own mean.
+ *
+ * Outputs count t_idx from the start of the run: k stride / dt + t'.
+ * The stream holds two device windows of stride + overlap raw integrations
+ * ([nint][nbl][nchan][npol] complex64) on the plan's device and uses the
+ * plan for its searches; the plan must outlive the stream and may not be
+ * searched by another thread while a push or flush runs (RF_ERR_BUSY).  A
+ * stream is used by one thread at a time.
+ */
+/* Keep every searched image's statistics for rf_stream_pop_stats. */
+#define RF_STREAM_KEEP_STATS 0x1u
+
+typedef struct rf_stream_info {
+  int32_t stride;           /* integrations between segment starts            */
+  int32_t overlap;          /* max dispersion delay, integrations             */
+  int32_t segment_nint;     /* stride + overlap                               */
+  int32_t fill;             /* integrations waiting in the current window     */
+  int64_t pushed;           /* integrations pushed since creation or flush    */
+  int64_t segments;         /* segments searched since creation or flush      */
+  uint64_t pending_candidates;
+  uint64_t pending_stats;
+} rf_stream_info;
+
+/* stride must be >= 1 and a multiple of every dt of the plan, and
+ * stride + overlap <= the plan's max_nint.  Errors: RF_ERR_INVALID_ARG
+ * (also for a RF_HOST_ONLY plan), RF_ERR_NO_MEMORY, RF_ERR_CUDA. */
+rf_status rf_stream_create(struct rf_plan* plan, int32_t stride, uint32_t flags, struct rf_stream** out);
+
+/* Append nint integrations (host or device memory, layout as for
+ * rf_search_segment) and search every segment they complete, in order, on
+ * `stream` (NULL: the default stream).  Returns when those searches are
+ * done; their candidates (and stats) are queued.  *n_segments (may be NULL)
+ * = segments searched by this call. */
+rf_status rf_stream_push(struct rf_stream* s, const void* vis, int32_t nint, void* stream, int32_t* n_segments);
+
+/* Search the integrations still in the window (if any) as the last segment
+ * under the plan's edge rule, then start a new run (t_idx from 0 again). */
+rf_status rf_stream_flush(struct rf_stream* s, void* stream, int32_t* n_segments);
+
+/* Move up to cap queued candidates (oldest segment first, each segment's
+ * sorted by (dm_idx, dt_idx, t_idx)) into out; *n_out = number moved. */
+rf_status rf_stream_pop(struct rf_stream* s, rf_candidate* out, size_t cap, size_t* n_out);
+
+/* Same for image statistics (only with RF_STREAM_KEEP_STATS). */
+rf_status rf_stream_pop_stats(struct rf_stream* s, rf_image_stat* out, size_t cap, size_t* n_out);
+
+rf_status rf_stream_get_info(const struct rf_stream* s, rf_stream_info* out);
+
+/* Free the windows and queues (NULL-safe).  The plan is not destroyed. */
+rf_status rf_stream_destroy(struct rf_stream* s);
+
 /* Library version string. */
 const char* rf_version(void);
 

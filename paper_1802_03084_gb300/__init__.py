@@ -26,8 +26,9 @@ __all__ = [
     "rf_plan_delays", "rf_plan_cells", "rf_count_images", "rf_last_error", "rf_version",
     "rf_plan_set_profiling", "rf_plan_get_profile", "RfKernelProfile", "rf_image_stats_noalloc", "rf_plan_set_tuning", "rf_plan_get_tuning", "rf_plan_autotune",
     "RfTuneReport", "Server", "RfServerDesc", "RfRequestInfo", "rf_plan_estimate_bytes",
+    "Stream", "RfStreamInfo",
     "Plan", "CANDIDATE_DTYPE", "STAT_DTYPE", "declared_symbols",
-    "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_MEAN_SUBTRACT", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
+    "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_MEAN_SUBTRACT", "RF_STREAM_KEEP_STATS", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
 ]
 
 RF_OK = 0
@@ -46,6 +47,7 @@ STATUS_NAMES = {0: "RF_OK", 1: "RF_ERR_INVALID_ARG", 2: "RF_ERR_NO_MEMORY", 3: "
 RF_STORE_FP16 = 0x1
 RF_EDGE_PARTIAL = 0x2
 RF_MEAN_SUBTRACT = 0x4
+RF_STREAM_KEEP_STATS = 0x1
 RF_HOST_ONLY = 0x100
 RF_FORM_BATCHED = 0
 RF_FORM_PLAIN = 1
@@ -116,6 +118,12 @@ class RfRequestInfo(ctypes.Structure):
                 ("n_candidates", ctypes.c_uint64), ("plan_reused", ctypes.c_int32)]
 
 
+class RfStreamInfo(ctypes.Structure):
+    _fields_ = [("stride", ctypes.c_int32), ("overlap", ctypes.c_int32), ("segment_nint", ctypes.c_int32),
+                ("fill", ctypes.c_int32), ("pushed", ctypes.c_int64), ("segments", ctypes.c_int64),
+                ("pending_candidates", ctypes.c_uint64), ("pending_stats", ctypes.c_uint64)]
+
+
 class RfKernelProfile(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -173,6 +181,13 @@ def lib() -> ctypes.CDLL:
         "rf_server_results": ([P, ctypes.c_int64, P, S, ctypes.POINTER(S)], ctypes.c_int),
         "rf_server_destroy": ([P], ctypes.c_int),
         "rf_plan_get_profile": ([P, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "rf_stream_create": ([P, ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(P)], ctypes.c_int),
+        "rf_stream_push": ([P, P, ctypes.c_int32, P, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "rf_stream_flush": ([P, P, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "rf_stream_pop": ([P, P, S, ctypes.POINTER(S)], ctypes.c_int),
+        "rf_stream_pop_stats": ([P, P, S, ctypes.POINTER(S)], ctypes.c_int),
+        "rf_stream_get_info": ([P, ctypes.POINTER(RfStreamInfo)], ctypes.c_int),
+        "rf_stream_destroy": ([P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -365,6 +380,60 @@ def rf_plan_estimate_bytes(desc: RfPlanDesc, wave_images: int = 0) -> int:
     b = ctypes.c_uint64()
     _check(lib().rf_plan_estimate_bytes(ctypes.byref(desc), wave_images, ctypes.byref(b)))
     return int(b.value)
+
+
+class Stream:
+    """Continuous search of a run of integrations in segments that overlap by
+    the plan's longest sweep (rf_stream_* in the C ABI).  t_idx of every
+    output counts from the start of the run."""
+
+    def __init__(self, plan, stride: int, keep_stats: bool = False):
+        self.plan = plan
+        self.handle = ctypes.c_void_p()
+        flags = RF_STREAM_KEEP_STATS if keep_stats else 0
+        _check(lib().rf_stream_create(plan.handle, stride, flags, ctypes.byref(self.handle)))
+
+    def push(self, vis, nint=None, stream=None) -> int:
+        """Append integrations (host or device); returns the segments searched."""
+        n = ctypes.c_int32()
+        nint = len(vis) if nint is None else nint
+        _check(lib().rf_stream_push(self.handle, _ptr(vis), nint, _stream(stream), ctypes.byref(n)))
+        return int(n.value)
+
+    def flush(self, stream=None) -> int:
+        n = ctypes.c_int32()
+        _check(lib().rf_stream_flush(self.handle, _stream(stream), ctypes.byref(n)))
+        return int(n.value)
+
+    def info(self) -> dict:
+        i = RfStreamInfo()
+        _check(lib().rf_stream_get_info(self.handle, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in RfStreamInfo._fields_}
+
+    def pop(self) -> np.ndarray:
+        cap = max(int(self.info()["pending_candidates"]), 1)
+        out = np.zeros(cap, dtype=CANDIDATE_DTYPE)
+        n = ctypes.c_size_t()
+        _check(lib().rf_stream_pop(self.handle, out.ctypes.data, cap, ctypes.byref(n)))
+        return out[:n.value]
+
+    def pop_stats(self) -> np.ndarray:
+        cap = max(int(self.info()["pending_stats"]), 1)
+        out = np.zeros(cap, dtype=STAT_DTYPE)
+        n = ctypes.c_size_t()
+        _check(lib().rf_stream_pop_stats(self.handle, out.ctypes.data, cap, ctypes.byref(n)))
+        return out[:n.value]
+
+    def close(self):
+        if self.handle:
+            _check(lib().rf_stream_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Server:

@@ -233,8 +233,11 @@ struct rf_plan {
   float2* d_stage = nullptr;
   int stage_nint = 0;
 
-  // image list of the last nint searched
+  // image list of the last (nint, span) searched; span > 0 limits every
+  // (DM, dt) to t' < span / dt (segments of a stream)
   int cached_nint = -1;
+  int cached_span = 0;
+  int t_span = 0;
   std::vector<int4> img_info;
   std::vector<Group> groups;
   std::vector<Wave> waves;
@@ -307,12 +310,19 @@ struct rf_plan {
 
 namespace {
 
-int n_times(const rf_plan* p, int nint, int d, int s) {
+int n_times_span(const rf_plan* p, int nint, int d, int s, int t_span) {
   const int dt = p->dt[s];
-  if (p->flags & RF_EDGE_PARTIAL) return nint / dt;
-  const int span = nint - p->max_delay[d];
-  return span > 0 ? span / dt : 0;
+  int n;
+  if (p->flags & RF_EDGE_PARTIAL) {
+    n = nint / dt;
+  } else {
+    const int span = nint - p->max_delay[d];
+    n = span > 0 ? span / dt : 0;
+  }
+  return t_span > 0 ? std::min(n, t_span / dt) : n;
 }
+
+int n_times(const rf_plan* p, int nint, int d, int s) { return n_times_span(p, nint, d, s, p->t_span); }
 
 int64_t count_images(const rf_plan* p, int nint) {
   int64_t n = 0;
@@ -537,6 +547,7 @@ void build_lists(rf_plan* p, int nint) {
   w.img_end = (int)p->img_info.size();
   if (w.img_end > w.img_begin) p->waves.push_back(w);
   p->cached_nint = nint;
+  p->cached_span = p->t_span;
   p->drop_graph();
 }
 
@@ -898,8 +909,16 @@ rf_status run_plain(rf_plan* p, int nint, DevStat* d_stats, cudaStream_t st) {
   return RF_OK;
 }
 
+// Sets the plan's t' span for one search and clears it on every exit.
+struct SpanGuard {
+  rf_plan* p;
+  SpanGuard(rf_plan* pl, int span) : p(pl) { p->t_span = span; }
+  ~SpanGuard() { p->t_span = 0; }
+};
+
 rf_status search_impl(rf_plan* p, const void* vis, int nint, void* stream, rf_candidate* out, size_t cap,
-                      size_t* n_out, bool want_stats, rf_image_stat* stats, size_t stats_cap, size_t* n_stats) {
+                      size_t* n_out, bool want_stats, rf_image_stat* stats, size_t stats_cap, size_t* n_stats,
+                      int span = 0) {
   if (!p) return fail(RF_ERR_INVALID_ARG, "plan is NULL");
   if (p->host_only) return fail(RF_ERR_INVALID_ARG, "plan was created with RF_HOST_ONLY");
   if (!vis) return fail(RF_ERR_INVALID_ARG, "vis is NULL");
@@ -912,12 +931,13 @@ rf_status search_impl(rf_plan* p, const void* vis, int nint, void* stream, rf_ca
   if (!dg.ok) return fail(RF_ERR_CUDA, "cannot select device %d", p->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   *n_out = 0;
+  SpanGuard sg(p, span);
 
   rf_status s = ingest(p, vis, nint, st);
   if (s != RF_OK) return s;
   s = resample_all(p, nint, st);
   if (s != RF_OK) return s;
-  if (p->cached_nint != nint) {
+  if (p->cached_nint != nint || p->cached_span != p->t_span) {
     build_lists(p, nint);
     if (!p->img_info.empty()) {
       RF_CUDA(cudaMemcpyAsync(p->d_img_info, p->img_info.data(), p->img_info.size() * sizeof(int4),
@@ -1011,6 +1031,42 @@ rf_status search_impl(rf_plan* p, const void* vis, int nint, void* stream, rf_ca
 
 namespace rf {
 void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+rf_status plan_geometry(const rf_plan* p, PlanGeometry* g) {
+  if (!p || !g) return fail(RF_ERR_INVALID_ARG, "NULL argument");
+  g->nbl = p->nbl;
+  g->nchan = p->nchan;
+  g->npol = p->npol;
+  g->max_nint = p->max_nint;
+  g->max_delay = 0;
+  for (int d = 0; d < p->ndm; ++d) g->max_delay = std::max(g->max_delay, p->max_delay[d]);
+  g->device = p->device;
+  g->host_only = p->host_only;
+  g->dt.assign(p->dt.begin(), p->dt.end());
+  return RF_OK;
+}
+
+rf_status search_span(rf_plan* p, const void* vis, int nint, int span, void* stream,
+                      std::vector<rf_candidate>* cands, std::vector<rf_image_stat>* stats) {
+  if (!p || !cands) return fail(RF_ERR_INVALID_ARG, "NULL argument");
+  if (span < 0) return fail(RF_ERR_INVALID_ARG, "span %d < 0", span);
+  int64_t nimg = 0;  // images of this (nint, span): at most one candidate each
+  for (int d = 0; d < p->ndm; ++d)
+    for (int k = 0; k < p->ndt; ++k) nimg += n_times_span(p, nint, d, k, span);
+  cands->resize((size_t)std::max<int64_t>(nimg, 1));
+  size_t n_out = 0, n_stats = 0;
+  rf_status s;
+  if (stats) {
+    stats->resize((size_t)std::max<int64_t>(nimg, 1));
+    s = search_impl(p, vis, nint, stream, cands->data(), cands->size(), &n_out, true, stats->data(), stats->size(),
+                    &n_stats, span);
+    stats->resize(s == RF_OK ? n_stats : 0);
+  } else {
+    s = search_impl(p, vis, nint, stream, cands->data(), cands->size(), &n_out, false, nullptr, 0, nullptr, span);
+  }
+  cands->resize(s == RF_OK ? n_out : 0);
+  return s;
+}
 }  // namespace rf
 
 extern "C" {

@@ -5,6 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
+#include "realfast_gb300.h"
+
 namespace rf {
 
 // Gridding entry flags (low bits of GridEntry.cflags).
@@ -172,5 +176,19 @@ bool image_kernel_shape(int npix, ImageKernelShape* out);
 
 // Sets the thread-local message returned by rf_last_error().
 void set_last_error(const char* msg);
+
+// ---------------------------------------------------------- host helpers --
+// For the stream runtime (host code only).
+struct PlanGeometry {
+  int nbl, nchan, npol, max_nint, max_delay, device;
+  bool host_only;
+  std::vector<int> dt;
+};
+rf_status plan_geometry(const struct ::rf_plan* p, PlanGeometry* g);
+// One search of nint integrations in which every (DM, dt) is limited to
+// t' < span / dt besides the plan's edge rule (span 0: no limit).  Returns
+// the candidates and, if stats is not NULL, every image's statistics.
+rf_status search_span(struct ::rf_plan* p, const void* vis, int nint, int span, void* stream,
+                      std::vector<rf_candidate>* cands, std::vector<rf_image_stat>* stats);
 
 }  // namespace rf

@@ -148,3 +148,24 @@ def test_estimate_bytes_without_device(L):
     assert b > 351 * 256 * 1024 * 8
     b_small = rf.rf_plan_estimate_bytes(rf.make_desc(**kw), wave_images=64)
     assert b_small < b
+
+
+def test_stream_rejects_bad_arguments(L):
+    spec = synth.config("tiny")
+    p, _ = _host_plan(spec)
+    P = ctypes.c_void_p
+    with p:
+        h = P()
+        # a host-only plan cannot stream
+        assert L.rf_stream_create(p.handle, 64, 0, ctypes.byref(h)) == rf.RF_ERR_INVALID_ARG
+        assert "HOST_ONLY" in rf.rf_last_error()
+        assert not h.value
+    assert L.rf_stream_create(None, 64, 0, ctypes.byref(P())) == rf.RF_ERR_INVALID_ARG
+    assert L.rf_stream_create(None, 64, 0, None) == rf.RF_ERR_INVALID_ARG
+    assert L.rf_stream_destroy(None) == 0
+    n = ctypes.c_int32()
+    assert L.rf_stream_push(None, None, 1, None, ctypes.byref(n)) == rf.RF_ERR_INVALID_ARG
+    assert L.rf_stream_flush(None, None, ctypes.byref(n)) == rf.RF_ERR_INVALID_ARG
+    m = ctypes.c_size_t()
+    assert L.rf_stream_pop(None, None, 0, ctypes.byref(m)) == rf.RF_ERR_INVALID_ARG
+    assert L.rf_stream_get_info(None, None) == rf.RF_ERR_INVALID_ARG
