@@ -12,6 +12,8 @@ from .realfast_oracle import (  # noqa: F401
     ImageStats,
     OraclePlan,
     baseline_uvw,
+    candidate_features,
+    candidate_spectrum,
     cell_table,
     dedisperse_resample,
     delay_table,
@@ -20,6 +22,7 @@ from .realfast_oracle import (  # noqa: F401
     dirty_image_fft,
     grid_full_plane,
     image_stats,
+    moments,
     n_valid_times,
     round_half_away,
     search_segment,

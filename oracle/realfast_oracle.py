@@ -385,3 +385,64 @@ def search_stream(plan: OraclePlan, vis: np.ndarray, stride: int, with_stats: bo
                 cands.append(plan.candidate(*key, st))
     cands.sort(key=lambda c: (c["dm_idx"], c["dt_idx"], c["t_idx"]))
     return (cands, stats) if with_stats else cands
+
+
+# ----------------------------------------------------------------------------
+# Candidate products (Sec. 3.3: statistics from each candidate's image and
+# spectrum at a low threshold, image and spectrum plots at a higher one)
+# ----------------------------------------------------------------------------
+
+def moments(v: np.ndarray):
+    """Population mean, standard deviation, skewness and excess kurtosis:
+    mu, sqrt(m2), m3 / m2^1.5, m4 / m2^2 - 3 with m_k = mean((v - mu)^k).
+    Skewness and kurtosis are 0 when m2 = 0."""
+    v = np.asarray(v, dtype=np.float64).ravel()
+    if v.size == 0:
+        return 0.0, 0.0, 0.0, 0.0
+    mu = v.mean()
+    d = v - mu
+    m2 = float(np.mean(d * d))
+    if m2 <= 0:
+        return float(mu), 0.0, 0.0, 0.0
+    m3 = float(np.mean(d * d * d))
+    m4 = float(np.mean(d * d * d * d))
+    return float(mu), float(np.sqrt(m2)), m3 / m2 ** 1.5, m4 / (m2 * m2) - 3.0
+
+
+def candidate_spectrum(plan: OraclePlan, S: np.ndarray, d: int, s: int, t: int, x: int, y: int,
+                       nint: Optional[int] = None):
+    """Spectrum of a candidate: per channel, the dedispersed, resampled
+    visibilities phased to pixel (x, y) with the image's own cell phases,
+    averaged over the on-grid baselines and samples:
+
+        spec[c] = sum_{b on-grid} R[b,c] exp(+2 pi i (iu (x - N/2) + iv (y - N/2)) / N) / w_c,
+        w_c = (on-grid baselines at c) * n_c.
+
+    Returns (spec complex128 [nchan], w_c [nchan]); spec is 0 where w_c = 0.
+    The w-weighted mean of Re(spec) is the image value at (x, y)."""
+    N = plan.npix
+    R, n = dedisperse_resample(S, plan.delays[d], int(plan.dt_list[s]), t, nint)
+    k = plan.iu * (x - N // 2) + plan.iv * (y - N // 2)
+    ph = np.exp(2j * np.pi * (k % N) / N)
+    w = plan.ongrid.sum(axis=0) * n
+    num = np.where(plan.ongrid, R * ph, 0).sum(axis=0)
+    spec = np.where(w > 0, num / np.where(w > 0, w, 1), 0)
+    return spec, w.astype(np.float64)
+
+
+def candidate_features(plan: OraclePlan, S: np.ndarray, d: int, s: int, t: int, nint: Optional[int] = None):
+    """Image and spectrum statistics of trial (d, s, t') at its peak pixel.
+
+    Image moments are over all N^2 pixels; spectrum moments over the real
+    part of the spectrum at the channels with data (w_c > 0)."""
+    I, W = plan.image(S, d, s, t, nint)
+    st = image_stats(I)
+    spec, w = candidate_spectrum(plan, S, d, s, t, st.x, st.y, nint)
+    im = moments(I)
+    used = w > 0
+    sp = moments(spec.real[used])
+    return dict(dm_idx=d, dt_idx=s, t_idx=t, x=st.x, y=st.y, snr=st.snr,
+                image_mean=im[0], image_sigma=im[1], image_skew=im[2], image_kurtosis=im[3],
+                spec_mean=sp[0], spec_std=sp[1], spec_skew=sp[2], spec_kurtosis=sp[3],
+                peak_from_spectrum=float((w * spec.real).sum() / w.sum()), nchan_used=int(used.sum()),
+                spectrum=spec, image=I)
