@@ -391,6 +391,51 @@ rf_status rf_server_results(struct rf_server* server, int64_t ticket, rf_candida
 /* Finish all queued work, then free the server and its plans. */
 rf_status rf_server_destroy(struct rf_server* server);
 
+/* ---- candidate products ----------------------------------------------
+ * Statistics measured from each candidate's image and spectrum (Sec. 3.3:
+ * kept for every candidate above a low threshold, about 6 sigma), and the
+ * image and spectrum themselves (Sec. 3.3: candidate plots, above about
+ * 7 sigma).  Which candidates get which product is the caller's choice.
+ *
+ * Spectrum of candidate (dm_idx, dt_idx, t_idx) at pixel (x, y): per channel
+ * c (in the plan's channel order), the dedispersed, resampled visibilities
+ * phased to (x, y) with the image's own cell phases
+ * exp(+2 pi i (iu (x - N/2) + iv (y - N/2)) / N), summed over the on-grid
+ * baselines and divided by w_c = (on-grid baselines at c) * (samples
+ * present); 0 where w_c = 0.  Its w-weighted mean real part equals the image
+ * value at (x, y).  Moments are population moments in FP64: image moments
+ * over all N^2 pixels, spectrum moments over Re(spectrum) at the channels
+ * with w_c > 0; kurtosis is the excess kurtosis m4 / m2^2 - 3.
+ */
+typedef struct rf_candidate_features {
+  int32_t dm_idx;
+  int32_t dt_idx;
+  int32_t t_idx;
+  int32_t x;
+  int32_t y;
+  int32_t nchan_used;        /* channels with w_c > 0                        */
+  double image_mean;
+  double image_sigma;
+  double image_skew;
+  double image_kurtosis;
+  double spec_mean;
+  double spec_std;
+  double spec_skew;
+  double spec_kurtosis;
+  double peak_from_spectrum; /* sum_c w_c Re(spec_c) / sum_c w_c           */
+} rf_candidate_features;
+
+/* Products of n candidates of a segment (the same vis and nint they were
+ * found in; only dm_idx, dt_idx, t_idx, x and y of each are read).
+ * features [n] is required; spectra [n][nchan][2] (re, im) FP32 and
+ * images [n][N][N] FP32 are written when not NULL.  The segment is ingested
+ * again; device scratch is allocated for the call.  Errors:
+ * RF_ERR_INVALID_ARG (a trial the plan does not search at nint, a pixel
+ * outside the image), RF_ERR_SHAPE, RF_ERR_NO_MEMORY, RF_ERR_BUSY. */
+rf_status rf_candidate_products(struct rf_plan* plan, const void* vis, int32_t nint, void* stream,
+                                const rf_candidate* cands, int32_t n, rf_candidate_features* features,
+                                float* spectra, float* images);
+
 /* ---- continuous search over overlapping segments ----------------------
  * A stream cuts an unbounded run of integrations into segments that overlap
  * by the plan's longest dispersion sweep (Sec. 3.2: consecutive segments

@@ -26,7 +26,7 @@ __all__ = [
     "rf_plan_delays", "rf_plan_cells", "rf_count_images", "rf_last_error", "rf_version",
     "rf_plan_set_profiling", "rf_plan_get_profile", "RfKernelProfile", "rf_image_stats_noalloc", "rf_plan_set_tuning", "rf_plan_get_tuning", "rf_plan_autotune",
     "RfTuneReport", "Server", "RfServerDesc", "RfRequestInfo", "rf_plan_estimate_bytes",
-    "Stream", "RfStreamInfo",
+    "Stream", "RfStreamInfo", "RfCandidateFeatures", "FEATURES_DTYPE", "rf_candidate_products",
     "Plan", "CANDIDATE_DTYPE", "STAT_DTYPE", "declared_symbols",
     "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_MEAN_SUBTRACT", "RF_STREAM_KEEP_STATS", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
 ]
@@ -118,6 +118,16 @@ class RfRequestInfo(ctypes.Structure):
                 ("n_candidates", ctypes.c_uint64), ("plan_reused", ctypes.c_int32)]
 
 
+class RfCandidateFeatures(ctypes.Structure):
+    _fields_ = [("dm_idx", ctypes.c_int32), ("dt_idx", ctypes.c_int32), ("t_idx", ctypes.c_int32),
+                ("x", ctypes.c_int32), ("y", ctypes.c_int32), ("nchan_used", ctypes.c_int32),
+                ("image_mean", ctypes.c_double), ("image_sigma", ctypes.c_double),
+                ("image_skew", ctypes.c_double), ("image_kurtosis", ctypes.c_double),
+                ("spec_mean", ctypes.c_double), ("spec_std", ctypes.c_double),
+                ("spec_skew", ctypes.c_double), ("spec_kurtosis", ctypes.c_double),
+                ("peak_from_spectrum", ctypes.c_double)]
+
+
 class RfStreamInfo(ctypes.Structure):
     _fields_ = [("stride", ctypes.c_int32), ("overlap", ctypes.c_int32), ("segment_nint", ctypes.c_int32),
                 ("fill", ctypes.c_int32), ("pushed", ctypes.c_int64), ("segments", ctypes.c_int64),
@@ -138,6 +148,7 @@ def _np_dtype(struct) -> np.dtype:
 
 CANDIDATE_DTYPE = _np_dtype(RfCandidate)
 STAT_DTYPE = _np_dtype(RfImageStat)
+FEATURES_DTYPE = _np_dtype(RfCandidateFeatures)
 
 _LIB = None
 
@@ -181,6 +192,7 @@ def lib() -> ctypes.CDLL:
         "rf_server_results": ([P, ctypes.c_int64, P, S, ctypes.POINTER(S)], ctypes.c_int),
         "rf_server_destroy": ([P], ctypes.c_int),
         "rf_plan_get_profile": ([P, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "rf_candidate_products": ([P, P, ctypes.c_int32, P, P, ctypes.c_int32, P, P, P], ctypes.c_int),
         "rf_stream_create": ([P, ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(P)], ctypes.c_int),
         "rf_stream_push": ([P, P, ctypes.c_int32, P, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "rf_stream_flush": ([P, P, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
@@ -306,6 +318,21 @@ def rf_render_images(plan, vis, nint: int, trials: Sequence, npix: int, stream=N
     _check(lib().rf_render_images(plan, _ptr(vis), nint, _stream(stream), tr.ctypes.data, tr.shape[0],
                                   out.ctypes.data))
     return out
+
+
+def rf_candidate_products(plan, vis, nint: int, cands, npix: int, nchan: int, spectra=True, images=True,
+                          stream=None):
+    """Features [n] (FEATURES_DTYPE) and, if asked, spectra [n, nchan] complex64
+    and images [n, N, N] float32 of the given candidates (CANDIDATE_DTYPE)."""
+    c = np.ascontiguousarray(cands, dtype=CANDIDATE_DTYPE)
+    n = c.shape[0]
+    feats = np.zeros(max(n, 1), dtype=FEATURES_DTYPE)
+    sp = np.zeros((max(n, 1), nchan), dtype=np.complex64) if spectra else None
+    im = np.zeros((max(n, 1), npix, npix), dtype=np.float32) if images else None
+    _check(lib().rf_candidate_products(plan, _ptr(vis), nint, _stream(stream), c.ctypes.data, n,
+                                       feats.ctypes.data, sp.ctypes.data if spectra else None,
+                                       im.ctypes.data if images else None))
+    return feats[:n], (sp[:n] if spectra else None), (im[:n] if images else None)
 
 
 def rf_plan_set_form(plan, form: int) -> None:
@@ -515,6 +542,28 @@ class Plan:
 
     def render(self, vis, trials, nint=None, stream=None):
         return rf_render_images(self.handle, vis, nint if nint is not None else len(vis), trials, self.npix, stream)
+
+    def candidate_products(self, vis, cands, nint=None, spectra=True, images=True, stream=None):
+        """Features (and spectra, images) of candidates of this segment."""
+        nint = nint if nint is not None else len(vis)
+        return rf_candidate_products(self.handle, vis, nint, cands, self.npix, self.desc.nchan, spectra, images,
+                                     stream)
+
+    def candidate_tiers(self, vis, cands, stats_sigma=6.0, plot_sigma=7.0, nint=None, stream=None):
+        """Sec. 3.3 tiers: features for candidates with snr >= stats_sigma,
+        spectra and images as well for those with snr >= plot_sigma.
+        Returns (features, plot_index, spectra, images); plot_index indexes
+        the features array."""
+        c = np.asarray(cands, dtype=CANDIDATE_DTYPE)
+        c = c[c["snr"] >= stats_sigma]
+        if len(c) == 0:
+            return np.zeros(0, FEATURES_DTYPE), np.zeros(0, np.int64), None, None
+        feats, _, _ = self.candidate_products(vis, c, nint, spectra=False, images=False, stream=stream)
+        idx = np.nonzero(c["snr"] >= plot_sigma)[0]
+        sp = im = None
+        if len(idx):
+            _, sp, im = self.candidate_products(vis, c[idx], nint, stream=stream)
+        return feats, idx, sp, im
 
     def info(self) -> RfPlanInfo:
         return rf_plan_get_info(self.handle)

@@ -230,6 +230,7 @@ struct rf_plan {
   DevCand* d_cands = nullptr;
   int* d_ncand = nullptr;
   DevStat* d_stats = nullptr;
+  int2* d_cellbc = nullptr;     // [nchan * nbl] (iu, iv) per row, for candidate spectra
   float2* d_stage = nullptr;
   int stage_nint = 0;
 
@@ -1027,6 +1028,65 @@ rf_status search_impl(rf_plan* p, const void* vis, int nint, void* stream, rf_ca
   return RF_OK;
 }
 
+// Every trial (d, s, t') must be one the plan searches at this nint.
+rf_status check_trials(const rf_plan* p, int nint, const int32_t* trials, int n) {
+  for (int k = 0; k < n; ++k) {
+    const int d = trials[3 * k], s = trials[3 * k + 1], t = trials[3 * k + 2];
+    if (d < 0 || d >= p->ndm || s < 0 || s >= p->ndt || t < 0 || t >= n_times(p, nint, d, s))
+      return fail(RF_ERR_INVALID_ARG, "trial %d (%d, %d, %d) is not searched", k, d, s, t);
+  }
+  return RF_OK;
+}
+
+// Images of n trials into d_img ([n][N][N]), after ingest and resampling.
+// The trials replace the plan's cached search lists.
+rf_status render_core(rf_plan* p, int nint, const int32_t* trials, int n, float* d_img, cudaStream_t st) {
+  if (n > p->img_cap) return fail(RF_ERR_INVALID_ARG, "at most %d images per call", p->img_cap);
+  std::vector<int4> info(n);
+  std::vector<Group> grp(n);
+  for (int k = 0; k < n; ++k) {
+    info[k] = make_int4(trials[3 * k], trials[3 * k + 1], trials[3 * k + 2], 0);
+    grp[k] = Group{trials[3 * k], trials[3 * k + 1], trials[3 * k + 2], 1, k, {0, 0, 0}};
+  }
+  p->cached_nint = -1;
+  p->drop_graph();
+  RF_CUDA(cudaMemcpyAsync(p->d_img_info, info.data(), n * sizeof(int4), cudaMemcpyHostToDevice, st));
+  RF_CUDA(cudaMemcpyAsync(p->d_groups, grp.data(), n * sizeof(Group), cudaMemcpyHostToDevice, st));
+  std::vector<Wave> waves;
+  const int per_wave = std::min(p->slots_max, p->gslots_max);  // single-image groups
+  for (int k = 0; k < n; k += per_wave) {
+    const int e = std::min(n, k + per_wave);
+    waves.push_back(Wave{k, e, k, e});
+  }
+  RF_CUDA(cudaMemsetAsync(p->d_ncand, 0, sizeof(int), st));
+  rf_status s = run_waves(p, nint, waves, n, nullptr, d_img, st);
+  // the host-side lists above must outlive the copies
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (s == RF_OK && e != cudaSuccess) s = fail(RF_ERR_CUDA, "render: %s", cudaGetErrorString(e));
+  return s;
+}
+
+// Device allocations freed when the scope ends (calls outside the hot path).
+struct DeviceScratch {
+  std::vector<void*> ptrs;
+  template <typename T>
+  rf_status get(T** q, size_t count) {
+    void* v = nullptr;
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&v, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(RF_ERR_NO_MEMORY, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    ptrs.push_back(v);
+    *q = static_cast<T*>(v);
+    return RF_OK;
+  }
+  ~DeviceScratch() {
+    for (void* v : ptrs) cudaFree(v);
+  }
+};
+
 }  // namespace
 
 namespace rf {
@@ -1183,35 +1243,16 @@ rf_status rf_render_images(rf_plan* p, const void* vis, int32_t nint, void* stre
   if (!vis || !trials || !images || n < 1) return fail(RF_ERR_INVALID_ARG, "bad render arguments");
   if (nint < 1 || nint > p->max_nint) return fail(RF_ERR_SHAPE, "nint %d out of [1, %d]", nint, p->max_nint);
   if (n > p->img_cap) return fail(RF_ERR_INVALID_ARG, "at most %d images per call", p->img_cap);
-  for (int k = 0; k < n; ++k) {
-    const int d = trials[3 * k], s = trials[3 * k + 1], t = trials[3 * k + 2];
-    if (d < 0 || d >= p->ndm || s < 0 || s >= p->ndt || t < 0 || t >= n_times(p, nint, d, s))
-      return fail(RF_ERR_INVALID_ARG, "trial %d (%d, %d, %d) is not searched", k, d, s, t);
-  }
+  rf_status s = check_trials(p, nint, trials, n);
+  if (s != RF_OK) return s;
   BusyGuard bg(&p->busy);
   if (!bg.owned) return fail(RF_ERR_BUSY, "plan is in use by another call");
   DeviceGuard dg(p->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  rf_status s = ingest(p, vis, nint, st);
+  s = ingest(p, vis, nint, st);
   if (s != RF_OK) return s;
   s = resample_all(p, nint, st);
   if (s != RF_OK) return s;
-  std::vector<int4> info(n);
-  std::vector<Group> grp(n);
-  for (int k = 0; k < n; ++k) {
-    info[k] = make_int4(trials[3 * k], trials[3 * k + 1], trials[3 * k + 2], 0);
-    grp[k] = Group{trials[3 * k], trials[3 * k + 1], trials[3 * k + 2], 1, k, {0, 0, 0}};
-  }
-  p->cached_nint = -1;  // the lists below replace the cached search lists
-  p->drop_graph();
-  RF_CUDA(cudaMemcpyAsync(p->d_img_info, info.data(), n * sizeof(int4), cudaMemcpyHostToDevice, st));
-  RF_CUDA(cudaMemcpyAsync(p->d_groups, grp.data(), n * sizeof(Group), cudaMemcpyHostToDevice, st));
-  std::vector<Wave> waves;
-  const int per_wave = std::min(p->slots_max, p->gslots_max);  // single-image groups
-  for (int k = 0; k < n; k += per_wave) {
-    const int e = std::min(n, k + per_wave);
-    waves.push_back(Wave{k, e, k, e});
-  }
   const size_t npx = (size_t)p->npix * p->npix;
   float* d_img = nullptr;
   cudaError_t e = cudaMalloc(&d_img, (size_t)n * npx * sizeof(float));
@@ -1219,8 +1260,7 @@ rf_status rf_render_images(rf_plan* p, const void* vis, int32_t nint, void* stre
     cudaGetLastError();
     return fail(RF_ERR_NO_MEMORY, "render buffer: %s", cudaGetErrorString(e));
   }
-  RF_CUDA(cudaMemsetAsync(p->d_ncand, 0, sizeof(int), st));
-  s = run_waves(p, nint, waves, n, nullptr, d_img, st);
+  s = render_core(p, nint, trials, n, d_img, st);
   if (s == RF_OK) {
     e = cudaMemcpyAsync(images, d_img, (size_t)n * npx * sizeof(float), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1230,6 +1270,101 @@ rf_status rf_render_images(rf_plan* p, const void* vis, int32_t nint, void* stre
   p->prof.collect();
   cudaFree(d_img);
   return s;
+}
+
+rf_status rf_candidate_products(rf_plan* p, const void* vis, int32_t nint, void* stream, const rf_candidate* cands,
+                                int32_t n, rf_candidate_features* features, float* spectra, float* images) {
+  if (!p) return fail(RF_ERR_INVALID_ARG, "plan is NULL");
+  if (p->host_only) return fail(RF_ERR_INVALID_ARG, "plan was created with RF_HOST_ONLY");
+  if (!vis || !cands || !features || n < 1) return fail(RF_ERR_INVALID_ARG, "bad candidate-product arguments");
+  if (nint < 1 || nint > p->max_nint) return fail(RF_ERR_SHAPE, "nint %d out of [1, %d]", nint, p->max_nint);
+  std::vector<int32_t> trials(3 * (size_t)n);
+  std::vector<rf::CandRef> refs(n);
+  for (int k = 0; k < n; ++k) {
+    const rf_candidate& c = cands[k];
+    if (c.x < 0 || c.x >= p->npix || c.y < 0 || c.y >= p->npix)
+      return fail(RF_ERR_INVALID_ARG, "candidate %d pixel (%d, %d) outside the image", k, c.x, c.y);
+    trials[3 * k] = c.dm_idx;
+    trials[3 * k + 1] = c.dt_idx;
+    trials[3 * k + 2] = c.t_idx;
+    refs[k] = rf::CandRef{c.dm_idx, c.dt_idx, c.t_idx, c.x, c.y, {0, 0, 0}};
+  }
+  rf_status s = check_trials(p, nint, trials.data(), n);
+  if (s != RF_OK) return s;
+  BusyGuard bg(&p->busy);
+  if (!bg.owned) return fail(RF_ERR_BUSY, "plan is in use by another call");
+  DeviceGuard dg(p->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s = ingest(p, vis, nint, st);
+  if (s != RF_OK) return s;
+  s = resample_all(p, nint, st);
+  if (s != RF_OK) return s;
+  if (!p->d_cellbc) {  // per-row (iu, iv) table, built on first use
+    std::vector<int2> cb((size_t)p->nbl * p->nchan);
+    for (int b = 0; b < p->nbl; ++b)
+      for (int c = 0; c < p->nchan; ++c) {
+        const size_t k = (size_t)b * p->nchan + c;
+        cb[(size_t)c * p->nbl + b] = p->ongrid[k] ? make_int2(p->iu[k], p->iv[k]) : make_int2(rf::kOffGrid, 0);
+      }
+    s = p->dalloc(&p->d_cellbc, cb.size());
+    if (s != RF_OK) return s;
+    RF_CUDA(cudaMemcpyAsync(p->d_cellbc, cb.data(), cb.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+  }
+  const size_t npx = (size_t)p->npix * p->npix;
+  const size_t nch = (size_t)p->nchan;
+  // scratch: refs, FP64 spectra and weights, FP32 spectra, moments; images in chunks
+  const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n, (size_t)(1ull << 30) / (npx * sizeof(float))));
+  DeviceScratch sc;
+  rf::CandRef* d_refs = nullptr;
+  double2* d_spec = nullptr;
+  double* d_wch = nullptr;
+  float2* d_spec32 = nullptr;
+  double* d_smom = nullptr;
+  double* d_imom = nullptr;
+  float* d_img = nullptr;
+  if ((s = sc.get(&d_refs, n)) != RF_OK || (s = sc.get(&d_spec, n * nch)) != RF_OK ||
+      (s = sc.get(&d_wch, n * nch)) != RF_OK || (s = sc.get(&d_smom, (size_t)n * 6)) != RF_OK ||
+      (s = sc.get(&d_imom, (size_t)n * 4)) != RF_OK || (s = sc.get(&d_img, (size_t)chunk * npx)) != RF_OK)
+    return s;
+  if (spectra && (s = sc.get(&d_spec32, n * nch)) != RF_OK) return s;
+  RF_CUDA(cudaMemcpyAsync(d_refs, refs.data(), n * sizeof(rf::CandRef), cudaMemcpyHostToDevice, st));
+  const SegmentGeom g = geom(p, nint);
+  RF_CUDA(rf::launch_cand_spectrum(g, p->tb, p->d_cellbc, d_refs, n, d_spec, d_wch, d_spec32, d_smom, st));
+  for (int k0 = 0; k0 < n; k0 += chunk) {
+    const int m = std::min(chunk, n - k0);
+    s = render_core(p, nint, trials.data() + 3 * (size_t)k0, m, d_img, st);
+    if (s != RF_OK) return s;
+    RF_CUDA(rf::launch_image_moments(d_img, m, npx, d_imom + (size_t)k0 * 4, st));
+    if (images)
+      RF_CUDA(cudaMemcpyAsync(images + (size_t)k0 * npx, d_img, (size_t)m * npx * sizeof(float),
+                              cudaMemcpyDeviceToHost, st));
+  }
+  std::vector<double> smom((size_t)n * 6), imom((size_t)n * 4);
+  RF_CUDA(cudaMemcpyAsync(smom.data(), d_smom, smom.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  RF_CUDA(cudaMemcpyAsync(imom.data(), d_imom, imom.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (spectra)
+    RF_CUDA(cudaMemcpyAsync(spectra, d_spec32, n * nch * sizeof(float2), cudaMemcpyDeviceToHost, st));
+  RF_CUDA(cudaStreamSynchronize(st));
+  p->prof.collect();
+  for (int k = 0; k < n; ++k) {
+    rf_candidate_features& f = features[k];
+    f.dm_idx = refs[k].d;
+    f.dt_idx = refs[k].s;
+    f.t_idx = refs[k].t;
+    f.x = refs[k].x;
+    f.y = refs[k].y;
+    f.nchan_used = (int32_t)smom[6 * k + 5];
+    f.image_mean = imom[4 * k];
+    f.image_sigma = imom[4 * k + 1];
+    f.image_skew = imom[4 * k + 2];
+    f.image_kurtosis = imom[4 * k + 3];
+    f.spec_mean = smom[6 * k];
+    f.spec_std = smom[6 * k + 1];
+    f.spec_skew = smom[6 * k + 2];
+    f.spec_kurtosis = smom[6 * k + 3];
+    f.peak_from_spectrum = smom[6 * k + 4];
+  }
+  return RF_OK;
 }
 
 rf_status rf_plan_set_form(rf_plan* plan, int32_t form) {

@@ -54,6 +54,15 @@ struct Group {
   int32_t pad[3];
 };
 
+// A candidate whose products are computed: trial (d, s, t') and pixel (x, y).
+struct CandRef {
+  int32_t d, s, t, x, y;
+  int32_t pad[3];
+};
+
+// Cell of an off-grid (baseline, channel) in the per-row cell table.
+constexpr int kOffGrid = -2147483647 - 1;
+
 // Row-block partial statistics of one image (raw pixel units).
 struct StatPartial {
   double sum;
@@ -176,6 +185,15 @@ bool image_kernel_shape(int npix, ImageKernelShape* out);
 
 // Sets the thread-local message returned by rf_last_error().
 void set_last_error(const char* msg);
+
+// Candidate products.  cellbc[c * nbl + b] = (iu, iv) or (kOffGrid, 0).
+// spec/wch: [n][nchan] FP64 spectrum and w_c; spec_out: FP32 copy or NULL;
+// spec_mom: [n][6] {mean, std, skew, excess kurtosis, w-mean, channels}.
+cudaError_t launch_cand_spectrum(const SegmentGeom& g, const DevTables& tb, const int2* cellbc, const CandRef* refs,
+                                 int n, double2* spec, double* wch, float2* spec_out, double* spec_mom,
+                                 cudaStream_t st);
+// out: [n][4] {mean, std, skew, excess kurtosis} of each image's npx pixels.
+cudaError_t launch_image_moments(const float* images, int n, size_t npx, double* out, cudaStream_t st);
 
 // ---------------------------------------------------------- host helpers --
 // For the stream runtime (host code only).
