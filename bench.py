@@ -247,14 +247,18 @@ def load_traffic(kernel, images_per_launch):
     return k["dram_bytes_per_image"] * images_per_launch
 
 
+KERNEL_SOURCES = ("rf_fft.cuh", "rf_image.cuh", "rf_image_small.cu", "rf_image_large.cu", "rf_kernels.cu")
+
+
 def source_hash():
+    """Hash of the sources of the search kernels whose DRAM traffic the
+    committed ncu summary records."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1802_03084_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
