@@ -145,13 +145,19 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_A, 2)
       const int nrounds = (nk + K::XA - 1) / K::XA;
       for (int rd = 0; rd < nrounds; ++rd) {
         const int kl = rd * K::XA + xf;
-        for (int i = t; i < K::STRIDE; i += K::T) buf[i] = make_float2(0.f, 0.f);
-        fft_sync<K::T>(xf);
-        if (kl < nk) {
-          const int kc = kl >> 1;
-          const int ko = kl & 1;
-          for (int c = t; c < ncells; c += K::T) buf[padx(crow[c])] = cellv[c * PI + 2 * (kc ^ (c & (CPC - 1))) + ko];
+        const int kc = kl >> 1;
+        const int ko = kl & 1;
+        // zero the transform's buffer, 16 bytes at a time where STRIDE is
+        // even (then every transform's buffer starts 16-byte aligned)
+        if constexpr (K::STRIDE % 2 == 0) {
+          float4* buf4 = reinterpret_cast<float4*>(buf);
+          for (int i = t; i < K::STRIDE / 2; i += K::T) buf4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+          for (int i = t; i < K::STRIDE; i += K::T) buf[i] = make_float2(0.f, 0.f);
         }
+        fft_sync<K::T>(xf);
+        if (kl < nk)
+          for (int c = t; c < ncells; c += K::T) buf[padx(crow[c])] = cellv[c * PI + 2 * (kc ^ (c & (CPC - 1))) + ko];
         fft_sync<K::T>(xf);
         float2 v[K::E];
         fft_inverse_to_regs<N>(v, buf, tb.twiddle, t, xf);
@@ -279,27 +285,34 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     // per-row-pair statistics: the max pixel and its lowest index (the
     // noise comes from the grid by Parseval's identity, see k_colfft)
     const int y = y0 + 2 * xf;
-    float lmax = -FLT_MAX;
     constexpr int LP = FftShape<N>::LAST_P;
-    float scale = 0.f;
+    constexpr int EM = K::E / LP;
     if (images != nullptr) {
       const double W = weight[img_base + slot];
-      scale = W > 0.0 ? (float)(0.5 / W) : 0.f;
-    }
+      const float scale = W > 0.0 ? (float)(0.5 / W) : 0.f;
+      float* im = images + ((size_t)slot * N + y) * N;
 #pragma unroll
-    for (int m = 0; m < K::E / LP; ++m) {
+      for (int m = 0; m < EM; ++m)
 #pragma unroll
-      for (int q = 0; q < LP; ++q) {
-        const float2 z = v[m * LP + dft_perm<LP>(q)];
-        lmax = fmaxf(lmax, fmaxf(z.x, z.y));
-        if (images != nullptr) {
+        for (int q = 0; q < LP; ++q) {
+          const float2 z = v[m * LP + dft_perm<LP>(q)];
           const int o = fft_out_index<N>(t, m, q);
-          float* im = images + ((size_t)slot * N + y) * N;
           im[o] = z.x * scale;
           im[N + o] = z.y * scale;
         }
-      }
     }
+    // max of row y (real parts) and of row y + 1 (imaginary parts), four
+    // independent chains each
+    float mxa[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
+    float mya[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
+#pragma unroll
+    for (int e = 0; e < K::E; ++e) {
+      mxa[e & 3] = fmaxf(mxa[e & 3], v[e].x);
+      mya[e & 3] = fmaxf(mya[e & 3], v[e].y);
+    }
+    const float mx = fmaxf(fmaxf(mxa[0], mxa[1]), fmaxf(mxa[2], mxa[3]));
+    const float my = fmaxf(fmaxf(mya[0], mya[1]), fmaxf(mya[2], mya[3]));
+    const float lmax = fmaxf(mx, my);
     // reduce over the transform's T threads (a warp, a part of one, or
     // several warps joined through shared memory)
     constexpr int WL = K::T < 32 ? K::T : 32;
@@ -307,18 +320,30 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     float wmax = lmax;
 #pragma unroll
     for (int off = WL / 2; off > 0; off >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(MASK, wmax, off));
+    // a lane holding the maximum finds its lowest index: row y comes before
+    // row y + 1, and within a row the lane's outputs ascend with (q, m)
     int best = INT_MAX;
     if (lmax == wmax) {
+      if (mx == wmax) {
 #pragma unroll
-      for (int m = 0; m < K::E / LP; ++m) {
+        for (int q = 0; q < LP; ++q)
 #pragma unroll
-        for (int q = 0; q < LP; ++q) {
-          const float2 z = v[m * LP + dft_perm<LP>(q)];
-          const int o = fft_out_index<N>(t, m, q);
-          if (z.x == wmax) best = min(best, y * N + o);
-          if (z.y == wmax) best = min(best, (y + 1) * N + o);
-        }
+          for (int m = 0; m < EM; ++m)
+            if (v[m * LP + dft_perm<LP>(q)].x == wmax) {
+              best = y * N + fft_out_index<N>(t, m, q);
+              goto found;
+            }
+      } else {
+#pragma unroll
+        for (int q = 0; q < LP; ++q)
+#pragma unroll
+          for (int m = 0; m < EM; ++m)
+            if (v[m * LP + dft_perm<LP>(q)].y == wmax) {
+              best = (y + 1) * N + fft_out_index<N>(t, m, q);
+              goto found;
+            }
       }
+    found:;
     }
 #pragma unroll
     for (int off = WL / 2; off > 0; off >>= 1) best = min(best, __shfl_xor_sync(MASK, best, off));
