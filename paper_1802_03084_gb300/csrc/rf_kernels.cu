@@ -199,8 +199,10 @@ __device__ __forceinline__ float2 load_s(const unsigned char* __restrict__ S, si
   return __ldg(reinterpret_cast<const float2*>(S) + i);
 }
 
+constexpr int kGatherBatch = 4;  // samples each lane has in flight (swept: 4 at 6 blocks per SM beat 8-32 at 2-5)
+
 template <bool FP16>
-__global__ void __launch_bounds__(256, 3) k_grid_cells(SegmentGeom g, DevTables tb, const Group* __restrict__ groups,
+__global__ void __launch_bounds__(256, 6) k_grid_cells(SegmentGeom g, DevTables tb, const Group* __restrict__ groups,
                                                     int g_begin, float2* __restrict__ cellbuf) {
   extern __shared__ int sdel[];  // [nchan] delays of this group's DM
   const int tid = threadIdx.x;
@@ -234,10 +236,10 @@ __global__ void __launch_bounds__(256, 3) k_grid_cells(SegmentGeom g, DevTables 
     const int mydel = mine ? sdel[my.cflags >> 2] : 0;
     const int mypart = (mydel % dt) * lp + mydel / dt;
     const int n = min(32, eend - base);
-    for (int i0 = 0; i0 < n; i0 += 16) {
-      float2 a[16];
+    for (int i0 = 0; i0 < n; i0 += kGatherBatch) {
+      float2 a[kGatherBatch];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
+      for (int q = 0; q < kGatherBatch; ++q) {
         const int i = (i0 + q) & 31;
         const int bc = __shfl_sync(0xffffffffu, my.bc, i);
         const int del = __shfl_sync(0xffffffffu, mydel, i);
@@ -246,7 +248,7 @@ __global__ void __launch_bounds__(256, 3) k_grid_cells(SegmentGeom g, DevTables 
         if (active && i0 + q < n && del < lim) a[q] = load_s<FP16>(Sd, (size_t)bc * rowpitch + part + tq);
       }
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
+      for (int q = 0; q < kGatherBatch; ++q) {
         const int i = (i0 + q) & 31;
         const int cf = __shfl_sync(0xffffffffu, my.cflags, i);
         const int cell = __shfl_sync(0xffffffffu, my.cell, i);
