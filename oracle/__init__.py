@@ -24,7 +24,12 @@ from .realfast_oracle import (  # noqa: F401
     image_stats,
     moments,
     n_valid_times,
+    periodic_dm_trials,
+    periodic_image,
+    periodic_series_transform,
+    periodic_stats,
     round_half_away,
+    search_periodic,
     search_segment,
     search_stream,
     stream_overlap,

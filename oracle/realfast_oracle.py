@@ -446,3 +446,100 @@ def candidate_features(plan: OraclePlan, S: np.ndarray, d: int, s: int, t: int, 
                 spec_mean=sp[0], spec_std=sp[1], spec_skew=sp[2], spec_kurtosis=sp[3],
                 peak_from_spectrum=float((w * spec.real).sum() / w.sum()), nchan_used=int(used.sum()),
                 spectrum=spec, image=I)
+
+
+# ----------------------------------------------------------------------------
+# Periodicity search (Sec. 3.1 footnote: a time segment is Fourier transformed
+# and each fluctuation frequency imaged; Fig. 2: a change of the innermost loop)
+# ----------------------------------------------------------------------------
+
+def periodic_series_transform(plan: OraclePlan, S: np.ndarray, d: int, L: int, ks: Sequence[int]):
+    """Cosine and sine sums of the dedispersed series of DM trial d.
+
+    For each (b, c) the series is x[t] = S[t + delta[d][c]][b, c], t < L (the
+    window starts at the segment start, the whole sweep inside it).  For each
+    fluctuation frequency k:
+
+        U_k[b,c] = (1/L) sum_t x[t] cos(2 pi k t / L),
+        Q_k[b,c] = (1/L) sum_t x[t] sin(2 pi k t / L).
+
+    Returns complex arrays U, Q of shape [len(ks), nbl, nchan]."""
+    nbl, nchan = S.shape[1], S.shape[2]
+    t = np.arange(L)
+    X = np.zeros((L, nbl, nchan), dtype=np.complex128)
+    cidx = np.arange(nchan)
+    for ti in range(L):
+        X[ti] = S[ti + plan.delays[d][cidx], np.arange(nbl)[:, None], cidx[None, :]]
+    U = np.zeros((len(ks), nbl, nchan), dtype=np.complex128)
+    Q = np.zeros((len(ks), nbl, nchan), dtype=np.complex128)
+    for j, k in enumerate(ks):
+        c = np.cos(2 * np.pi * k * t / L) / L
+        s = np.sin(2 * np.pi * k * t / L) / L
+        U[j] = np.tensordot(c, X, axes=(0, 0))
+        Q[j] = np.tensordot(s, X, axes=(0, 0))
+    return U, Q
+
+
+def periodic_image(plan: OraclePlan, U: np.ndarray, Q: np.ndarray):
+    """Power image of one fluctuation frequency.
+
+    A source whose flux varies as A(t) has visibility A(t) e^{-i theta_b} on
+    baseline b and A(t) e^{+i theta_b} on its mirror; imaging the time
+    transform at frequency k over both gives 2 (I_U - i I_Q), with I_U and
+    I_Q the ordinary dirty images (Sec. 3.1 arithmetic, weight W = on-grid
+    pairs) of U and Q.  The power image is P = I_U^2 + I_Q^2; a flux
+    A1 cos(2 pi k t / L + psi) at a pixel gives sqrt(P) = A1 / 2 there.
+    Returns (I_U, I_Q, P)."""
+    W = float(plan.ongrid.sum())
+    IU = dirty_image_fft(grid_full_plane(U, plan.iu, plan.iv, plan.ongrid, plan.npix), W)
+    IQ = dirty_image_fft(grid_full_plane(Q, plan.iu, plan.iv, plan.ongrid, plan.npix), W)
+    return IU, IQ, IU * IU + IQ * IQ
+
+
+@dataclasses.dataclass
+class PeriodicStats:
+    amplitude: float   # sqrt(max P)
+    sigma: float       # per-quadrature noise: sqrt((var(I_U) + var(I_Q)) / 2)
+    x: int
+    y: int
+    snr: float         # amplitude / sigma
+
+
+def periodic_stats(IU: np.ndarray, IQ: np.ndarray) -> PeriodicStats:
+    """Peak of the power image (lowest index on ties) against the noise of
+    the two quadrature images (population variances)."""
+    N = IU.shape[1]
+    P = (IU * IU + IQ * IQ).ravel()
+    k = int(np.argmax(P))
+    y, x = divmod(k, N)
+    sig = float(np.sqrt((IU.var() + IQ.var()) / 2.0))
+    amp = float(np.sqrt(P[k]))
+    return PeriodicStats(amp, sig, x, y, amp / sig if sig > 0 else 0.0)
+
+
+def periodic_dm_trials(plan: OraclePlan, nint: int, L: int) -> List[int]:
+    """DM trials whose whole window of L integrations and sweep fit in the segment."""
+    return [d for d in range(len(plan.dm_list)) if int(plan.max_delay[d]) + L <= nint]
+
+
+def search_periodic(plan: OraclePlan, vis: np.ndarray, L: int, kmin: int, kmax: int, threshold: float,
+                    nint: Optional[int] = None, with_stats: bool = False):
+    """Periodicity search of a segment: every DM trial whose window fits, every
+    k in [kmin, kmax] (1 <= kmin <= kmax <= L/2); a candidate (dm_idx, k, x,
+    y, snr) for each power image whose snr reaches the threshold."""
+    n = vis.shape[0] if nint is None else nint
+    S = plan.stokes(vis, n)
+    ks = list(range(kmin, kmax + 1))
+    cands, stats = [], {}
+    for d in periodic_dm_trials(plan, n, L):
+        U, Q = periodic_series_transform(plan, S, d, L, ks)
+        for j, k in enumerate(ks):
+            IU, IQ, _ = periodic_image(plan, U[j], Q[j])
+            st = periodic_stats(IU, IQ)
+            if with_stats:
+                stats[(d, k)] = st
+            if st.sigma > 0 and st.snr >= threshold:
+                cands.append(dict(dm_idx=d, k=k, x=st.x, y=st.y, snr=st.snr, amplitude=st.amplitude,
+                                  sigma=st.sigma))
+    cands.sort(key=lambda c: (c["dm_idx"], c["k"]))
+    return (cands, stats) if with_stats else cands
