@@ -66,7 +66,7 @@ typedef enum rf_status {
 #define RF_HOST_ONLY 0x100u
 
 /* ---- search forms (rf_plan_set_form) --------------------------------- */
-#define RF_FORM_BATCHED 0 /* all trials through the fused persistent launch */
+#define RF_FORM_BATCHED 0 /* all trials in waves of fused launches (a CUDA graph) */
 #define RF_FORM_PLAIN 1   /* one unfused launch set per (DM, dt) trial     */
 
 /*
@@ -435,6 +435,50 @@ typedef struct rf_candidate_features {
 rf_status rf_candidate_products(struct rf_plan* plan, const void* vis, int32_t nint, void* stream,
                                 const rf_candidate* cands, int32_t n, rf_candidate_features* features,
                                 float* spectra, float* images);
+
+/* ---- periodicity search ---------------------------------------------
+ * Sec. 3.1 (footnote): a time segment is Fourier transformed over time and
+ * each fluctuation frequency is imaged to search for periodic signals (Fig. 2:
+ * a change of the innermost loop).  For every DM trial whose window fits
+ * (max delay + L <= nint) and every (baseline, channel), the dedispersed
+ * window x[t] = S[t + delay[d][c]], t < L, gives at fluctuation frequency k
+ *   U_k = (1/L) sum_t x[t] cos(2 pi k t / L),  Q_k = (1/L) sum_t x[t] sin(2 pi k t / L).
+ * I_U and I_Q are their dirty images (the search's gridding and FFT, weight W =
+ * on-grid pairs); imaging the time transform over each baseline and its mirror
+ * gives 2 (I_U - i I_Q), so the power image is P = I_U^2 + I_Q^2.  A flux
+ * A1 cos(2 pi k t / L + psi) at a pixel gives amplitude sqrt(P) = A1 / 2 there.
+ * Per (DM, k): amplitude = sqrt(max P) (lowest pixel index on ties),
+ * sigma = sqrt((var(I_U) + var(I_Q)) / 2) (population variances over the N^2
+ * pixels), snr = amplitude / sigma; a candidate iff snr >= threshold.
+ */
+typedef struct rf_periodic_candidate {
+  int32_t dm_idx;
+  int32_t k;          /* fluctuation frequency index, kmin .. kmax           */
+  int32_t x;
+  int32_t y;
+  float snr;
+  float amplitude;
+  float sigma;
+  float pad;
+  double dm;
+  double freq_hz;     /* k / (L inttime_s)                                   */
+  double l_rad;
+  double m_rad;
+} rf_periodic_candidate;
+
+/* Periodicity search of one segment (vis and nint as for rf_search_segment).
+ * L: window length, a power of two in [16, 8192], L <= nint;
+ * 1 <= kmin <= kmax <= L/2; threshold > 0.  Candidates sorted by
+ * (dm_idx, k) go to out (RF_ERR_CAPACITY and *n_out = total if cap is too
+ * small).  stats (may be NULL) receives every (DM, k) searched, in the same
+ * order, with snr etc. set whether or not it is a candidate; *n_stats =
+ * (DM trials that fit) * (kmax - kmin + 1).  Device scratch is allocated for
+ * the call.  Errors: RF_ERR_INVALID_ARG, RF_ERR_SHAPE, RF_ERR_NO_MEMORY,
+ * RF_ERR_BUSY, RF_ERR_CAPACITY. */
+rf_status rf_periodicity_search(struct rf_plan* plan, const void* vis, int32_t nint, int32_t L, int32_t kmin,
+                                int32_t kmax, double threshold, void* stream, rf_periodic_candidate* out,
+                                size_t cap, size_t* n_out, rf_periodic_candidate* stats, size_t stats_cap,
+                                size_t* n_stats);
 
 /* ---- continuous search over overlapping segments ----------------------
  * A stream cuts an unbounded run of integrations into segments that overlap

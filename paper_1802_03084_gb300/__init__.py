@@ -27,6 +27,7 @@ __all__ = [
     "rf_plan_set_profiling", "rf_plan_get_profile", "RfKernelProfile", "rf_image_stats_noalloc", "rf_plan_set_tuning", "rf_plan_get_tuning", "rf_plan_autotune",
     "RfTuneReport", "Server", "RfServerDesc", "RfRequestInfo", "rf_plan_estimate_bytes",
     "Stream", "RfStreamInfo", "RfCandidateFeatures", "FEATURES_DTYPE", "rf_candidate_products",
+    "RfPeriodicCandidate", "PERIODIC_DTYPE", "rf_periodicity_search",
     "Plan", "CANDIDATE_DTYPE", "STAT_DTYPE", "declared_symbols",
     "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_MEAN_SUBTRACT", "RF_STREAM_KEEP_STATS", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
 ]
@@ -128,6 +129,13 @@ class RfCandidateFeatures(ctypes.Structure):
                 ("peak_from_spectrum", ctypes.c_double)]
 
 
+class RfPeriodicCandidate(ctypes.Structure):
+    _fields_ = [("dm_idx", ctypes.c_int32), ("k", ctypes.c_int32), ("x", ctypes.c_int32), ("y", ctypes.c_int32),
+                ("snr", ctypes.c_float), ("amplitude", ctypes.c_float), ("sigma", ctypes.c_float),
+                ("pad", ctypes.c_float), ("dm", ctypes.c_double), ("freq_hz", ctypes.c_double),
+                ("l_rad", ctypes.c_double), ("m_rad", ctypes.c_double)]
+
+
 class RfStreamInfo(ctypes.Structure):
     _fields_ = [("stride", ctypes.c_int32), ("overlap", ctypes.c_int32), ("segment_nint", ctypes.c_int32),
                 ("fill", ctypes.c_int32), ("pushed", ctypes.c_int64), ("segments", ctypes.c_int64),
@@ -149,6 +157,7 @@ def _np_dtype(struct) -> np.dtype:
 CANDIDATE_DTYPE = _np_dtype(RfCandidate)
 STAT_DTYPE = _np_dtype(RfImageStat)
 FEATURES_DTYPE = _np_dtype(RfCandidateFeatures)
+PERIODIC_DTYPE = _np_dtype(RfPeriodicCandidate)
 
 _LIB = None
 
@@ -192,6 +201,8 @@ def lib() -> ctypes.CDLL:
         "rf_server_results": ([P, ctypes.c_int64, P, S, ctypes.POINTER(S)], ctypes.c_int),
         "rf_server_destroy": ([P], ctypes.c_int),
         "rf_plan_get_profile": ([P, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "rf_periodicity_search": ([P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_double, P, P, S, ctypes.POINTER(S), P, S, ctypes.POINTER(S)], ctypes.c_int),
         "rf_candidate_products": ([P, P, ctypes.c_int32, P, P, ctypes.c_int32, P, P, P], ctypes.c_int),
         "rf_stream_create": ([P, ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(P)], ctypes.c_int),
         "rf_stream_push": ([P, P, ctypes.c_int32, P, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
@@ -333,6 +344,24 @@ def rf_candidate_products(plan, vis, nint: int, cands, npix: int, nchan: int, sp
                                        feats.ctypes.data, sp.ctypes.data if spectra else None,
                                        im.ctypes.data if images else None))
     return feats[:n], (sp[:n] if spectra else None), (im[:n] if images else None)
+
+
+def rf_periodicity_search(plan, vis, nint: int, L: int, kmin: int, kmax: int, threshold: float, ndm: int,
+                          with_stats=False, stream=None):
+    """Periodicity search: candidates (PERIODIC_DTYPE) and, with_stats, every
+    searched (DM, k) in (dm_idx, k) order."""
+    cap = max(ndm * (kmax - kmin + 1), 1)
+    out = np.zeros(cap, dtype=PERIODIC_DTYPE)
+    st = np.zeros(cap if with_stats else 1, dtype=PERIODIC_DTYPE)
+    n_out = ctypes.c_size_t()
+    n_st = ctypes.c_size_t()
+    _check(lib().rf_periodicity_search(plan, _ptr(vis), nint, L, kmin, kmax, threshold, _stream(stream),
+                                       out.ctypes.data, cap, ctypes.byref(n_out),
+                                       st.ctypes.data if with_stats else None, cap if with_stats else 0,
+                                       ctypes.byref(n_st)))
+    if with_stats:
+        return out[:n_out.value], st[:n_st.value]
+    return out[:n_out.value]
 
 
 def rf_plan_set_form(plan, form: int) -> None:
@@ -542,6 +571,12 @@ class Plan:
 
     def render(self, vis, trials, nint=None, stream=None):
         return rf_render_images(self.handle, vis, nint if nint is not None else len(vis), trials, self.npix, stream)
+
+    def periodicity_search(self, vis, L, kmin, kmax, threshold, nint=None, with_stats=False, stream=None):
+        """Fourier transform over time and image each fluctuation frequency."""
+        nint = nint if nint is not None else len(vis)
+        return rf_periodicity_search(self.handle, vis, nint, L, kmin, kmax, threshold, self.desc.ndm, with_stats,
+                                     stream)
 
     def candidate_products(self, vis, cands, nint=None, spectra=True, images=True, stream=None):
         """Features (and spectra, images) of candidates of this segment."""

@@ -52,6 +52,7 @@ constexpr uint32_t kKnownFlags = RF_STORE_FP16 | RF_EDGE_PARTIAL | RF_MEAN_SUBTR
 constexpr size_t kStageBytes = 256ull << 20;   // host->device chunk of raw visibilities
 constexpr size_t kTBudgetBytes = 4096ull << 20;  // column-FFT scratch per wave
 constexpr int kRangeEntries = 64;                // target entries per gridding warp
+constexpr size_t kPeriodicBudgetBytes = 1ull << 30;  // transformed series per DM batch
 constexpr size_t kPlainBudgetBytes = 4096ull << 20;  // plain form: intermediates of one chunk
 
 // Round half away from zero: sign(x) floor(|x| + 1/2).
@@ -1364,6 +1365,183 @@ rf_status rf_candidate_products(rf_plan* p, const void* vis, int32_t nint, void*
     f.spec_kurtosis = smom[6 * k + 3];
     f.peak_from_spectrum = smom[6 * k + 4];
   }
+  return RF_OK;
+}
+
+rf_status rf_periodicity_search(rf_plan* p, const void* vis, int32_t nint, int32_t L, int32_t kmin, int32_t kmax,
+                                double threshold, void* stream, rf_periodic_candidate* out, size_t cap,
+                                size_t* n_out, rf_periodic_candidate* stats, size_t stats_cap, size_t* n_stats) {
+  if (!p) return fail(RF_ERR_INVALID_ARG, "plan is NULL");
+  if (p->host_only) return fail(RF_ERR_INVALID_ARG, "plan was created with RF_HOST_ONLY");
+  if (!vis || !n_out || (cap > 0 && !out) || (stats_cap > 0 && !stats))
+    return fail(RF_ERR_INVALID_ARG, "bad periodicity-search arguments");
+  if (nint < 1 || nint > p->max_nint) return fail(RF_ERR_SHAPE, "nint %d out of [1, %d]", nint, p->max_nint);
+  if (L < 16 || L > 8192 || (L & (L - 1)) || L > nint)
+    return fail(RF_ERR_INVALID_ARG, "L %d must be a power of two in [16, min(8192, nint)]", L);
+  if (kmin < 1 || kmax < kmin || kmax > L / 2)
+    return fail(RF_ERR_INVALID_ARG, "need 1 <= kmin <= kmax <= L/2 (kmin %d, kmax %d)", kmin, kmax);
+  if (!(threshold > 0.0) || !std::isfinite(threshold)) return fail(RF_ERR_INVALID_ARG, "threshold must be > 0");
+  BusyGuard bg(&p->busy);
+  if (!bg.owned) return fail(RF_ERR_BUSY, "plan is in use by another call");
+  DeviceGuard dg(p->device);
+  if (!dg.ok) return fail(RF_ERR_CUDA, "cannot select device %d", p->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  *n_out = 0;
+  if (n_stats) *n_stats = 0;
+  rf_status s = ingest(p, vis, nint, st);
+  if (s != RF_OK) return s;
+
+  std::vector<int> dms;  // DM trials whose window and sweep fit in the segment
+  for (int d = 0; d < p->ndm; ++d)
+    if ((int64_t)p->max_delay[d] + L <= nint) dms.push_back(d);
+  const int K = kmax - kmin + 1;
+  const int kpad = (K + 31) / 32 * 32;
+  const int B = p->shape.images_per_group;
+  const int nkb = (K + B - 1) / B;
+  const size_t nrows = (size_t)p->nbl * p->nchan;
+  const size_t per_dm = 2 * nrows * kpad * sizeof(float2);
+  const int ndms = (int)dms.size();
+  const int nb_max = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(ndms, 1), kPeriodicBudgetBytes / per_dm));
+  const size_t npairs_total = (size_t)ndms * K;
+
+  DeviceScratch sc;
+  float2* d_per = nullptr;
+  float2* d_twl = nullptr;
+  int* d_dms = nullptr;
+  int* d_zero = nullptr;
+  int* d_ones = nullptr;
+  int* d_lps = nullptr;
+  unsigned long long* d_sdt = nullptr;
+  Group* d_grp = nullptr;
+  int4* d_pairs = nullptr;
+  rf::DevPeriodic* d_pst = nullptr;
+  rf::DevPeriodic* d_pc = nullptr;
+  int* d_npc = nullptr;
+  if ((s = sc.get(&d_per, (size_t)nb_max * per_dm / sizeof(float2))) != RF_OK || (s = sc.get(&d_twl, L)) != RF_OK ||
+      (s = sc.get(&d_dms, nb_max)) != RF_OK || (s = sc.get(&d_zero, p->nchan)) != RF_OK ||
+      (s = sc.get(&d_ones, 2 * nb_max)) != RF_OK || (s = sc.get(&d_lps, 2 * nb_max)) != RF_OK ||
+      (s = sc.get(&d_sdt, 2 * nb_max)) != RF_OK || (s = sc.get(&d_grp, (size_t)nb_max * nkb * 2)) != RF_OK ||
+      (s = sc.get(&d_pairs, (size_t)nb_max * K)) != RF_OK || (s = sc.get(&d_pst, npairs_total)) != RF_OK ||
+      (s = sc.get(&d_pc, npairs_total)) != RF_OK || (s = sc.get(&d_npc, 1)) != RF_OK)
+    return s;
+  {
+    std::vector<float2> tw(L);
+    for (int m = 0; m < L; ++m) {
+      const double a = kTwoPi * (double)m / (double)L;
+      tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    RF_CUDA(cudaMemcpyAsync(d_twl, tw.data(), L * sizeof(float2), cudaMemcpyHostToDevice, st));
+    std::vector<int> ones(2 * nb_max, 1), lps(2 * nb_max, kpad);
+    RF_CUDA(cudaMemcpyAsync(d_ones, ones.data(), ones.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    RF_CUDA(cudaMemcpyAsync(d_lps, lps.data(), lps.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    RF_CUDA(cudaMemsetAsync(d_zero, 0, p->nchan * sizeof(int), st));
+    RF_CUDA(cudaMemsetAsync(d_npc, 0, sizeof(int), st));
+    std::vector<unsigned long long> sdt(2 * nb_max);
+    for (int q = 0; q < 2 * nb_max; ++q)
+      sdt[q] = (unsigned long long)(uintptr_t)(d_per + (size_t)q * nrows * kpad);
+    RF_CUDA(cudaMemcpyAsync(d_sdt, sdt.data(), sdt.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
+  }
+  // the search's gridding and column kernels, pointed at the transformed
+  // series: "dt index" 2 j + q selects trial j's U (q = 0) or Q (q = 1)
+  // series, delays are zero and "t'" is k - kmin
+  rf::DevTables tbp = p->tb;
+  tbp.delays = d_zero;
+  tbp.dt_list = d_ones;
+  tbp.sdt_ptr = d_sdt;
+  tbp.sdt_lp = d_lps;
+  const SegmentGeom g = geom(p, nint);
+  SegmentGeom gp = g;
+  gp.nint = K;
+  gp.fp16 = false;  // the transformed series are FP32 whatever the storage
+
+  for (int b0 = 0; b0 < ndms; b0 += nb_max) {
+    const int nb = std::min(nb_max, ndms - b0);
+    RF_CUDA(cudaMemcpyAsync(d_dms, dms.data() + b0, nb * sizeof(int), cudaMemcpyHostToDevice, st));
+    RF_CUDA(rf::launch_period_dft(g, p->d_S, p->tb.delays, d_dms, nb, L, d_twl, kmin, K, kpad, d_per, st));
+    // image list: per (trial j, block kb of up to B frequencies) a U group
+    // then a Q group; a wave holds whole blocks so that each pair's two
+    // images are in the same wave
+    std::vector<Group> grp;
+    std::vector<int4> pairs;
+    struct PW { int g0, g1, i0, i1, p0, p1; };
+    std::vector<PW> waves;
+    PW w{0, 0, 0, 0, 0, 0};
+    int nimg = 0;
+    for (int j = 0; j < nb; ++j)
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int n = std::min(B, K - kb * B);
+        if ((nimg + 2 * n) - w.i0 > p->slots_max || ((int)grp.size() + 2) - w.g0 > p->gslots_max) {
+          w.g1 = (int)grp.size();
+          w.i1 = nimg;
+          w.p1 = (int)pairs.size();
+          waves.push_back(w);
+          w = PW{w.g1, w.g1, nimg, nimg, w.p1, w.p1};
+        }
+        grp.push_back(Group{0, 2 * j, kb * B, n, nimg, {0, 0, 0}});
+        grp.push_back(Group{0, 2 * j + 1, kb * B, n, nimg + n, {0, 0, 0}});
+        for (int i = 0; i < n; ++i)
+          pairs.push_back(make_int4(nimg + i - w.i0, nimg + n + i - w.i0, dms[b0 + j], kmin + kb * B + i));
+        nimg += 2 * n;
+      }
+    w.g1 = (int)grp.size();
+    w.i1 = nimg;
+    w.p1 = (int)pairs.size();
+    if (w.i1 > w.i0) waves.push_back(w);
+    RF_CUDA(cudaMemcpyAsync(d_grp, grp.data(), grp.size() * sizeof(Group), cudaMemcpyHostToDevice, st));
+    RF_CUDA(cudaMemcpyAsync(d_pairs, pairs.data(), pairs.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    const size_t pbase = (size_t)b0 * K;
+    for (const PW& v : waves) {
+      const int ng = v.g1 - v.g0;
+      const int np = v.p1 - v.p0;
+      RF_CUDA(rf::launch_grid_cells(gp, tbp, d_grp, v.g0, ng, p->d_cellbuf, st));
+      RF_CUDA(rf::launch_colfft(gp, tbp, d_grp, v.g0, ng, v.i0, p->d_cellbuf, p->d_T, p->d_colsq, p->d_mean0, st));
+      RF_CUDA(rf::launch_rowfft_power(gp, tbp, p->d_T, d_pairs + v.p0, np, p->d_partials, st));
+      RF_CUDA(rf::launch_finalize_power(gp, p->d_partials, p->d_colsq, p->d_mean0, d_pairs + v.p0, np,
+                                        (int)(pbase + v.p0), (double)p->n_on, threshold, d_pst, d_pc, d_npc,
+                                        (int)npairs_total, st));
+    }
+    // the host lists above are reused by the next batch
+    RF_CUDA(cudaStreamSynchronize(st));
+  }
+  int npc = 0;
+  RF_CUDA(cudaMemcpyAsync(&npc, d_npc, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RF_CUDA(cudaStreamSynchronize(st));
+  npc = std::min(npc, (int)npairs_total);
+  std::vector<rf::DevPeriodic> pc(npc), pst;
+  if (npc > 0) RF_CUDA(cudaMemcpyAsync(pc.data(), d_pc, npc * sizeof(rf::DevPeriodic), cudaMemcpyDeviceToHost, st));
+  if (stats && npairs_total > 0) {
+    pst.resize(npairs_total);
+    RF_CUDA(cudaMemcpyAsync(pst.data(), d_pst, npairs_total * sizeof(rf::DevPeriodic), cudaMemcpyDeviceToHost, st));
+  }
+  RF_CUDA(cudaStreamSynchronize(st));
+  std::sort(pc.begin(), pc.end(), [](const rf::DevPeriodic& a, const rf::DevPeriodic& b) {
+    return a.d != b.d ? a.d < b.d : a.k < b.k;
+  });
+  const int half = p->npix / 2;
+  auto fill = [&](const rf::DevPeriodic& a, rf_periodic_candidate& o) {
+    o.dm_idx = a.d;
+    o.k = a.k;
+    o.x = a.x;
+    o.y = a.y;
+    o.snr = a.snr;
+    o.amplitude = a.amplitude;
+    o.sigma = a.sigma;
+    o.pad = 0.f;
+    o.dm = p->dm[a.d];
+    o.freq_hz = (double)a.k / ((double)L * p->inttime);
+    o.l_rad = (double)(a.x - half) * p->cell;
+    o.m_rad = (double)(a.y - half) * p->cell;
+  };
+  const size_t nw = std::min<size_t>(cap, pc.size());
+  for (size_t k = 0; k < nw; ++k) fill(pc[k], out[k]);
+  *n_out = pc.size();
+  if (n_stats) *n_stats = npairs_total;
+  if (stats) {
+    const size_t ns = std::min(stats_cap, npairs_total);
+    for (size_t k = 0; k < ns; ++k) fill(pst[k], stats[k]);
+    if (npairs_total > stats_cap) return fail(RF_ERR_CAPACITY, "%zu stats, capacity %zu", npairs_total, stats_cap);
+  }
+  if (pc.size() > cap) return fail(RF_ERR_CAPACITY, "%zu candidates, capacity %zu", pc.size(), cap);
   return RF_OK;
 }
 

@@ -54,6 +54,13 @@ struct Group {
   int32_t pad[3];
 };
 
+// Statistics of one periodicity pair (DM trial d, fluctuation frequency k).
+struct DevPeriodic {
+  int32_t d, k, x, y;
+  float amplitude, sigma, snr;
+  int32_t pad;
+};
+
 // A candidate whose products are computed: trial (d, s, t') and pixel (x, y).
 struct CandRef {
   int32_t d, s, t, x, y;
@@ -194,6 +201,19 @@ cudaError_t launch_cand_spectrum(const SegmentGeom& g, const DevTables& tb, cons
                                  cudaStream_t st);
 // out: [n][4] {mean, std, skew, excess kurtosis} of each image's npx pixels.
 cudaError_t launch_image_moments(const float* images, int n, size_t npx, double* out, cudaStream_t st);
+
+// Periodicity search.  Time transform of the dedispersed windows of nb DM
+// trials (dms[j] indexes delays) into out[(2 j + q) nrows + row][kk].
+cudaError_t launch_period_dft(const SegmentGeom& g, const void* S, const int* delays, const int* dms, int nb,
+                              int L, const float2* twl, int kmin, int K, int kpad, float2* out, cudaStream_t st);
+// Row pass over npairs (U, Q) image pairs: partials[j * N + y] = row maxima of I_U^2 + I_Q^2.
+cudaError_t launch_rowfft_power(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, const int4* pairs,
+                                int npairs, StatPartial* partials, cudaStream_t st);
+// Per pair: amplitude, sigma, snr, pixel; stats[pair_base + j]; candidates appended.
+cudaError_t launch_finalize_power(const SegmentGeom& g, const StatPartial* partials, const float* colsq,
+                                  const float* mean0, const int4* pairs, int npairs, int pair_base, double W,
+                                  double threshold, DevPeriodic* stats, DevPeriodic* cands, int* ncand, int cand_cap,
+                                  cudaStream_t st);
 
 // ---------------------------------------------------------- host helpers --
 // For the stream runtime (host code only).

@@ -392,6 +392,158 @@ inline int sm_count() {
   return n;
 }
 
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// Periodicity row pass (Sec. 3.1 footnote).  A pair is the two quadrature
+// images (U and Q) of one (DM trial, fluctuation frequency); work item =
+// (pair, block of XB rows), and each transform takes one row y with
+// Z[u] = T_U[u][y] + i T_Q[u][y] (Hermitian-extended as in the search's row
+// pass), so its output holds row y of I_U in the real parts and of I_Q in
+// the imaginary parts.  Per row it writes the maximum of I_U^2 + I_Q^2 (raw
+// pixel units) and its lowest index.  pairs[j] = {U slot, Q slot, -, -}.
+template <int N>
+__global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
+    k_rowfft_power(SegmentGeom g, DevTables tb, const float2* __restrict__ Tbuf, const int4* __restrict__ pairs,
+                   int npairs, StatPartial* __restrict__ partials) {
+  using K = ImgCfg<N>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* fbuf = reinterpret_cast<float2*>(smraw);                     // [XB][STRIDE]
+  float4* tile = reinterpret_cast<float4*>(fbuf + K::XB * K::STRIDE);  // [ncol][CH]
+  __shared__ float w_max[32];
+  __shared__ int w_idx[32];
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int wid = tid >> 5;
+  const int ncol = g.ncol;
+  constexpr int nrb = N / K::XB;  // row blocks per pair
+  const int nitems = npairs * nrb;
+  const int xf = tid / K::T;
+  const int t = tid - xf * K::T;
+
+  auto prefetch = [&](int it) {
+    const int pj = it / nrb;
+    const int yb = (it - pj * nrb) * K::XB;
+    const int4 pr = pairs[pj];
+    const float2* su = Tbuf + (size_t)pr.x * ncol * N + yb;
+    const float2* sq = Tbuf + (size_t)pr.y * ncol * N + yb;
+    for (int i = tid; i < ncol * K::CH; i += K::THREADS_B) {
+      const int u = i / K::CH;
+      const int c = i - u * K::CH;
+      float2* d = reinterpret_cast<float2*>(tile + u * K::CH + (c ^ (u & (K::CH - 1))));
+      cp_async8(d, su + (size_t)u * N + c);
+      cp_async8(d + 1, sq + (size_t)u * N + c);
+    }
+    cp_async_commit();
+  };
+
+  int item = blockIdx.x;
+  if (item < nitems) prefetch(item);
+  for (; item < nitems; item += gridDim.x) {
+    cp_async_wait_all();
+    __syncthreads();
+    const int pj = item / nrb;
+    const int y = (item - pj * nrb) * K::XB + xf;
+    float2 v[K::E];
+#pragma unroll
+    for (int r = 0; r < K::E; ++r) {
+      const int u = t + r * K::T;
+      float2 z = make_float2(0.f, 0.f);
+      if (u < ncol) {
+        const float4 ab = tile[u * K::CH + (xf ^ (u & (K::CH - 1)))];
+        z = (u == 0) ? make_float2(ab.x, ab.z) : make_float2(ab.x - ab.w, ab.y + ab.z);
+      } else if (N - u < ncol) {
+        const int uu = N - u;
+        const float4 ab = tile[uu * K::CH + (xf ^ (uu & (K::CH - 1)))];
+        z = make_float2(ab.x + ab.w, ab.z - ab.y);
+      }
+      v[r] = z;
+    }
+    __syncthreads();  // tile consumed: prefetch the next item
+    if (item + (int)gridDim.x < nitems) prefetch(item + gridDim.x);
+    fft_inverse_from_regs<N>(v, fbuf + xf * K::STRIDE, tb.twiddle, t, xf);
+
+    constexpr int LP = FftShape<N>::LAST_P;
+    constexpr int EM = K::E / LP;
+    float pa[4] = {-1.f, -1.f, -1.f, -1.f};
+#pragma unroll
+    for (int e = 0; e < K::E; ++e) pa[e & 3] = fmaxf(pa[e & 3], fmaf(v[e].x, v[e].x, v[e].y * v[e].y));
+    const float lmax = fmaxf(fmaxf(pa[0], pa[1]), fmaxf(pa[2], pa[3]));
+    constexpr int WL = K::T < 32 ? K::T : 32;
+    constexpr unsigned MASK = 0xffffffffu;
+    float wmax = lmax;
+#pragma unroll
+    for (int off = WL / 2; off > 0; off >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(MASK, wmax, off));
+    int best = INT_MAX;
+    if (lmax == wmax) {
+#pragma unroll
+      for (int q = 0; q < LP; ++q)
+#pragma unroll
+        for (int m = 0; m < EM; ++m) {
+          const float2 z = v[m * LP + dft_perm<LP>(q)];
+          if (fmaf(z.x, z.x, z.y * z.y) == wmax) {
+            best = y * N + fft_out_index<N>(t, m, q);
+            goto found;
+          }
+        }
+    found:;
+    }
+#pragma unroll
+    for (int off = WL / 2; off > 0; off >>= 1) best = min(best, __shfl_xor_sync(MASK, best, off));
+    float mx = wmax;
+    int mi = best;
+    if (K::T > 32) {
+      constexpr int WPT = K::T / 32;
+      const int wi = t >> 5;
+      if (lane == 0) {
+        w_max[wid] = wmax;
+        w_idx[wid] = best;
+      }
+      fft_sync<K::T>(xf);
+      if (t == 0) {
+        const int w0 = wid - wi;
+        mx = -1.f;
+        mi = INT_MAX;
+        for (int w = 0; w < WPT; ++w) max_merge(mx, mi, w_max[w0 + w], w_idx[w0 + w]);
+      }
+      fft_sync<K::T>(xf);
+    }
+    if (t == 0) {
+      StatPartial sp;
+      sp.sum = 0.0;
+      sp.sumsq = 0.0;
+      sp.max = mx;
+      sp.idx = mi;
+      sp.pad[0] = sp.pad[1] = 0;
+      partials[(size_t)pj * N + y] = sp;
+    }
+  }
+}
+
+template <int N>
+cudaError_t run_rowfft_power(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, const int4* pairs,
+                             int npairs, StatPartial* partials, cudaStream_t st) {
+  using K = ImgCfg<N>;
+  const int smem = K::SMEM_B_FIXED + g.ncol * K::CH * 16;
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_rowfft_power<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_rowfft_power<N>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  if (npairs <= 0) return cudaSuccess;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rowfft_power<N>, K::THREADS_B, smem);
+  if (e != cudaSuccess) return e;
+  const long nitems = (long)npairs * (N / K::XB);
+  const long grid = std::min<long>(nitems, (long)std::max(per_sm, 1) * sm_count());
+  k_rowfft_power<N><<<(int)grid, K::THREADS_B, smem, st>>>(g, tb, Tbuf, pairs, npairs, partials);
+  return cudaGetLastError();
+}
+
+
 template <int N>
 cudaError_t run_colfft(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin, int ngroups,
                        int img_base, const float2* cellbuf, float2* Tbuf, float* colsq, float* mean0,
@@ -451,6 +603,8 @@ void fill_shape(ImageKernelShape* o) {
                                      const float2*, float2*, float*, float*, cudaStream_t);                 \
   template cudaError_t run_rowfft_stats<N>(const SegmentGeom&, const DevTables&, const float2*, int, int,    \
                                            const double*, StatPartial*, float*, cudaStream_t);              \
-  template void fill_shape<N>(ImageKernelShape*);
+  template void fill_shape<N>(ImageKernelShape*);                                                           \
+  template cudaError_t run_rowfft_power<N>(const SegmentGeom&, const DevTables&, const float2*, const int4*, \
+                                           int, StatPartial*, cudaStream_t);
 
 }  // namespace rf

@@ -430,6 +430,9 @@ cudaError_t run_rowfft_stats(const SegmentGeom&, const DevTables&, const float2*
                              StatPartial*, float*, cudaStream_t);
 template <int N>
 void fill_shape(ImageKernelShape*);
+template <int N>
+cudaError_t run_rowfft_power(const SegmentGeom&, const DevTables&, const float2*, const int4*, int, StatPartial*,
+                             cudaStream_t);
 
 #define RF_FOR_EACH_N(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
 
@@ -454,6 +457,19 @@ cudaError_t launch_rowfft_stats(const SegmentGeom& g, const DevTables& tb, const
 #define RF_CASE(N) \
   case N:          \
     return run_rowfft_stats<N>(g, tb, Tbuf, nimg, img_base, weight, partials, images, st);
+    RF_FOR_EACH_N(RF_CASE)
+#undef RF_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_rowfft_power(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, const int4* pairs,
+                                int npairs, StatPartial* partials, cudaStream_t st) {
+  switch (g.npix) {
+#define RF_CASE(N) \
+  case N:          \
+    return run_rowfft_power<N>(g, tb, Tbuf, pairs, npairs, partials, st);
     RF_FOR_EACH_N(RF_CASE)
 #undef RF_CASE
     default:
