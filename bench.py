@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--serving-segments", type=int, default=16)
     ap.add_argument("--serving-slots", type=int, default=3)
     ap.add_argument("--serving-load", type=float, default=1.0, help="offered load in units of real time")
+    ap.add_argument("--next-rows", action="store_true",
+                    help="time the periodicity search, stream, mean subtraction and candidate products")
     ap.add_argument("--host-input", action="store_true",
                     help="time the search from pinned host input only (small device footprint for profilers)")
     return ap.parse_args()
@@ -420,6 +422,84 @@ def run_serving(args):
 
 
 # ------------------------------------------------------------------- engine --
+def run_next_rows(args):
+    """Times the rows around the search on the same segment (one GPU, events on
+    the default stream): the periodicity search, the overlapping-segment
+    stream, mean subtraction and candidate products.  One JSON line."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_1802_03084_gb300 as rf
+    from paper_1802_03084_gb300.build import build
+    build()
+    rf.lib()
+    spec = synth.config(args.config)
+    seg = synth.make_segment(spec)
+    nint = spec.nint
+    vis = torch.from_numpy(seg["vis"]).cuda()
+    torch.cuda.synchronize()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    line = {"metric": "rows around the search", "config": {"workload": workload_name(spec)}, "n_gpus": 1}
+    plan = rf.Plan.from_spec(spec, seg["ant_uvw"], seg["freq_hz"], max_nint=nint)
+    n_images = plan.count_images(nint)
+    ms, cands = timed(lambda: plan.search(vis, nint), 3)
+    line["search_ms"] = ms
+    # periodicity: L = 64, k = 1 .. 32 over every DM trial whose window fits
+    L, kmin, kmax = 64, 1, 32
+    pms, (pc, pst) = timed(lambda: plan.periodicity_search(vis, L, kmin, kmax, 7.0, nint, with_stats=True), 3)
+    line["periodicity"] = {"L": L, "k": [kmin, kmax], "pairs": int(len(pst)), "power_images": int(2 * len(pst)),
+                           "ms": pms, "images_per_s": 2 * len(pst) / (pms / 1e3), "candidates": int(len(pc))}
+    # candidate products of up to 64 candidates
+    c64 = cands[np.argsort(-cands["snr"])[:64]] if len(cands) else cands
+    if len(c64):
+        cms, _ = timed(lambda: plan.candidate_products(vis, c64, nint), 2)
+        line["candidate_products"] = {"candidates": int(len(c64)), "ms": cms}
+    plan.close()
+    # mean subtraction on the same search
+    spec_m = synth.config(args.config)
+    spec_m.mean_subtract = True
+    plan_m = rf.Plan.from_spec(spec_m, seg["ant_uvw"], seg["freq_hz"], max_nint=nint)
+    mms, _ = timed(lambda: plan_m.search(vis, nint), 3)
+    line["mean_subtract"] = {"ms": mms, "overhead_ms": mms - ms}
+    plan_m.close()
+    # stream: segments of nint integrations overlapping by the longest sweep,
+    # fed the same segment repeatedly in chunks of 128 integrations
+    plan_s = rf.Plan.from_spec(spec, seg["ant_uvw"], seg["freq_hz"], max_nint=nint)
+    overlap = int(plan_s.info().max_delay)
+    lcm = int(np.lcm.reduce(spec.dt_list))
+    stride = (nint - overlap) // lcm * lcm
+    reps = 4
+    with rf.Stream(plan_s, stride) as st:
+        st.push(vis, nint)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            for c0 in range(0, nint, 128):
+                st.push(vis[c0:c0 + 128], min(128, nint - c0))
+        t1 = time.perf_counter()
+        info = st.info()
+        st.pop()
+    plan_s.close()
+    ints = reps * nint
+    line["stream"] = {"stride": stride, "overlap": overlap, "segment_nint": stride + overlap,
+                      "integrations_per_s": ints / (t1 - t0),
+                      "realtime_factor": ints * spec.inttime_s / (t1 - t0), "segments": int(info["segments"])}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -429,6 +509,8 @@ def main():
         return run_reference(args, rank, world)
     if args.serving:
         return run_serving(args) if rank == 0 else 0
+    if args.next_rows:
+        return run_next_rows(args) if rank == 0 else 0
 
     import numpy as np
     import torch
