@@ -72,6 +72,27 @@ def parse():
     return ap.parse_args()
 
 
+# ----------------------------------------------------------- multi-rank --
+def rank_seed(seed, rank):
+    """Seed of rank `rank`'s segment: every rank searches its own segment."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(value, dist, device):
+    """The slowest rank's time, returned on every rank (no-op without dist)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, steps, units_per_rank, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * steps * units_per_rank / (ms / 1e3)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -530,7 +551,7 @@ def main():
     rf.lib()
 
     spec = synth.config(args.config)
-    spec.seed += 1000 * rank       # each rank searches its own segment
+    spec.seed = rank_seed(spec.seed, rank)   # each rank searches its own segment
     seg = synth.make_segment(spec)
     nint = spec.nint
     vis_pin = torch.from_numpy(seg["vis"]).pin_memory() if (not args.no_e2e or args.host_input) else None
@@ -567,10 +588,7 @@ def main():
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     prof = plan.profile()
     plan.set_profiling(False)
     n_cand = len(cands)
@@ -589,11 +607,8 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         ems = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ems], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * args.steps * n_images / (ems / 1e3), "unit": UNIT,
+        ems = max_over_ranks(ems, dist, "cuda")
+        e2e = {"value": job_rate(world, args.steps, n_images, ems), "unit": UNIT,
                "h2d_bytes_per_step": int(seg["vis"].nbytes),
                "d2h_bytes_per_step": int(4 + len(c2) * rf.CANDIDATE_DTYPE.itemsize),
                "ms_per_step": ems / args.steps}
@@ -609,7 +624,7 @@ def main():
         plan.search(vis_dev, nint)
     g1.record()
     torch.cuda.synchronize()
-    graph_value = world * args.steps * n_images / (g0.elapsed_time(g1) / 1e3)
+    graph_value = job_rate(world, args.steps, n_images, max_over_ranks(g0.elapsed_time(g1), dist, "cuda"))
     plain = None
     if not args.no_plain and args.form == "batched":
         plan.set_form(rf.RF_FORM_PLAIN)
@@ -628,7 +643,7 @@ def main():
     hbm_peak, peak_kind = peaks()
     roof, per_kernel = roofline(prof, spec, info, n_images, args.steps, fp16, hbm_peak, peak_kind)
     launches = sum(v[0] for k, v in prof.items() if k != "h2d_copy")
-    value = world * args.steps * n_images / (ms / 1e3)
+    value = job_rate(world, args.steps, n_images, ms)
     seg_s = nint * spec.inttime_s
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
