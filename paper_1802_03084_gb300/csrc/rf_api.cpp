@@ -2,6 +2,8 @@
 // (FP64 host tables), device buffers, and the orchestration of one segment
 // search.  Compiled with -ffp-contract=off so the FP64 table arithmetic is
 // plain IEEE double in the stated order.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -232,6 +234,8 @@ struct rf_plan {
   int* d_ncand = nullptr;
   DevStat* d_stats = nullptr;
   int2* d_cellbc = nullptr;     // [nchan * nbl] (iu, iv) per row, for candidate spectra
+  int* d_err = nullptr;         // set by a kernel whose bounded wait gave up
+  rf::TileMap tmap_T{};         // tensor map of d_T for the row pass (nbox 0: none)
   float2* d_stage = nullptr;
   int stage_nint = 0;
 
@@ -553,6 +557,53 @@ void build_lists(rf_plan* p, int nint) {
   p->drop_graph();
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+
+// Tensor map of the column-FFT output d_T ([slots][ncol][N] complex, seen as
+// FP32 pairs) for the row pass's tile copies, N >= 1024: the box is one
+// work item's 2 XB rows (XB 16-byte chunks) by `rows` columns u, swizzled so
+// that chunk c of column u lands at c ^ ((u >> sh) & (XB - 1)).  Where the
+// encoder is unavailable the row pass copies with cp.async (nbox = 0).
+void encode_tile_map(rf_plan* p) {
+  rf::TileMap& tm = p->tmap_T;
+  tm.nbox = 0;
+  const int N = p->npix;
+  if (N < 1024 || !p->d_T) return;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return;
+  const int xb = std::min(256 / (N / 32), N / 2);
+  int nbox, rows;
+  rf::tile_boxes(p->ncol, &nbox, &rows);
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * N, (cuuint64_t)p->ncol, (cuuint64_t)p->slots_max};
+  const cuuint64_t strides[2] = {(cuuint64_t)N * 8, (cuuint64_t)p->ncol * N * 8};
+  const cuuint32_t box[3] = {(cuuint32_t)(4 * xb), (cuuint32_t)rows, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUtensorMapSwizzle sw = xb == 8   ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : xb == 4 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                : xb == 2 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                          : CU_TENSOR_MAP_SWIZZLE_NONE;
+  const CUresult r = enc(&tm.map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p->d_T, dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r == CUDA_SUCCESS) {
+    tm.nbox = nbox;
+    tm.rows = rows;
+  }
+}
+
 // (Re)allocate the per-wave scratch for `slots` images (clamped to
 // [images_per_group, 32768]: images per wave ride on gridDim.y).
 rf_status alloc_wave_scratch(rf_plan* p, int slots) {
@@ -591,6 +642,7 @@ rf_status alloc_wave_scratch(rf_plan* p, int slots) {
   if ((s = p->dalloc(&p->d_cellbuf, (size_t)p->gslots_max * std::max(p->n_cells, 1) * 32)) != RF_OK) return s;
   if ((s = p->dalloc(&p->d_colsq, (size_t)slots * p->ncol)) != RF_OK) return s;
   if ((s = p->dalloc(&p->d_mean0, (size_t)slots)) != RF_OK) return s;
+  encode_tile_map(p);
   return RF_OK;
 }
 
@@ -615,7 +667,7 @@ uint64_t estimate_device_bytes(const rf_plan* p, int slots) {
   }
   b += r(p->dt.size(), 8) + r(p->dt.size(), 4);
   const int64_t img_cap = std::max<int64_t>(count_images(p, p->max_nint), 1);
-  b += r(img_cap, sizeof(int4)) + r(img_cap, sizeof(Group)) + r(img_cap, 8) + r(img_cap, sizeof(DevCand)) + 4;
+  b += r(img_cap, sizeof(int4)) + r(img_cap, sizeof(Group)) + r(img_cap, 8) + r(img_cap, sizeof(DevCand)) + 4 + 4;  // candidate count, error flag
   const size_t per_slot = (size_t)p->ncol * N * sizeof(float2);
   if (slots <= 0) slots = (int)std::min<size_t>(kTBudgetBytes / per_slot, (size_t)img_cap);
   const int B = p->shape.images_per_group;
@@ -717,6 +769,8 @@ rf_status alloc_device(rf_plan* p) {
   if ((s = p->dalloc(&p->d_weight, p->img_cap)) != RF_OK) return s;
   if ((s = p->dalloc(&p->d_cands, p->img_cap)) != RF_OK) return s;
   if ((s = p->dalloc(&p->d_ncand, 1)) != RF_OK) return s;
+  if ((s = p->dalloc(&p->d_err, 1)) != RF_OK) return s;
+  RF_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
 
   // column-FFT scratch, whole groups per wave
   const size_t per_slot = (size_t)p->ncol * N * sizeof(float2);
@@ -806,7 +860,8 @@ rf_status run_waves(rf_plan* p, int nint, const std::vector<Wave>& waves, int ni
                                p->d_colsq, p->d_mean0, st));
     float* im = d_images ? d_images + (size_t)w.img_begin * p->npix * p->npix : nullptr;
     RF_TIMED(p->prof, K_ROWFFT_STATS, st,
-             rf::launch_rowfft_stats(g, p->tb, p->d_T, ni, w.img_begin, p->d_weight, p->d_partials, im, st));
+             rf::launch_rowfft_stats(g, p->tb, p->d_T, ni, w.img_begin, p->d_weight, p->d_partials, im,
+                                     p->tmap_T.nbox > 0 ? &p->tmap_T : nullptr, p->d_err, st));
     RF_TIMED(p->prof, K_FINALIZE, st,
              rf::launch_finalize(g, p->d_partials, p->d_colsq, p->d_mean0, p->d_img_info, p->d_weight, ni,
                                  w.img_begin, p->threshold,
@@ -967,9 +1022,14 @@ rf_status search_impl(rf_plan* p, const void* vis, int nint, void* stream, rf_ca
       s = run_waves(p, nint, p->waves, nimg, d_stats, nullptr, st);
     if (s != RF_OK) return s;
   }
-  int ncand = 0;
+  int ncand = 0, kerr = 0;
   RF_CUDA(cudaMemcpyAsync(&ncand, p->d_ncand, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RF_CUDA(cudaMemcpyAsync(&kerr, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   RF_CUDA(cudaStreamSynchronize(st));
+  if (kerr) {
+    cudaMemset(p->d_err, 0, sizeof(int));
+    return fail(RF_ERR_TIMEOUT, "a row-pass tile copy did not complete within its wait limit");
+  }
   ncand = std::min(ncand, p->img_cap);
   std::vector<DevCand> dc(ncand);
   if (ncand > 0)
@@ -1064,6 +1124,11 @@ rf_status render_core(rf_plan* p, int nint, const int32_t* trials, int n, float*
   // the host-side lists above must outlive the copies
   cudaError_t e = cudaStreamSynchronize(st);
   if (s == RF_OK && e != cudaSuccess) s = fail(RF_ERR_CUDA, "render: %s", cudaGetErrorString(e));
+  int kerr = 0;
+  if (s == RF_OK && cudaMemcpy(&kerr, p->d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && kerr) {
+    cudaMemset(p->d_err, 0, sizeof(int));
+    s = fail(RF_ERR_TIMEOUT, "a row-pass tile copy did not complete within its wait limit");
+  }
   return s;
 }
 

@@ -2,6 +2,7 @@
 // (rf_api.cpp) and the CUDA kernels.  Plain C++ types only.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -53,6 +54,21 @@ struct Group {
   int32_t img0;  // index of the group's first image in the image list
   int32_t pad[3];
 };
+
+// Tensor map of a column-FFT output buffer T[slot][u][N] (as FP32 pairs) for
+// the row pass's tile copies: nbox boxes of `rows` u rows each cover ncol.
+struct TileMap {
+  CUtensorMap map;
+  int nbox;
+  int rows;
+};
+
+// Boxes of at most 256 rows (a multiple of 8) covering ncol rows.
+inline void tile_boxes(int ncol, int* nbox, int* rows) {
+  const int n0 = (ncol + 255) / 256;
+  *rows = ((ncol + n0 - 1) / n0 + 7) / 8 * 8;  // whole swizzle atoms per box
+  *nbox = (ncol + *rows - 1) / *rows;
+}
 
 // Statistics of one periodicity pair (DM trial d, fluctuation frequency k).
 struct DevPeriodic {
@@ -146,7 +162,7 @@ cudaError_t launch_colfft(const SegmentGeom& g, const DevTables& tb, const Group
 // first image index is img_base.  Optionally writes the scaled images.
 cudaError_t launch_rowfft_stats(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, int nimg,
                                 int img_base, const double* weight, StatPartial* partials, float* images,
-                                cudaStream_t st);
+                                const TileMap* tm, int* err, cudaStream_t st);
 
 // Reduce row-block partials, compute sigma / snr, append candidates and
 // (optionally) per-image stats for images [img_base, img_base + nimg).

@@ -21,6 +21,7 @@
 #include <limits.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "rf_engine.h"
 #include "rf_fft.cuh"
@@ -53,6 +54,13 @@ struct ImgCfg {
   static constexpr int CH = XB;                                  // 16-byte chunks per tile row
   static constexpr int STRIDE = fft_stride<N>();
   static constexpr int SMEM_B_FIXED = XB * STRIDE * 8;
+  // N >= 1024: the row-pass tile arrives by tensor copies (TMA) whose
+  // 16 CH-byte rows are swizzled by the hardware: chunk c of row u lands at
+  // c ^ ((u >> SWZ_SH) & (CH - 1)) for 128-, 64- and 32-byte rows.  The same
+  // pattern is used by the cp.async fallback and by every read of the tile.
+  static constexpr bool TILE_TMA = N >= 1024;
+  static constexpr int SWZ_SH = CH == 4 ? 1 : (CH == 2 ? 2 : 0);
+  __device__ static __forceinline__ int swz(int u, int c) { return c ^ ((u >> SWZ_SH) & (CH - 1)); }
   static_assert(T <= 32 || (XA <= 15 && XB <= 15), "named barriers: at most 15 wide transforms per block");
 };
 
@@ -62,6 +70,39 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// mbarrier and tensor-copy (TMA) helpers for the row-pass tile.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after about 2^20 polls (each may suspend briefly).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (int i = 0; i < (1 << 20); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
 
 template <bool FP16>
 __device__ __forceinline__ float2 load_sample(const void* __restrict__ S, size_t i);
@@ -192,18 +233,26 @@ __device__ __forceinline__ void max_merge(float& m, int& i, float m2, int i2) {
 // rows (FP32 per thread and pairwise across the transform's threads; the
 // N/2 partials of an image are added in FP64 by the finalisation) and the
 // max pixel with its lowest index.
+// With tma_boxes > 0 (N >= 1024 only) thread 0 fetches each item's tile with
+// tma_boxes tensor copies of tma_rows u rows from `tmap` ([slot][u][2N
+// floats]) and every thread waits on an mbarrier; a wait that gives up sets
+// *err and the block returns.  Otherwise the threads copy it with cp.async.
 template <int N>
 __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     k_rowfft_stats(SegmentGeom g, DevTables tb, const float2* __restrict__ Tbuf, int nimg, int img_base,
                    const double* __restrict__ weight, StatPartial* __restrict__ partials,
-                   float* __restrict__ images) {
+                   float* __restrict__ images, const __grid_constant__ CUtensorMap tmap, int tma_boxes,
+                   int tma_rows, int* __restrict__ err) {
   using K = ImgCfg<N>;
   constexpr int NWB = (K::THREADS_B + 31) / 32;
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* fbuf = reinterpret_cast<float2*>(smraw);                  // [XB][STRIDE]
-  float4* tile = reinterpret_cast<float4*>(fbuf + K::XB * K::STRIDE);  // [ncol][CH]
+  float2* fbuf = reinterpret_cast<float2*>(smraw);  // [XB][STRIDE]
+  unsigned char* tb0 = smraw + K::XB * K::STRIDE * 8;
+  if constexpr (K::TILE_TMA) tb0 += (1024u - (smem_u32(tb0) & 1023u)) & 1023u;  // swizzle atom alignment
+  float4* tile = reinterpret_cast<float4*>(tb0);    // [rows][CH]
   __shared__ float w_max[32];
   __shared__ int w_idx[32];
+  __shared__ __align__(8) unsigned long long tbar;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int wid = tid >> 5;
@@ -212,21 +261,46 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
   const int nitems = nimg * nrb;
   const int xf = tid / K::T;
   const int t = tid - xf * K::T;
+  const bool use_tma = K::TILE_TMA && tma_boxes > 0;
+  unsigned phase = 0;
+  if (use_tma) {
+    if (tid == 0) mbar_init(&tbar, 1);
+    __syncthreads();
+  }
+  auto fetch = [&](int it) {
+    const int sl = it / nrb;
+    const int yb = (it - sl * nrb) * K::RB;
+    if (use_tma) {
+      if (tid == 0) {
+        mbar_expect_tx(&tbar, (unsigned)(tma_boxes * tma_rows * K::CH * 16));
+        for (int b = 0; b < tma_boxes; ++b)
+          tma_load_3d(tile + (size_t)b * tma_rows * K::CH, &tmap, 2 * yb, b * tma_rows, sl, &tbar);
+      }
+    } else {
+      const float2* src = Tbuf + (size_t)sl * ncol * N + yb;
+      for (int i = tid; i < ncol * K::CH; i += K::THREADS_B) {
+        const int u = i / K::CH;
+        const int c = i - u * K::CH;
+        cp_async16(tile + u * K::CH + K::swz(u, c), src + (size_t)u * N + 2 * c);
+      }
+      cp_async_commit();
+    }
+  };
 
   int item = blockIdx.x;
-  if (item < nitems) {
-    const int slot = item / nrb;
-    const float2* src = Tbuf + (size_t)slot * ncol * N + (item - slot * nrb) * K::RB;
-    for (int i = tid; i < ncol * K::CH; i += K::THREADS_B) {
-      const int u = i / K::CH;
-      const int c = i - u * K::CH;
-      cp_async16(tile + u * K::CH + (c ^ (u & (K::CH - 1))), src + (size_t)u * N + 2 * c);
-    }
-    cp_async_commit();
-  }
+  if (item < nitems) fetch(item);
   for (; item < nitems; item += gridDim.x) {
-    cp_async_wait_all();
-    __syncthreads();
+    if (use_tma) {
+      const bool ok = mbar_wait(&tbar, phase);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(err, 1);
+        return;
+      }
+    } else {
+      cp_async_wait_all();
+      __syncthreads();
+    }
     const int slot = item / nrb;
     const int y0 = (item - slot * nrb) * K::RB;
     // first-pass inputs Z[u], u = t + r T: a + i b for 0 < u < ncol, the
@@ -234,12 +308,12 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     // u = 0, zero elsewhere (columns beyond iu_max are empty).  N/2 = 16 T,
     // so r < 16 can only be a direct column and r >= 16 only a mirror.
     float2 v[K::E];
-    if constexpr (K::E == 32 && K::T % K::CH == 0) {
-      // the swizzle term depends on u mod CH = t mod CH only
+    if constexpr (K::E == 32 && K::T % (K::CH << K::SWZ_SH) == 0) {
+      // the swizzle term of u = t + r T (or N - t - r T) is that of t (N - t)
       const int rd_end = ncol > t ? (ncol - t + K::T - 1) / K::T : 0;
       const int rm_beg = (N - ncol - t) / K::T + 1;
-      const float4* pd = tile + t * K::CH + (xf ^ (t & (K::CH - 1)));
-      const float4* pm = tile + (size_t)(N - t) * K::CH + (xf ^ ((N - t) & (K::CH - 1)));
+      const float4* pd = tile + t * K::CH + K::swz(t, xf);
+      const float4* pm = tile + (size_t)(N - t) * K::CH + K::swz(N - t, xf);
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
         float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -258,28 +332,18 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
         const int u = t + r * K::T;
         float2 z = make_float2(0.f, 0.f);
         if (u < ncol) {
-          const float4 ab = tile[u * K::CH + (xf ^ (u & (K::CH - 1)))];
+          const float4 ab = tile[u * K::CH + K::swz(u, xf)];
           z = (u == 0) ? make_float2(ab.x, ab.z) : make_float2(ab.x - ab.w, ab.y + ab.z);
         } else if (N - u < ncol) {
           const int uu = N - u;
-          const float4 ab = tile[uu * K::CH + (xf ^ (uu & (K::CH - 1)))];
+          const float4 ab = tile[uu * K::CH + K::swz(uu, xf)];
           z = make_float2(ab.x + ab.w, ab.z - ab.y);
         }
         v[r] = z;
       }
     }
     __syncthreads();  // tile consumed: prefetch the next item
-    const int next = item + gridDim.x;
-    if (next < nitems) {
-      const int ns = next / nrb;
-      const float2* src = Tbuf + (size_t)ns * ncol * N + (next - ns * nrb) * K::RB;
-      for (int i = tid; i < ncol * K::CH; i += K::THREADS_B) {
-        const int u = i / K::CH;
-        const int c = i - u * K::CH;
-        cp_async16(tile + u * K::CH + (c ^ (u & (K::CH - 1))), src + (size_t)u * N + 2 * c);
-      }
-      cp_async_commit();
-    }
+    if (item + (int)gridDim.x < nitems) fetch(item + gridDim.x);
     fft_inverse_from_regs<N>(v, fbuf + xf * K::STRIDE, tb.twiddle, t, xf);
 
     // per-row-pair statistics: the max pixel and its lowest index (the
@@ -562,12 +626,21 @@ cudaError_t run_colfft(const SegmentGeom& g, const DevTables& tb, const Group* g
   return cudaGetLastError();
 }
 
+// Rows of the row-pass tile: ncol, or the boxes' total under tensor copies.
+template <int N>
+int rowfft_tile_rows(int ncol) {
+  if (!ImgCfg<N>::TILE_TMA) return ncol;
+  int nbox, rows;
+  tile_boxes(ncol, &nbox, &rows);
+  return nbox * rows;
+}
+
 template <int N>
 cudaError_t run_rowfft_stats(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, int nimg,
                              int img_base, const double* weight, StatPartial* partials, float* images,
-                             cudaStream_t st) {
+                             const TileMap* tm, int* err, cudaStream_t st) {
   using K = ImgCfg<N>;
-  const int smem = K::SMEM_B_FIXED + g.ncol * K::CH * 16;
+  const int smem = K::SMEM_B_FIXED + (K::TILE_TMA ? 1024 : 0) + rowfft_tile_rows<N>(g.ncol) * K::CH * 16;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_rowfft_stats<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -580,7 +653,12 @@ cudaError_t run_rowfft_stats(const SegmentGeom& g, const DevTables& tb, const fl
   if (e != cudaSuccess) return e;
   const long nitems = (long)nimg * (N / K::RB);
   const long grid = std::min<long>(nitems, (long)std::max(per_sm, 1) * sm_count());
-  k_rowfft_stats<N><<<(int)grid, K::THREADS_B, smem, st>>>(g, tb, Tbuf, nimg, img_base, weight, partials, images);
+  const bool tma = K::TILE_TMA && tm != nullptr && tm->nbox > 0 && err != nullptr;
+  CUtensorMap none;
+  memset(&none, 0, sizeof(none));
+  k_rowfft_stats<N><<<(int)grid, K::THREADS_B, smem, st>>>(g, tb, Tbuf, nimg, img_base, weight, partials, images,
+                                                           tma ? tm->map : none, tma ? tm->nbox : 0,
+                                                           tma ? tm->rows : 0, err);
   return cudaGetLastError();
 }
 
@@ -602,7 +680,8 @@ void fill_shape(ImageKernelShape* o) {
   template cudaError_t run_colfft<N>(const SegmentGeom&, const DevTables&, const Group*, int, int, int,      \
                                      const float2*, float2*, float*, float*, cudaStream_t);                 \
   template cudaError_t run_rowfft_stats<N>(const SegmentGeom&, const DevTables&, const float2*, int, int,    \
-                                           const double*, StatPartial*, float*, cudaStream_t);              \
+                                           const double*, StatPartial*, float*, const TileMap*, int*,       \
+                                           cudaStream_t);                                                   \
   template void fill_shape<N>(ImageKernelShape*);                                                           \
   template cudaError_t run_rowfft_power<N>(const SegmentGeom&, const DevTables&, const float2*, const int4*, \
                                            int, StatPartial*, cudaStream_t);

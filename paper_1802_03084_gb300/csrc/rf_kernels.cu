@@ -427,7 +427,7 @@ cudaError_t run_colfft(const SegmentGeom&, const DevTables&, const Group*, int, 
                        float*, float*, cudaStream_t);
 template <int N>
 cudaError_t run_rowfft_stats(const SegmentGeom&, const DevTables&, const float2*, int, int, const double*,
-                             StatPartial*, float*, cudaStream_t);
+                             StatPartial*, float*, const TileMap*, int*, cudaStream_t);
 template <int N>
 void fill_shape(ImageKernelShape*);
 template <int N>
@@ -452,11 +452,11 @@ cudaError_t launch_colfft(const SegmentGeom& g, const DevTables& tb, const Group
 
 cudaError_t launch_rowfft_stats(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, int nimg,
                                 int img_base, const double* weight, StatPartial* partials, float* images,
-                                cudaStream_t st) {
+                                const TileMap* tm, int* err, cudaStream_t st) {
   switch (g.npix) {
 #define RF_CASE(N) \
   case N:          \
-    return run_rowfft_stats<N>(g, tb, Tbuf, nimg, img_base, weight, partials, images, st);
+    return run_rowfft_stats<N>(g, tb, Tbuf, nimg, img_base, weight, partials, images, tm, err, st);
     RF_FOR_EACH_N(RF_CASE)
 #undef RF_CASE
     default:

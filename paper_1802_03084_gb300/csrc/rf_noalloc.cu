@@ -207,7 +207,7 @@ cudaError_t run_noalloc(const float2* grid, double weight, const DeviceSetup& d,
   g.ncol = NC;
   DevTables tb{};
   tb.twiddle = tw;
-  e = launch_rowfft_stats(g, tb, T, 1, 0, nullptr, partials, nullptr, st);
+  e = launch_rowfft_stats(g, tb, T, 1, 0, nullptr, partials, nullptr, nullptr, nullptr, st);
   if (e != cudaSuccess) return e;
   k_noalloc_finalize<<<1, 32, 0, st>>>(partials, N / 2, colsq, mean0, N, weight, out);
   return cudaGetLastError();

@@ -110,6 +110,9 @@ def test_full_edge_rule_counts_and_parity():
     (128, 7, 5, 31, [3], True, 3),
     (256, 8, 9, 50, [1, 5], False, 4),
     (512, 9, 6, 19, [1, 2], True, 3),
+    # tensor-copy tiles in the row pass (N >= 1024): 128- and 64-byte swizzles, two and more boxes
+    (1024, 10, 4, 12, [1, 2], True, 3),
+    (2048, 6, 3, 6, [1], False, 2),
 ])
 def test_random_shapes(case):
     npix, nant, nchan, nint, dts, partial, ndm = case
