@@ -27,7 +27,7 @@ __all__ = [
     "rf_plan_set_profiling", "rf_plan_get_profile", "RfKernelProfile", "rf_image_stats_noalloc", "rf_plan_set_tuning", "rf_plan_get_tuning", "rf_plan_autotune",
     "RfTuneReport", "Server", "RfServerDesc", "RfRequestInfo", "rf_plan_estimate_bytes",
     "Stream", "RfStreamInfo", "RfCandidateFeatures", "FEATURES_DTYPE", "rf_candidate_products",
-    "RfPeriodicCandidate", "PERIODIC_DTYPE", "rf_periodicity_search",
+    "RfPeriodicCandidate", "PERIODIC_DTYPE", "rf_periodicity_search", "rf_selftest_bounded_wait",
     "Plan", "CANDIDATE_DTYPE", "STAT_DTYPE", "declared_symbols",
     "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_MEAN_SUBTRACT", "RF_STREAM_KEEP_STATS", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
 ]
@@ -203,6 +203,7 @@ def lib() -> ctypes.CDLL:
         "rf_plan_get_profile": ([P, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "rf_periodicity_search": ([P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.c_double, P, P, S, ctypes.POINTER(S), P, S, ctypes.POINTER(S)], ctypes.c_int),
+        "rf_selftest_bounded_wait": ([ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "rf_candidate_products": ([P, P, ctypes.c_int32, P, P, ctypes.c_int32, P, P, P], ctypes.c_int),
         "rf_stream_create": ([P, ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(P)], ctypes.c_int),
         "rf_stream_push": ([P, P, ctypes.c_int32, P, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
@@ -362,6 +363,13 @@ def rf_periodicity_search(plan, vis, nint: int, L: int, kmin: int, kmax: int, th
     if with_stats:
         return out[:n_out.value], st[:n_st.value]
     return out[:n_out.value]
+
+
+def rf_selftest_bounded_wait(device: int = 0, polls: int = 1000) -> int:
+    """1 if the device-side bounded wait gave up as it must (see the header)."""
+    g = ctypes.c_int32()
+    _check(lib().rf_selftest_bounded_wait(device, polls, ctypes.byref(g)))
+    return int(g.value)
 
 
 def rf_plan_set_form(plan, form: int) -> None:

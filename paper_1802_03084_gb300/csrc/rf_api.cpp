@@ -1610,6 +1610,29 @@ rf_status rf_periodicity_search(rf_plan* p, const void* vis, int32_t nint, int32
   return RF_OK;
 }
 
+rf_status rf_selftest_bounded_wait(int32_t device, int32_t polls, int32_t* gave_up) {
+  if (!gave_up || polls < 1 || polls > (1 << 20)) return fail(RF_ERR_INVALID_ARG, "need gave_up and 1 <= polls <= 2^20");
+  *gave_up = 0;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(RF_ERR_NO_DEVICE, "no CUDA device");
+  }
+  if (device < 0 || device >= ndev) return fail(RF_ERR_INVALID_ARG, "device %d out of range", device);
+  DeviceGuard dg(device);
+  if (!dg.ok) return fail(RF_ERR_CUDA, "cannot select device %d", device);
+  int* d = nullptr;
+  RF_CUDA(cudaMalloc(&d, sizeof(int)));
+  int h = 0;
+  cudaError_t e = cudaMemset(d, 0, sizeof(int));
+  if (e == cudaSuccess) e = rf::launch_wait_selftest(polls, d, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(RF_ERR_CUDA, "bounded-wait check: %s", cudaGetErrorString(e));
+  *gave_up = h;
+  return RF_OK;
+}
+
 rf_status rf_plan_set_form(rf_plan* plan, int32_t form) {
   if (!plan) return fail(RF_ERR_INVALID_ARG, "plan is NULL");
   if (form != RF_FORM_BATCHED && form != RF_FORM_PLAIN) return fail(RF_ERR_INVALID_ARG, "unknown form %d", form);

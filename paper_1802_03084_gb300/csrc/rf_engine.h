@@ -231,6 +231,10 @@ cudaError_t launch_finalize_power(const SegmentGeom& g, const StatPartial* parti
                                   double threshold, DevPeriodic* stats, DevPeriodic* cands, int* ncand, int cand_cap,
                                   cudaStream_t st);
 
+// One block waits, at most `polls` polls, on an mbarrier that nothing
+// arrives at; *status = 1 when the wait gave up (it always should).
+cudaError_t launch_wait_selftest(int polls, int* status, cudaStream_t st);
+
 // ---------------------------------------------------------- host helpers --
 // For the stream runtime (host code only).
 struct PlanGeometry {

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 
+#include "rf_async.cuh"
 #include "rf_engine.h"
 
 namespace rf {
@@ -490,4 +491,24 @@ bool image_kernel_shape(int npix, ImageKernelShape* out) {
   }
 }
 
+}  // namespace rf
+
+// ------------------------------------------------------ bounded-wait check --
+namespace rf {
+namespace {
+// The row pass's bounded mbarrier wait on a barrier that nothing arrives at:
+// it must give up and report it (status 1) instead of hanging.
+__global__ void k_wait_selftest(int polls, int* status) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0, polls);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) *status = 1;
+}
+}  // namespace
+
+cudaError_t launch_wait_selftest(int polls, int* status, cudaStream_t st) {
+  k_wait_selftest<<<1, 64, 0, st>>>(polls, status);
+  return cudaGetLastError();
+}
 }  // namespace rf
