@@ -611,6 +611,7 @@ rf_status alloc_wave_scratch(rf_plan* p, int slots) {
   slots = std::max(std::min(slots, 32768), B);
   const size_t per_slot = (size_t)p->ncol * p->npix;
   const int nrb = p->shape.partials_per_image;
+  p->tmap_T.nbox = 0;  // the map describes d_T, about to be freed
   if (p->d_T) {
     p->device_bytes -= (uint64_t)p->slots_max * per_slot * sizeof(float2);
     p->dfree(p->d_T);
