@@ -328,7 +328,7 @@ def run_reference(args, rank, world):
     seg = synth.make_segment(spec)
     run = OracleRunner(spec, seg)
     try:
-        n = run.cores * 2
+        n = run.cores * 8   # about 0.3 s of oracle work per step
         for _ in range(args.warmup):
             run.run(run.sample(n))
         t_total = 0.0
