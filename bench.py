@@ -270,7 +270,8 @@ def load_traffic(kernel, images_per_launch):
     return k["dram_bytes_per_image"] * images_per_launch
 
 
-KERNEL_SOURCES = ("rf_fft.cuh", "rf_image.cuh", "rf_image_small.cu", "rf_image_large.cu", "rf_kernels.cu")
+KERNEL_SOURCES = ("rf_async.cuh", "rf_fft.cuh", "rf_image.cuh", "rf_image_small.cu", "rf_image_large.cu",
+                  "rf_kernels.cu")
 
 
 def source_hash():
