@@ -221,15 +221,25 @@ class ImageStats:
     snr: float
 
 
-def image_stats(I: np.ndarray) -> ImageStats:
+CLIP_SIGMA = 5.0
+
+
+def image_stats(I: np.ndarray, clip: bool = False) -> ImageStats:
     """Population mean/std of all pixels, the maximum pixel and peak/sigma (Sec. 3.1).
 
-    Ties for the maximum go to the lowest linear index y N + x.
+    Ties for the maximum go to the lowest linear index y N + x.  With
+    ``clip`` the noise takes one clipping pass: with mu0, sigma0 over all
+    pixels, mean and sigma are recomputed over the pixels with
+    |I - mu0| <= 5 sigma0 (the peak is still the maximum of all pixels).
     """
     N = I.shape[1]
     flat = np.asarray(I, dtype=np.float64).ravel()
     mu = flat.mean()
     sigma = float(np.sqrt(np.mean((flat - mu) ** 2)))
+    if clip:
+        kept = flat[np.abs(flat - mu) <= CLIP_SIGMA * sigma]
+        mu = kept.mean()
+        sigma = float(np.sqrt(np.mean((kept - mu) ** 2)))
     k = int(np.argmax(flat))
     peak = float(flat[k])
     y, x = divmod(k, N)
@@ -255,6 +265,7 @@ class OraclePlan:
     edge: str = EDGE_FULL
     npol: int = 2
     mean_subtract: bool = False
+    noise_clipped: bool = False
 
     def __post_init__(self):
         self.bl_uvw = baseline_uvw(self.ant_uvw)
@@ -302,6 +313,10 @@ class OraclePlan:
         G = grid_full_plane(R, self.iu, self.iv, self.ongrid, self.npix)
         return dirty_image_fft(G, W), W
 
+    def stats(self, I: np.ndarray) -> ImageStats:
+        """Image statistics under the plan's noise rule."""
+        return image_stats(I, self.noise_clipped)
+
     def candidate(self, d: int, s: int, t: int, st: ImageStats) -> Dict:
         N = self.npix
         return dict(dm_idx=d, dt_idx=s, t_idx=t, x=st.x, y=st.y, snr=st.snr, peak=st.peak,
@@ -324,7 +339,7 @@ def search_segment(plan: OraclePlan, vis: np.ndarray, nint: Optional[int] = None
         I, W = plan.image(S, d, s, t, n)
         if I is None:
             continue
-        st = image_stats(I)
+        st = plan.stats(I)
         if with_stats:
             stats[(d, s, t)] = st
         if st.sigma > 0 and st.snr >= plan.threshold:
@@ -377,7 +392,7 @@ def search_stream(plan: OraclePlan, vis: np.ndarray, stride: int, with_stats: bo
             I, W = plan.image(S, d, s, t, n)
             if I is None:
                 continue
-            st = image_stats(I)
+            st = plan.stats(I)
             key = (d, s, start // dts[s] + t)
             if with_stats:
                 stats[key] = st
@@ -436,7 +451,7 @@ def candidate_features(plan: OraclePlan, S: np.ndarray, d: int, s: int, t: int, 
     Image moments are over all N^2 pixels; spectrum moments over the real
     part of the spectrum at the channels with data (w_c > 0)."""
     I, W = plan.image(S, d, s, t, nint)
-    st = image_stats(I)
+    st = plan.stats(I)
     spec, w = candidate_spectrum(plan, S, d, s, t, st.x, st.y, nint)
     im = moments(I)
     used = w > 0

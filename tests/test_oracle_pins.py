@@ -386,3 +386,37 @@ def test_mean_subtraction_removes_a_constant_source_and_keeps_a_pulse():
     X[5] = 1.0
     np.testing.assert_allclose(oracle.subtract_mean(X)[5], 1.0 - 1.0 / 16)
     np.testing.assert_allclose(oracle.subtract_mean(X)[4], -1.0 / 16)
+
+
+def test_clipped_noise_excludes_a_bright_source():
+    # one clipping pass at 5 sigma: a spike far above the noise is excluded,
+    # so sigma becomes the noise pixels' own population std
+    rng = np.random.default_rng(9)
+    I = rng.standard_normal((64, 64)) * 0.1
+    I = np.clip(I, -0.45, 0.45)             # every noise pixel within 4.5 of its own sigma
+    I[10, 20] = 50.0
+    noise = np.delete(I.ravel(), 10 * 64 + 20)
+    st = oracle.image_stats(I, clip=True)
+    assert abs(st.sigma - noise.std()) < 1e-12
+    assert abs(st.mean - noise.mean()) < 1e-12
+    assert (st.x, st.y, st.peak) == (20, 10, 50.0)
+    full = oracle.image_stats(I)
+    assert full.sigma > 5 * st.sigma and st.snr > 5 * full.snr
+    # nothing beyond 5 sigma: clipping changes nothing
+    J = np.clip(rng.standard_normal((32, 32)), -3, 3)
+    a, b = oracle.image_stats(J), oracle.image_stats(J, clip=True)
+    assert (a.sigma, a.mean, a.snr) == (b.sigma, b.mean, b.snr)
+
+
+def test_clipped_noise_raises_a_pulse_snr():
+    spec = synth.config("tiny")
+    seg = synth.make_segment(spec)
+    kw = dict(edge=spec.edge)
+    op = oracle.OraclePlan(seg["ant_uvw"], seg["freq_hz"], spec.inttime_s, spec.npix, spec.cell_rad, spec.dm_list,
+                           spec.dt_list, spec.threshold, **kw)
+    opc = oracle.OraclePlan(seg["ant_uvw"], seg["freq_hz"], spec.inttime_s, spec.npix, spec.cell_rad, spec.dm_list,
+                            spec.dt_list, spec.threshold, noise_clipped=True, **kw)
+    c0 = max(oracle.search_segment(op, seg["vis"]), key=lambda c: c["snr"])
+    c1 = max(oracle.search_segment(opc, seg["vis"]), key=lambda c: c["snr"])
+    assert (c0["x"], c0["y"], c0["t_idx"]) == (c1["x"], c1["y"], c1["t_idx"])
+    assert c1["snr"] >= c0["snr"] and c1["sigma"] <= c0["sigma"]
