@@ -69,6 +69,11 @@ def parse():
                     help="time the periodicity search, stream, mean subtraction and candidate products")
     ap.add_argument("--host-input", action="store_true",
                     help="time the search from pinned host input only (small device footprint for profilers)")
+    ap.add_argument("--write-traffic", metavar="RAW_CSV",
+                    help="write profiles/traffic.json from `ncu -i <rep> --page raw --csv` output of the imaging "
+                         "kernels (no GPU needed) and exit")
+    ap.add_argument("--traffic-images", type=int, default=256, help="images per captured launch (the wave size)")
+    ap.add_argument("--traffic-command", default="", help="the ncu command the capture came from")
     return ap.parse_args()
 
 
@@ -286,6 +291,41 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+TRAFFIC_KERNELS = (("k_grid_cells", "grid_cells"), ("k_colfft", "grid_colfft"), ("k_rowfft_stats", "rowfft_stats"))
+_BYTE_UNITS = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "tbyte": 1e12}
+
+
+def write_traffic(raw_csv, images_per_launch, command, workload):
+    """profiles/traffic.json from an ncu raw-page CSV (header row, unit row,
+    one row per captured launch): DRAM read + write bytes per launch of each
+    imaging kernel, averaged over its captured launches, and per image."""
+    import csv
+    with open(raw_csv, newline="") as f:
+        rows = [r for r in csv.reader(f) if r]
+    hdr = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    names, units, data = rows[hdr], rows[hdr + 1], rows[hdr + 2:]
+    col = {n: i for i, n in enumerate(names)}
+
+    def value(r, metric):
+        i = col[metric]
+        return float(r[i].replace(",", "")) * _BYTE_UNITS[units[i].strip().lower()]
+
+    out = {}
+    for pattern, key in TRAFFIC_KERNELS:
+        per = [value(r, "dram__bytes_read.sum") + value(r, "dram__bytes_write.sum")
+               for r in data if pattern in r[col["Kernel Name"]]]
+        if per:
+            b = sum(per) / len(per)
+            out[key] = {"dram_bytes_per_launch": b, "images_per_launch": images_per_launch,
+                        "dram_bytes_per_image": b / images_per_launch, "launches_captured": len(per)}
+    doc = {"source_hash": source_hash(), "workload": workload, "command": command, "kernels": out}
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    with open(path, "w") as f:
+        json.dump(doc, f, indent=1)
+        f.write("\n")
+    return doc
+
+
 def roofline(prof, spec, info, n_images, steps, fp16, hbm_peak, peak_kind):
     work = work_per_image(spec, info, fp16)
     per = {}
@@ -496,6 +536,14 @@ def run_next_rows(args):
     mms, _ = timed(lambda: plan_m.search(vis, nint), 3)
     line["mean_subtract"] = {"ms": mms, "overhead_ms": mms - ms}
     plan_m.close()
+    # clipped noise (one 5-sigma clipping pass) on the same search
+    spec_c = synth.config(args.config)
+    spec_c.noise_clipped = True
+    plan_c = rf.Plan.from_spec(spec_c, seg["ant_uvw"], seg["freq_hz"], max_nint=nint)
+    cms_, cc = timed(lambda: plan_c.search(vis, nint), 3)
+    line["noise_clipped"] = {"ms": cms_, "overhead_ms": cms_ - ms, "candidates": int(len(cc)),
+                             "candidates_plain_noise": int(len(cands))}
+    plan_c.close()
     # stream: segments of nint integrations overlapping by the longest sweep,
     # fed the same segment repeatedly in chunks of 128 integrations
     plan_s = rf.Plan.from_spec(spec, seg["ant_uvw"], seg["freq_hz"], max_nint=nint)
@@ -527,6 +575,11 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.write_traffic:
+        doc = write_traffic(args.write_traffic, args.traffic_images, args.traffic_command,
+                            f"{args.config}, {args.traffic_images}-image waves, pinned host input")
+        print(json.dumps(doc))
+        return 0
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.serving:

@@ -60,6 +60,14 @@ typedef enum rf_status {
  * which removes sources that are constant over the segment.  The mean is
  * summed in FP64 over the stored Stokes-I values. */
 #define RF_MEAN_SUBTRACT 0x4u
+/* Clipped noise (Sec. 3.1 asks only for an S/N above a threshold; this is
+ * the one-pass robust variant): with mu0 and sigma0 the mean and population
+ * standard deviation of all N^2 pixels, mean and sigma are recomputed over
+ * the pixels with |I - mu0| <= 5 sigma0.  The peak stays the maximum of all
+ * pixels and snr = peak / sigma.  The search reads each image once as
+ * without it (the kept-pixel sums are taken in the row FFT's registers,
+ * around mu0 and sigma0 obtained from the grid by Parseval's identity). */
+#define RF_NOISE_CLIPPED 0x8u
 /* Build the host tables only; no device memory is touched.  Such a plan
  * answers the table queries (rf_plan_info, rf_plan_delays, rf_plan_cells,
  * rf_count_images) and rejects searches with RF_ERR_INVALID_ARG. */
@@ -87,7 +95,8 @@ typedef enum rf_status {
  * dm_list    [ndm] dispersion measures in pc cm^-3, each >= 0.
  * dt_list    [ndt] boxcar widths in integrations, each in [1, 1024].
  * threshold_sigma  candidate threshold on peak / sigma (> 0).
- * flags      RF_STORE_FP16 | RF_EDGE_PARTIAL | RF_MEAN_SUBTRACT | RF_HOST_ONLY.
+ * flags      RF_STORE_FP16 | RF_EDGE_PARTIAL | RF_MEAN_SUBTRACT | RF_NOISE_CLIPPED |
+ *            RF_HOST_ONLY.
  * max_nint   largest segment length (integrations) this plan will search;
  *            sizes the device buffers.
  * device     CUDA device ordinal the plan lives on.
@@ -116,7 +125,8 @@ typedef struct rf_plan_desc {
  * whose peak / sigma reached the threshold (Sec. 3.1; at most one per image).
  * x, y     peak pixel; l_rad = (x - N/2) cell, m_rad = (y - N/2) cell.
  * peak     peak pixel value (units of the visibilities, a weighted mean).
- * sigma    population standard deviation of all N^2 pixels.
+ * sigma    population standard deviation of all N^2 pixels (of the kept
+ *          pixels with RF_NOISE_CLIPPED).
  * snr      peak / sigma.
  * t_idx    output integration t' (start integration t' * dt at f_top).
  */

@@ -5,6 +5,7 @@ the CPU-baseline leg of the benchmark, never by the engine itself.
 """
 
 from .realfast_oracle import (  # noqa: F401
+    CLIP_SIGMA,
     C_LIGHT,
     DISP_CONST,
     EDGE_FULL,

@@ -29,7 +29,7 @@ __all__ = [
     "Stream", "RfStreamInfo", "RfCandidateFeatures", "FEATURES_DTYPE", "rf_candidate_products",
     "RfPeriodicCandidate", "PERIODIC_DTYPE", "rf_periodicity_search", "rf_selftest_bounded_wait",
     "Plan", "CANDIDATE_DTYPE", "STAT_DTYPE", "declared_symbols",
-    "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_MEAN_SUBTRACT", "RF_STREAM_KEEP_STATS", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
+    "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_MEAN_SUBTRACT", "RF_NOISE_CLIPPED", "RF_STREAM_KEEP_STATS", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
 ]
 
 RF_OK = 0
@@ -48,6 +48,7 @@ STATUS_NAMES = {0: "RF_OK", 1: "RF_ERR_INVALID_ARG", 2: "RF_ERR_NO_MEMORY", 3: "
 RF_STORE_FP16 = 0x1
 RF_EDGE_PARTIAL = 0x2
 RF_MEAN_SUBTRACT = 0x4
+RF_NOISE_CLIPPED = 0x8
 RF_STREAM_KEEP_STATS = 0x1
 RF_HOST_ONLY = 0x100
 RF_FORM_BATCHED = 0
@@ -568,6 +569,8 @@ class Plan:
                 flags |= RF_STORE_FP16
             if getattr(spec, "mean_subtract", False):
                 flags |= RF_MEAN_SUBTRACT
+            if getattr(spec, "noise_clipped", False):
+                flags |= RF_NOISE_CLIPPED
         return cls(ant_uvw, freq_hz, spec.inttime_s, spec.npix, spec.cell_rad, spec.dm_list, spec.dt_list,
                    spec.threshold, npol=spec.npol, flags=flags, max_nint=max_nint or spec.nint, device=device)
 

@@ -50,7 +50,7 @@ rf_status fail(rf_status s, const char* fmt, ...) {
 constexpr double kDispConst = 4.1488e-3;  // s GHz^2 per pc cm^-3 (Sec. 2.1 footnote)
 constexpr double kCLight = 299792458.0;   // m/s
 constexpr double kTwoPi = 6.283185307179586476925286766559;
-constexpr uint32_t kKnownFlags = RF_STORE_FP16 | RF_EDGE_PARTIAL | RF_MEAN_SUBTRACT | RF_HOST_ONLY;
+constexpr uint32_t kKnownFlags = RF_STORE_FP16 | RF_EDGE_PARTIAL | RF_MEAN_SUBTRACT | RF_NOISE_CLIPPED | RF_HOST_ONLY;
 constexpr size_t kStageBytes = 256ull << 20;   // host->device chunk of raw visibilities
 constexpr size_t kTBudgetBytes = 4096ull << 20;  // column-FFT scratch per wave
 constexpr int kRangeEntries = 64;                // target entries per gridding warp
@@ -94,12 +94,12 @@ struct BusyGuard {
 
 enum KernelKind {
   K_H2D = 0, K_INGEST, K_RESAMPLE, K_WEIGHTS, K_GRID_CELLS, K_GRID_COLFFT, K_ROWFFT_STATS, K_FINALIZE,
-  K_PLAIN_TRIAL, K_MEAN_SUBTRACT, K_NKINDS
+  K_PLAIN_TRIAL, K_MEAN_SUBTRACT, K_CLIP_WINDOW, K_NKINDS
 };
 const char* const kKindNames[K_NKINDS] = {"h2d_copy",    "ingest",       "resample",
                                            "weights",     "grid_cells",   "grid_colfft",
                                            "rowfft_stats", "finalize",    "plain_trial_chunk",
-                                           "mean_subtract"};
+                                           "mean_subtract", "clip_window"};
 
 // Event-pair timing of every launch a plan issues while profiling is on.
 struct Profiler {
@@ -251,6 +251,7 @@ struct rf_plan {
   float2* d_cellbuf = nullptr;
   float* d_colsq = nullptr;     // [slots][ncol] Parseval sums
   float* d_mean0 = nullptr;     // [slots] Re H(0, 0)
+  float2* d_clip = nullptr;     // [slots] clipping window (RF_NOISE_CLIPPED only)
   rf::PlainBuffers plain{};     // allocated on the first plain-form search
 
   // CUDA graph of the batched wave loop for the current image list
@@ -633,6 +634,11 @@ rf_status alloc_wave_scratch(rf_plan* p, int slots) {
     p->dfree(p->d_mean0);
     p->d_colsq = p->d_mean0 = nullptr;
   }
+  if (p->d_clip) {
+    p->device_bytes -= (uint64_t)p->slots_max * sizeof(float2);
+    p->dfree(p->d_clip);
+    p->d_clip = nullptr;
+  }
   p->slots_max = slots;
   p->gslots_max = std::max(2 * ((slots + B - 1) / B), 1);
   p->cached_nint = -1;
@@ -643,6 +649,7 @@ rf_status alloc_wave_scratch(rf_plan* p, int slots) {
   if ((s = p->dalloc(&p->d_cellbuf, (size_t)p->gslots_max * std::max(p->n_cells, 1) * 32)) != RF_OK) return s;
   if ((s = p->dalloc(&p->d_colsq, (size_t)slots * p->ncol)) != RF_OK) return s;
   if ((s = p->dalloc(&p->d_mean0, (size_t)slots)) != RF_OK) return s;
+  if ((p->flags & RF_NOISE_CLIPPED) && (s = p->dalloc(&p->d_clip, (size_t)slots)) != RF_OK) return s;
   encode_tile_map(p);
   return RF_OK;
 }
@@ -677,6 +684,7 @@ uint64_t estimate_device_bytes(const rf_plan* p, int slots) {
   b += r((size_t)slots * per_slot, 1) + r((size_t)slots * p->shape.partials_per_image, sizeof(StatPartial)) +
        r((size_t)gslots * std::max(p->n_cells, 1) * 32, sizeof(float2)) + r((size_t)slots * p->ncol, 4) +
        r(slots, 4);
+  if (p->flags & RF_NOISE_CLIPPED) b += r(slots, sizeof(float2));
   const size_t per_int = rows * p->npol * sizeof(float2);
   const size_t stage_nint = std::max<size_t>(1, std::min<size_t>(kStageBytes / per_int, (size_t)p->max_nint));
   b += r(stage_nint * per_int, 1);
@@ -859,14 +867,18 @@ rf_status run_waves(rf_plan* p, int nint, const std::vector<Wave>& waves, int ni
     RF_TIMED(p->prof, K_GRID_COLFFT, st,
              rf::launch_colfft(g, p->tb, p->d_groups, w.g_begin, ng, w.img_begin, p->d_cellbuf, p->d_T,
                                p->d_colsq, p->d_mean0, st));
+    const bool clip = (p->flags & RF_NOISE_CLIPPED) != 0;
+    if (clip)
+      RF_TIMED(p->prof, K_CLIP_WINDOW, st, rf::launch_clip_window(g, p->d_colsq, p->d_mean0, ni, p->d_clip, st));
     float* im = d_images ? d_images + (size_t)w.img_begin * p->npix * p->npix : nullptr;
     RF_TIMED(p->prof, K_ROWFFT_STATS, st,
              rf::launch_rowfft_stats(g, p->tb, p->d_T, ni, w.img_begin, p->d_weight, p->d_partials, im,
-                                     p->tmap_T.nbox > 0 ? &p->tmap_T : nullptr, p->d_err, st));
+                                     p->tmap_T.nbox > 0 ? &p->tmap_T : nullptr, p->d_err, st,
+                                     clip ? p->d_clip : nullptr));
     RF_TIMED(p->prof, K_FINALIZE, st,
              rf::launch_finalize(g, p->d_partials, p->d_colsq, p->d_mean0, p->d_img_info, p->d_weight, ni,
-                                 w.img_begin, p->threshold,
-                                 p->d_cands, p->d_ncand, p->img_cap, d_stats, st));
+                                 w.img_begin, p->threshold, p->d_cands, p->d_ncand, p->img_cap, d_stats, st,
+                                 clip));
   }
   return RF_OK;
 }
@@ -960,7 +972,8 @@ rf_status run_plain(rf_plan* p, int nint, DevStat* d_stats, cudaStream_t st) {
         const int nk = std::min(p->plain.cap, nt - t0);
         RF_TIMED(p->prof, K_PLAIN_TRIAL, st,
                  rf::launch_plain_chunk(g, p->tb, p->plain, d, sdt, t0, nk, img0, p->d_img_info, p->d_weight,
-                                        p->threshold, p->d_cands, p->d_ncand, p->img_cap, d_stats, st));
+                                        p->threshold, p->d_cands, p->d_ncand, p->img_cap, d_stats, st,
+                                        (p->flags & RF_NOISE_CLIPPED) != 0));
         img0 += nk;
       }
     }

@@ -86,14 +86,21 @@ struct CandRef {
 // Cell of an off-grid (baseline, channel) in the per-row cell table.
 constexpr int kOffGrid = -2147483647 - 1;
 
-// Row-block partial statistics of one image (raw pixel units).
+// Row-block partial statistics of one image (raw pixel units).  With the
+// clipped noise, sum and sumsq hold the sums of d = J - mean0 and d^2 over
+// the `kept` pixels J of the block with |d| <= clip sigmas (else zero).
 struct StatPartial {
   double sum;
   double sumsq;
   float max;
   int32_t idx;  // y * N + x of max (lowest on ties)
-  int32_t pad[2];
+  int32_t kept;
+  int32_t pad;
 };
+
+// Clipping radius of the optional one-pass clipped noise, in units of the
+// noise over all pixels.
+constexpr double kClipSigmas = 5.0;
 
 // Candidate record written on the device.
 struct DevCand {
@@ -158,18 +165,28 @@ cudaError_t launch_colfft(const SegmentGeom& g, const DevTables& tb, const Group
                           int ngroups, int img_base, const float2* cellbuf, float2* Tbuf, float* colsq,
                           float* mean0, cudaStream_t st);
 
+// Clipping window of each of `nimg` slots for the clipped noise, in raw
+// pixel units (the image times 2W): clip[i] = {mean0[i], kClipSigmas *
+// sigma over all pixels}, the sigma from the Parseval sums colsq.
+cudaError_t launch_clip_window(const SegmentGeom& g, const float* colsq, const float* mean0, int nimg,
+                               float2* clip, cudaStream_t st);
+
 // Row C2R (pass B) + statistics of `nimg` images in slots [0, nimg) whose
 // first image index is img_base.  Optionally writes the scaled images.
+// With `clip` (per slot, from launch_clip_window) the partials also carry
+// the kept-pixel sums of the clipped noise.
 cudaError_t launch_rowfft_stats(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, int nimg,
                                 int img_base, const double* weight, StatPartial* partials, float* images,
-                                const TileMap* tm, int* err, cudaStream_t st);
+                                const TileMap* tm, int* err, cudaStream_t st, const float2* clip = nullptr);
 
 // Reduce row-block partials, compute sigma / snr, append candidates and
 // (optionally) per-image stats for images [img_base, img_base + nimg).
+// With `clip` the mean and sigma are those of the kept pixels, from the
+// partials' sums around mean0.
 cudaError_t launch_finalize(const SegmentGeom& g, const StatPartial* partials, const float* colsq,
                             const float* mean0, const int4* img_info, const double* weight, int nimg, int img_base,
                             double threshold, DevCand* cands, int* ncand, int cand_cap, DevStat* stats,
-                            cudaStream_t st);
+                            cudaStream_t st, bool clip = false);
 
 // Buffers of the plain per-trial form (chunks of up to `cap` images).
 struct PlainBuffers {
@@ -186,11 +203,12 @@ struct PlainBuffers {
 
 // One unfused launch set for images [img0, img0 + nk) = t' t0 .. t0+nk-1 of
 // trial (d, s): dedisperse, grid (atomics), column FFTs, row FFTs writing the
-// images, image statistics read back from HBM.
+// images, image statistics read back from HBM (a second read for the
+// clipped noise with `clip`).
 cudaError_t launch_plain_chunk(const SegmentGeom& g, const DevTables& tb, const PlainBuffers& pb, int d, int s,
                                int t0, int nk, int img0, const int4* img_info, const double* weight,
                                double threshold, DevCand* cands, int* ncand, int cand_cap, DevStat* stats,
-                               cudaStream_t st);
+                               cudaStream_t st, bool clip = false);
 
 // Compile-time layout facts per image size, for host-side sizing.
 struct ImageKernelShape {

@@ -206,12 +206,16 @@ __device__ __forceinline__ void max_merge(float& m, int& i, float m2, int i2) {
 // tma_boxes tensor copies of tma_rows u rows from `tmap` ([slot][u][2N
 // floats]) and every thread waits on an mbarrier; a wait that gives up sets
 // *err and the block returns.  Otherwise the threads copy it with cp.async.
-template <int N>
+// CLIP (the one-pass clipped noise): clip[slot] = {mean0, r} in raw pixel
+// units, and each row pair also sums d = J - mean0 and d^2 over its pixels J
+// with |d| <= r and counts them (FP32 per thread and across the transform's
+// threads in a fixed order).
+template <int N, bool CLIP>
 __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     k_rowfft_stats(SegmentGeom g, DevTables tb, const float2* __restrict__ Tbuf, int nimg, int img_base,
                    const double* __restrict__ weight, StatPartial* __restrict__ partials,
                    float* __restrict__ images, const __grid_constant__ CUtensorMap tmap, int tma_boxes,
-                   int tma_rows, int* __restrict__ err) {
+                   int tma_rows, int* __restrict__ err, const float2* __restrict__ clip) {
   using K = ImgCfg<N>;
   constexpr int NWB = (K::THREADS_B + 31) / 32;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -221,6 +225,8 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
   float4* tile = reinterpret_cast<float4*>(tb0);    // [rows][CH]
   __shared__ float w_max[32];
   __shared__ int w_idx[32];
+  __shared__ float w_s1[CLIP ? 32 : 1], w_s2[CLIP ? 32 : 1];
+  __shared__ int w_cn[CLIP ? 32 : 1];
   __shared__ __align__(8) unsigned long long tbar;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -380,6 +386,39 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     }
 #pragma unroll
     for (int off = WL / 2; off > 0; off >>= 1) best = min(best, __shfl_xor_sync(MASK, best, off));
+    // clipped noise: sums of the kept pixels' deviations from mean0, rows y
+    // and y + 1 in separate chains
+    float s1 = 0.f, s2 = 0.f;
+    int cn = 0;
+    if constexpr (CLIP) {
+      const float2 cw = clip[slot];
+      float ax = 0.f, qx = 0.f, ay = 0.f, qy = 0.f;
+      int nx = 0, ny = 0;
+#pragma unroll
+      for (int e = 0; e < K::E; ++e) {
+        const float dx = v[e].x - cw.x;
+        const float dy = v[e].y - cw.x;
+        if (fabsf(dx) <= cw.y) {
+          ax += dx;
+          qx = fmaf(dx, dx, qx);
+          ++nx;
+        }
+        if (fabsf(dy) <= cw.y) {
+          ay += dy;
+          qy = fmaf(dy, dy, qy);
+          ++ny;
+        }
+      }
+      s1 = ax + ay;
+      s2 = qx + qy;
+      cn = nx + ny;
+#pragma unroll
+      for (int off = WL / 2; off > 0; off >>= 1) {
+        s1 += __shfl_xor_sync(MASK, s1, off);
+        s2 += __shfl_xor_sync(MASK, s2, off);
+        cn += __shfl_xor_sync(MASK, cn, off);
+      }
+    }
     if (K::T > 32) {
       // wide transforms: combine the warps of one transform in shared memory
       constexpr int WPT = K::T / 32;
@@ -387,6 +426,11 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
       if (lane == 0) {
         w_max[wid] = wmax;
         w_idx[wid] = best;
+        if constexpr (CLIP) {
+          w_s1[wid] = s1;
+          w_s2[wid] = s2;
+          w_cn[wid] = cn;
+        }
       }
       fft_sync<K::T>(xf);
       if (t == 0) {
@@ -397,19 +441,33 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
         StatPartial sp;
         sp.sum = 0.0;
         sp.sumsq = 0.0;
+        sp.kept = 0;
+        if constexpr (CLIP) {
+          float a = 0.f, q = 0.f;
+          int n = 0;
+          for (int w = 0; w < WPT; ++w) {
+            a += w_s1[w0 + w];
+            q += w_s2[w0 + w];
+            n += w_cn[w0 + w];
+          }
+          sp.sum = a;
+          sp.sumsq = q;
+          sp.kept = n;
+        }
         sp.max = mx;
         sp.idx = mi;
-        sp.pad[0] = sp.pad[1] = 0;
+        sp.pad = 0;
         partials[(size_t)slot * (N / 2) + (y0 >> 1) + xf] = sp;
       }
       fft_sync<K::T>(xf);
     } else if (t == 0) {
       StatPartial sp;
-      sp.sum = 0.0;
-      sp.sumsq = 0.0;
+      sp.sum = s1;
+      sp.sumsq = s2;
+      sp.kept = cn;
       sp.max = wmax;
       sp.idx = best;
-      sp.pad[0] = sp.pad[1] = 0;
+      sp.pad = 0;
       partials[(size_t)slot * (N / 2) + (y0 >> 1) + xf] = sp;
     }
   }
@@ -549,7 +607,8 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
       sp.sumsq = 0.0;
       sp.max = mx;
       sp.idx = mi;
-      sp.pad[0] = sp.pad[1] = 0;
+      sp.kept = 0;
+      sp.pad = 0;
       partials[(size_t)pj * N + y] = sp;
     }
   }
@@ -604,31 +663,40 @@ int rowfft_tile_rows(int ncol) {
   return nbox * rows;
 }
 
-template <int N>
-cudaError_t run_rowfft_stats(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, int nimg,
-                             int img_base, const double* weight, StatPartial* partials, float* images,
-                             const TileMap* tm, int* err, cudaStream_t st) {
+template <int N, bool CLIP>
+cudaError_t run_rowfft_stats_k(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, int nimg,
+                               int img_base, const double* weight, StatPartial* partials, float* images,
+                               const TileMap* tm, int* err, cudaStream_t st, const float2* clip) {
   using K = ImgCfg<N>;
   const int smem = K::SMEM_B_FIXED + (K::TILE_TMA ? 1024 : 0) + rowfft_tile_rows<N>(g.ncol) * K::CH * 16;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_rowfft_stats<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  auto kern = k_rowfft_stats<N, CLIP>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_rowfft_stats<N>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cudaSharedmemCarveoutMaxShared);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   if (nimg <= 0) return cudaSuccess;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rowfft_stats<N>, K::THREADS_B, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, K::THREADS_B, smem);
   if (e != cudaSuccess) return e;
   const long nitems = (long)nimg * (N / K::RB);
   const long grid = std::min<long>(nitems, (long)std::max(per_sm, 1) * sm_count());
   const bool tma = K::TILE_TMA && tm != nullptr && tm->nbox > 0 && err != nullptr;
   CUtensorMap none;
   memset(&none, 0, sizeof(none));
-  k_rowfft_stats<N><<<(int)grid, K::THREADS_B, smem, st>>>(g, tb, Tbuf, nimg, img_base, weight, partials, images,
-                                                           tma ? tm->map : none, tma ? tm->nbox : 0,
-                                                           tma ? tm->rows : 0, err);
+  kern<<<(int)grid, K::THREADS_B, smem, st>>>(g, tb, Tbuf, nimg, img_base, weight, partials, images,
+                                              tma ? tm->map : none, tma ? tm->nbox : 0, tma ? tm->rows : 0, err,
+                                              clip);
   return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t run_rowfft_stats(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, int nimg,
+                             int img_base, const double* weight, StatPartial* partials, float* images,
+                             const TileMap* tm, int* err, cudaStream_t st, const float2* clip) {
+  if (clip != nullptr)
+    return run_rowfft_stats_k<N, true>(g, tb, Tbuf, nimg, img_base, weight, partials, images, tm, err, st, clip);
+  return run_rowfft_stats_k<N, false>(g, tb, Tbuf, nimg, img_base, weight, partials, images, tm, err, st, nullptr);
 }
 
 template <int N>
@@ -650,7 +718,7 @@ void fill_shape(ImageKernelShape* o) {
                                      const float2*, float2*, float*, float*, cudaStream_t);                 \
   template cudaError_t run_rowfft_stats<N>(const SegmentGeom&, const DevTables&, const float2*, int, int,    \
                                            const double*, StatPartial*, float*, const TileMap*, int*,       \
-                                           cudaStream_t);                                                   \
+                                           cudaStream_t, const float2*);                                    \
   template void fill_shape<N>(ImageKernelShape*);                                                           \
   template cudaError_t run_rowfft_power<N>(const SegmentGeom&, const DevTables&, const float2*, const int4*, \
                                            int, StatPartial*, cudaStream_t);

@@ -329,34 +329,76 @@ __device__ __forceinline__ void fmax_merge(float& m, int& i, float m2, int i2) {
   }
 }
 
+// Sum over the ncol Parseval column sums of one image, lanes strided and an
+// xor tree (fixed order); every lane holds the result.
+__device__ __forceinline__ double parseval_sum(const float* __restrict__ cs, int ncol, int lane) {
+  double sq = 0.0;
+  for (int c = lane; c < ncol; c += 32) sq += (double)cs[c];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
+  return sq;
+}
+
+// One warp per image slot: the clipping window {mean, kClipSigmas sigma} of
+// the raw image J = 2W I.  mean(J) = Re G(0, 0) and mean(J^2) = the sum of
+// |G|^2 over the full plane (Parseval), so var(J) = sum - mean^2.
+__global__ void k_clip_window(int ncol, const float* __restrict__ colsq, const float* __restrict__ mean0, int nimg,
+                              float2* __restrict__ clip) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= nimg) return;
+  const double sq = parseval_sum(colsq + (size_t)i * ncol, ncol, lane);
+  if (lane != 0) return;
+  const float m = mean0[i];
+  double var = sq - (double)m * (double)m;
+  var = var > 0.0 ? var : 0.0;
+  clip[i] = make_float2(m, (float)(kClipSigmas * sqrt(var)));
+}
+
+cudaError_t launch_clip_window(const SegmentGeom& g, const float* colsq, const float* mean0, int nimg, float2* clip,
+                               cudaStream_t st) {
+  if (nimg <= 0) return cudaSuccess;
+  k_clip_window<<<(nimg + 7) / 8, 256, 0, st>>>(g.ncol, colsq, mean0, nimg, clip);
+  return cudaGetLastError();
+}
+
 __global__ void k_finalize(int npix, int nrb, int ncol, const StatPartial* __restrict__ partials,
                            const float* __restrict__ colsq, const float* __restrict__ mean0,
                            const int4* __restrict__ img_info, const double* __restrict__ weight, int nimg,
                            int img_base, double threshold, DevCand* __restrict__ cands, int* __restrict__ ncand,
-                           int cand_cap, DevStat* __restrict__ stats) {
-  // one warp per image; lanes stride over the row-pair partials (peak) and
-  // the per-column Parseval sums (FP64), then an xor-tree (fixed order)
-  // combines them
+                           int cand_cap, DevStat* __restrict__ stats, int clip) {
+  // one warp per image; lanes stride over the row-pair partials (peak, and
+  // the kept-pixel sums of the clipped noise) and the per-column Parseval
+  // sums (FP64), then an xor-tree (fixed order) combines them
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= nimg) return;
   const int img = img_base + i;
   const StatPartial* pp = partials + (size_t)i * nrb;
-  const float* cs = colsq + (size_t)i * ncol;
-  double sq = 0.0;
   float mx = -FLT_MAX;
   int mi = INT_MAX;
+  double ks1 = 0.0, ks2 = 0.0;
+  long long kn = 0;
   for (int r = lane; r < nrb; r += 32) {
     const StatPartial p = pp[r];
     fmax_merge(mx, mi, p.max, p.idx);
+    if (clip) {
+      ks1 += p.sum;
+      ks2 += p.sumsq;
+      kn += p.kept;
+    }
   }
-  for (int c = lane; c < ncol; c += 32) sq += (double)cs[c];
+  const double sq = parseval_sum(colsq + (size_t)i * ncol, ncol, lane);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    sq += __shfl_xor_sync(0xffffffffu, sq, off);
     const float om = __shfl_xor_sync(0xffffffffu, mx, off);
     const int oi = __shfl_xor_sync(0xffffffffu, mi, off);
     fmax_merge(mx, mi, om, oi);
+    if (clip) {
+      ks1 += __shfl_xor_sync(0xffffffffu, ks1, off);
+      ks2 += __shfl_xor_sync(0xffffffffu, ks2, off);
+      kn += __shfl_xor_sync(0xffffffffu, kn, off);
+    }
   }
   if (lane != 0) return;
   const double W = weight[img];
@@ -376,8 +418,15 @@ __global__ void k_finalize(int npix, int nrb, int ncol, const StatPartial* __res
   }
   // mean = G(0,0) / 2W; mean of I^2 = sum_full |G|^2 / 4W^2 (Parseval)
   const double inv = 0.5 / W;
-  const double mean = (double)mean0[i] * inv;
+  double mean = (double)mean0[i] * inv;
   double var = sq * inv * inv - mean * mean;
+  if (clip) {
+    // clipped noise: the kept pixels' deviations d from mean0 (raw units)
+    const double n = kn > 0 ? (double)kn : 1.0;
+    const double m1 = ks1 / n;
+    mean = ((double)mean0[i] + m1) * inv;
+    var = (ks2 / n - m1 * m1) * inv * inv;
+  }
   var = var > 0.0 ? var : 0.0;
   const double sigma = sqrt(var);
   const double peak = (double)mx * inv;
@@ -411,14 +460,13 @@ __global__ void k_finalize(int npix, int nrb, int ncol, const StatPartial* __res
 cudaError_t launch_finalize(const SegmentGeom& g, const StatPartial* partials, const float* colsq,
                             const float* mean0, const int4* img_info, const double* weight, int nimg, int img_base,
                             double threshold, DevCand* cands, int* ncand, int cand_cap, DevStat* stats,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool clip) {
   if (nimg <= 0) return cudaSuccess;
   ImageKernelShape sh;
   if (!image_kernel_shape(g.npix, &sh)) return cudaErrorInvalidValue;
   const int nrb = sh.partials_per_image;
   k_finalize<<<(nimg + 7) / 8, 256, 0, st>>>(g.npix, nrb, g.ncol, partials, colsq, mean0, img_info, weight, nimg,
-                                              img_base,
-                                                  threshold, cands, ncand, cand_cap, stats);
+                                              img_base, threshold, cands, ncand, cand_cap, stats, clip ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -428,7 +476,7 @@ cudaError_t run_colfft(const SegmentGeom&, const DevTables&, const Group*, int, 
                        float*, float*, cudaStream_t);
 template <int N>
 cudaError_t run_rowfft_stats(const SegmentGeom&, const DevTables&, const float2*, int, int, const double*,
-                             StatPartial*, float*, const TileMap*, int*, cudaStream_t);
+                             StatPartial*, float*, const TileMap*, int*, cudaStream_t, const float2*);
 template <int N>
 void fill_shape(ImageKernelShape*);
 template <int N>
@@ -453,11 +501,11 @@ cudaError_t launch_colfft(const SegmentGeom& g, const DevTables& tb, const Group
 
 cudaError_t launch_rowfft_stats(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, int nimg,
                                 int img_base, const double* weight, StatPartial* partials, float* images,
-                                const TileMap* tm, int* err, cudaStream_t st) {
+                                const TileMap* tm, int* err, cudaStream_t st, const float2* clip) {
   switch (g.npix) {
 #define RF_CASE(N) \
   case N:          \
-    return run_rowfft_stats<N>(g, tb, Tbuf, nimg, img_base, weight, partials, images, tm, err, st);
+    return run_rowfft_stats<N>(g, tb, Tbuf, nimg, img_base, weight, partials, images, tm, err, st, clip);
     RF_FOR_EACH_N(RF_CASE)
 #undef RF_CASE
     default:

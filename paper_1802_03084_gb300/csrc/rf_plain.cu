@@ -105,20 +105,45 @@ __global__ void __launch_bounds__(ImgCfg<N>::T * ImgCfg<N>::XA)
 // 5. statistics of each stored image: mean, population sigma, max with the
 // lowest index; candidate iff peak / sigma >= threshold.  One block per
 // image; FP32 sums over 32 pixels per step, FP64 per thread and block.
+// With `clip` (the one-pass clipped noise) a second read of the image sums
+// the deviations d = I - mean of the pixels with |d| <= kClipSigmas sigma,
+// and mean and sigma become those of the kept pixels.
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* sh) {
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, off);
+    b += __shfl_xor_sync(0xffffffffu, b, off);
+    c += __shfl_xor_sync(0xffffffffu, c, off);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    sh[3 * w] = a;
+    sh[3 * w + 1] = b;
+    sh[3 * w + 2] = c;
+  }
+  __syncthreads();
+  a = b = c = 0.0;
+  for (int i = 0; i < 8; ++i) {
+    a += sh[3 * i];
+    b += sh[3 * i + 1];
+    c += sh[3 * i + 2];
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(256) k_plain_stats(int npix, const float* __restrict__ images,
                                                      const int4* __restrict__ img_info,
                                                      const double* __restrict__ weight, int img_base,
                                                      double threshold, DevCand* __restrict__ cands,
                                                      int* __restrict__ ncand, int cand_cap,
-                                                     DevStat* __restrict__ stats) {
-  __shared__ double s_sum[8], s_sq[8];
+                                                     DevStat* __restrict__ stats, int clip) {
+  __shared__ double s_red[24];
   __shared__ float s_max[8];
   __shared__ int s_idx[8];
   const int k = blockIdx.x;
   const int img = img_base + k;
   const size_t n2 = (size_t)npix * npix;
   const float* im = images + (size_t)k * n2;
-  double sum = 0.0, sq = 0.0;
+  double sum = 0.0, sq = 0.0, unused = 0.0;
   float mx = -FLT_MAX;
   int mi = INT_MAX;
   for (size_t base = 0; base < n2; base += 256 * 32) {
@@ -139,8 +164,6 @@ __global__ void __launch_bounds__(256) k_plain_stats(int npix, const float* __re
     sq += pq;
   }
   for (int off = 16; off > 0; off >>= 1) {
-    sum += __shfl_xor_sync(0xffffffffu, sum, off);
-    sq += __shfl_xor_sync(0xffffffffu, sq, off);
     const float om = __shfl_xor_sync(0xffffffffu, mx, off);
     const int oi = __shfl_xor_sync(0xffffffffu, mi, off);
     if (om > mx || (om == mx && oi < mi)) {
@@ -150,28 +173,54 @@ __global__ void __launch_bounds__(256) k_plain_stats(int npix, const float* __re
   }
   const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
-    s_sum[w] = sum;
-    s_sq[w] = sq;
     s_max[w] = mx;
     s_idx[w] = mi;
   }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  for (int i = 1; i < 8; ++i) {
-    s_sum[0] += s_sum[i];
-    s_sq[0] += s_sq[i];
-    if (s_max[i] > s_max[0] || (s_max[i] == s_max[0] && s_idx[i] < s_idx[0])) {
-      s_max[0] = s_max[i];
-      s_idx[0] = s_idx[i];
+  block_sum3(sum, sq, unused, s_red);
+  mx = s_max[0];
+  mi = s_idx[0];
+  for (int i = 1; i < 8; ++i)
+    if (s_max[i] > mx || (s_max[i] == mx && s_idx[i] < mi)) {
+      mx = s_max[i];
+      mi = s_idx[i];
     }
+  double mean = sum / (double)n2;
+  double var = sq / (double)n2 - mean * mean;
+  var = var > 0.0 ? var : 0.0;
+  if (clip) {
+    const float mu = (float)mean;
+    const float r = (float)(kClipSigmas * sqrt(var));
+    double ks1 = 0.0, ks2 = 0.0, kn = 0.0;
+    for (size_t base = 0; base < n2; base += 256 * 32) {
+      float ps = 0.f, pq = 0.f;
+      int pn = 0;
+      for (int j = 0; j < 32; ++j) {
+        const size_t i = base + (size_t)j * 256 + threadIdx.x;
+        if (i < n2) {
+          const float dv = im[i] - mu;
+          if (fabsf(dv) <= r) {
+            ps += dv;
+            pq = fmaf(dv, dv, pq);
+            ++pn;
+          }
+        }
+      }
+      ks1 += ps;
+      ks2 += pq;
+      kn += pn;
+    }
+    block_sum3(ks1, ks2, kn, s_red);
+    const double nk = kn > 0.0 ? kn : 1.0;
+    const double m1 = ks1 / nk;
+    mean = (double)mu + m1;
+    var = ks2 / nk - m1 * m1;
+    var = var > 0.0 ? var : 0.0;
   }
+  if (threadIdx.x != 0) return;
   const double W = weight[img];
   const int4 info = img_info[img];
-  const double mean = s_sum[0] / (double)n2;
-  double var = s_sq[0] / (double)n2 - mean * mean;
-  var = var > 0.0 ? var : 0.0;
   const double sigma = sqrt(var);
-  const double peak = s_max[0];
+  const double peak = mx;
   const double snr = sigma > 0.0 ? peak / sigma : 0.0;
   DevStat ds;
   ds.pad = 0;
@@ -180,8 +229,8 @@ __global__ void __launch_bounds__(256) k_plain_stats(int npix, const float* __re
   ds.peak = (float)peak;
   ds.sigma = (float)sigma;
   ds.snr = (float)snr;
-  ds.y = s_idx[0] / npix;
-  ds.x = s_idx[0] - ds.y * npix;
+  ds.y = mi / npix;
+  ds.x = mi - ds.y * npix;
   if (!(W > 0.0)) {
     ds.peak = ds.sigma = ds.snr = 0.f;
     ds.x = ds.y = 0;
@@ -220,7 +269,7 @@ cudaError_t run_plain_colfft(const float2* grid, float2* T, const float2* tw, in
 cudaError_t launch_plain_chunk(const SegmentGeom& g, const DevTables& tb, const PlainBuffers& pb, int d, int s,
                                int t0, int nk, int img0, const int4* img_info, const double* weight,
                                double threshold, DevCand* cands, int* ncand, int cand_cap, DevStat* stats,
-                               cudaStream_t st) {
+                               cudaStream_t st, bool clip) {
   const size_t rows = (size_t)g.nbl * g.nchan;
   const int blocks = (int)std::min<size_t>((rows * nk + 255) / 256, 152 * 32);
   k_plain_dedisperse<<<blocks, 256, 0, st>>>(g, tb, pb.S, d, s, t0, nk, pb.R);
@@ -249,7 +298,7 @@ cudaError_t launch_plain_chunk(const SegmentGeom& g, const DevTables& tb, const 
   e = launch_rowfft_stats(gr, tb, pb.T, nk, img0, weight, pb.partials, pb.images, nullptr, nullptr, st);
   if (e != cudaSuccess) return e;
   k_plain_stats<<<nk, 256, 0, st>>>(g.npix, pb.images, img_info, weight, img0, threshold, cands, ncand, cand_cap,
-                                    stats);
+                                    stats, clip ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -23,15 +23,19 @@ def plans_for(spec, seg, flags=None, max_nint=None, dt_list=None):
     dts = spec.dt_list if dt_list is None else dt_list
     edge = spec.edge
     mean = bool(getattr(spec, "mean_subtract", False))
+    clip = bool(getattr(spec, "noise_clipped", False))
     if flags is not None:
         edge = "partial" if flags & rf.RF_EDGE_PARTIAL else "full"
         mean = bool(flags & rf.RF_MEAN_SUBTRACT)
+        clip = bool(flags & rf.RF_NOISE_CLIPPED)
     op = oracle.OraclePlan(seg["ant_uvw"], seg["freq_hz"], spec.inttime_s, spec.npix, spec.cell_rad,
-                           spec.dm_list, dts, spec.threshold, edge=edge, npol=spec.npol, mean_subtract=mean)
+                           spec.dm_list, dts, spec.threshold, edge=edge, npol=spec.npol, mean_subtract=mean,
+                           noise_clipped=clip)
     if flags is None:
         flags = (rf.RF_EDGE_PARTIAL if spec.edge == "partial" else 0) | \
                 (rf.RF_STORE_FP16 if spec.store == "fp16" else 0) | \
-                (rf.RF_MEAN_SUBTRACT if mean else 0)
+                (rf.RF_MEAN_SUBTRACT if mean else 0) | \
+                (rf.RF_NOISE_CLIPPED if clip else 0)
     gp = rf.Plan(seg["ant_uvw"], seg["freq_hz"], spec.inttime_s, spec.npix, spec.cell_rad, spec.dm_list, dts,
                  spec.threshold, npol=spec.npol, flags=flags, max_nint=max_nint or seg["vis"].shape[0])
     return gp, op

@@ -169,3 +169,17 @@ def test_stream_rejects_bad_arguments(L):
     m = ctypes.c_size_t()
     assert L.rf_stream_pop(None, None, 0, ctypes.byref(m)) == rf.RF_ERR_INVALID_ARG
     assert L.rf_stream_get_info(None, None) == rf.RF_ERR_INVALID_ARG
+
+
+def test_clipped_noise_flag_accepted_and_sized(L):
+    spec = synth.config("realtime")
+    kw = _desc_kwargs(spec)
+    kw["flags"] = rf.RF_HOST_ONLY | rf.RF_NOISE_CLIPPED
+    with rf.Plan(**kw) as p:
+        assert p.count_images(spec.nint) == 177521
+    kw["flags"] = 0
+    b0 = rf.rf_plan_estimate_bytes(rf.make_desc(**kw), wave_images=1024)
+    kw["flags"] = rf.RF_NOISE_CLIPPED
+    b1 = rf.rf_plan_estimate_bytes(rf.make_desc(**kw), wave_images=1024)
+    # one clipping window (two floats) per image slot of a wave
+    assert b1 - b0 == 1024 * 8
