@@ -27,8 +27,28 @@
 
 namespace rf {
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex add and subtract as one packed FP32-pair instruction each
+// (add/sub.rn.f32x2: both components rounded to nearest, as two scalar ops).
+__device__ __forceinline__ unsigned long long f2_pack(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+  return f2_unpack(d);
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+  return f2_unpack(d);
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -50,16 +70,17 @@ __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c
 __host__ __device__ __forceinline__ constexpr int padx(int i) { return i + (i >> 5); }
 
 // In-register inverse radix-4 on v[0], v[S], v[2S], v[3S] (natural order out).
+// The odd outputs t1 +- i u mix the components of u, so they stay scalar.
 template <int S>
 __device__ __forceinline__ void dft4(float2* v) {
-  float2 t0 = cadd(v[0], v[2 * S]);
-  float2 t1 = csub(v[0], v[2 * S]);
-  float2 t2 = cadd(v[S], v[3 * S]);
-  float2 t3 = cmul_i(csub(v[S], v[3 * S]));
+  const float2 t0 = cadd(v[0], v[2 * S]);
+  const float2 t1 = csub(v[0], v[2 * S]);
+  const float2 t2 = cadd(v[S], v[3 * S]);
+  const float2 u = csub(v[S], v[3 * S]);
   v[0] = cadd(t0, t2);
-  v[S] = cadd(t1, t3);
+  v[S] = make_float2(t1.x - u.y, t1.y + u.x);
   v[2 * S] = csub(t0, t2);
-  v[3 * S] = csub(t1, t3);
+  v[3 * S] = make_float2(t1.x + u.y, t1.y - u.x);
 }
 
 // Radix-P inverse DFT of v[0..P) in registers; X[q] ends in v[dft_perm<P>(q)].
