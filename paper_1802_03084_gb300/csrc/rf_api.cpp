@@ -662,7 +662,7 @@ uint64_t estimate_device_bytes(const rf_plan* p, int slots) {
   auto r = [](size_t n, size_t sz) { return (uint64_t)std::max<size_t>(n, 1) * sz; };
   uint64_t b = 0;
   b += r(p->delays.size(), 4) + r(p->dt.size(), 4) + r(p->ranges.size(), 8) + r(p->col_cell_ptr.size(), 4) +
-       r(p->cell_row.size(), 4) + r(p->ent.size(), sizeof(GridEntry)) + r(p->ongrid_chan.size(), 4) + r(N, 8);
+       r(p->cell_row.size(), 4) + r(p->ent.size(), sizeof(GridEntry)) + r(p->ongrid_chan.size(), 4) + r(rf::fft_twiddle_len((int)N), 8);
   const size_t nint_pad = (p->max_nint + 31) / 32 * 32;
   const size_t esz = (p->flags & RF_STORE_FP16) ? 4 : 8;
   const size_t rows = (size_t)p->nbl * p->nchan;
@@ -714,11 +714,8 @@ rf_status alloc_device(rf_plan* p) {
   if ((s = up(&d_crow, p->cell_row)) != RF_OK) return s;
   if ((s = up(&d_ent, p->ent)) != RF_OK) return s;
   if ((s = up(&d_ogc, p->ongrid_chan)) != RF_OK) return s;
-  std::vector<float2> tw(N);
-  for (int m = 0; m < N; ++m) {
-    const double a = kTwoPi * (double)m / (double)N;
-    tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
-  }
+  std::vector<float2> tw(rf::fft_twiddle_len(N));
+  rf::fft_twiddle_table(N, tw.data());
   float2* d_tw = nullptr;
   if ((s = up(&d_tw, tw)) != RF_OK) return s;
   p->tb.delays = d_delays;
@@ -1496,7 +1493,7 @@ rf_status rf_periodicity_search(rf_plan* p, const void* vis, int32_t nint, int32
   rf::DevPeriodic* d_pst = nullptr;
   rf::DevPeriodic* d_pc = nullptr;
   int* d_npc = nullptr;
-  if ((s = sc.get(&d_per, (size_t)nb_max * per_dm / sizeof(float2))) != RF_OK || (s = sc.get(&d_twl, L)) != RF_OK ||
+  if ((s = sc.get(&d_per, (size_t)nb_max * per_dm / sizeof(float2))) != RF_OK || (s = sc.get(&d_twl, rf::fft_twiddle_len(L))) != RF_OK ||
       (s = sc.get(&d_dms, nb_max)) != RF_OK || (s = sc.get(&d_zero, p->nchan)) != RF_OK ||
       (s = sc.get(&d_ones, 2 * nb_max)) != RF_OK || (s = sc.get(&d_lps, 2 * nb_max)) != RF_OK ||
       (s = sc.get(&d_sdt, 2 * nb_max)) != RF_OK || (s = sc.get(&d_grp, (size_t)nb_max * nkb * 2)) != RF_OK ||
@@ -1504,12 +1501,9 @@ rf_status rf_periodicity_search(rf_plan* p, const void* vis, int32_t nint, int32
       (s = sc.get(&d_pc, npairs_total)) != RF_OK || (s = sc.get(&d_npc, 1)) != RF_OK)
     return s;
   {
-    std::vector<float2> tw(L);
-    for (int m = 0; m < L; ++m) {
-      const double a = kTwoPi * (double)m / (double)L;
-      tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
-    }
-    RF_CUDA(cudaMemcpyAsync(d_twl, tw.data(), L * sizeof(float2), cudaMemcpyHostToDevice, st));
+    std::vector<float2> tw(rf::fft_twiddle_len(L));
+    rf::fft_twiddle_table(L, tw.data());
+    RF_CUDA(cudaMemcpyAsync(d_twl, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
     std::vector<int> ones(2 * nb_max, 1), lps(2 * nb_max, kpad);
     RF_CUDA(cudaMemcpyAsync(d_ones, ones.data(), ones.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     RF_CUDA(cudaMemcpyAsync(d_lps, lps.data(), lps.size() * sizeof(int), cudaMemcpyHostToDevice, st));

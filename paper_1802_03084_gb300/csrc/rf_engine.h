@@ -83,6 +83,20 @@ struct CandRef {
   int32_t pad[3];
 };
 
+// Twiddle table of a length-n FFT (n a power of two, 16..8192): entries
+// [0, n) hold exp(+2 pi i m / n); when the transform has a second pass
+// (n >= 64) entries n + r * 32 + k, r < P2, k < 32, hold that pass's
+// twiddles exp(+2 pi i k r / (32 P2)), P2 = fft_pass2_radix(n).  All are
+// computed in FP64 and rounded to FP32.
+constexpr int fft_ilog2(int n) { return n <= 1 ? 0 : 1 + fft_ilog2(n >> 1); }
+constexpr int fft_pass2_radix(int n) {
+  // radix-E passes (E = 32, 16 for n = 16), the last of radix n / E^k
+  return n < 64 ? 0 : (fft_ilog2(n) < 10 ? (1 << (fft_ilog2(n) - 5)) : 32);
+}
+constexpr int fft_twiddle_len(int n) { return n + 32 * fft_pass2_radix(n); }
+// Fills out[0 .. fft_twiddle_len(n)).
+void fft_twiddle_table(int n, float2* out);
+
 // Cell of an off-grid (baseline, channel) in the per-row cell table.
 constexpr int kOffGrid = -2147483647 - 1;
 

@@ -16,10 +16,11 @@
 // place.  Transforms of at most 32 threads synchronise with __syncwarp, wider
 // ones with a named barrier of their own.  Sign +1 (inverse DFT), no 1/N.
 //
-// Twiddles: per butterfly, the powers w^(s r), r < P, are built from the
-// table values w^s, w^2s, w^4s, ... (FP64-computed, rounded to FP32) by one
-// complex product each, so every twiddle is at most four roundings away
-// from the table.
+// Twiddles: the second pass (Ns = E) reads its P - 1 twiddles per butterfly
+// from a table of exactly those values that follows the N table entries
+// (FP64-computed, rounded to FP32).  A third pass (N >= 2048, radix 2..8)
+// builds the powers w^(s r) from the table values w^s, w^2s, w^4s by one
+// complex product each, at most four roundings from the table.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -187,7 +188,9 @@ struct FftShape {
   static constexpr int RL = 1 << (LOG2N % LOG2E);       // last radix (1 = none)
   static constexpr int NPASS = NFULL + (RL > 1 ? 1 : 0);
   static constexpr int LAST_P = RL > 1 ? RL : E;
+  static constexpr int P2 = NPASS == 1 ? 0 : (NPASS == 2 ? LAST_P : E);  // radix of the second pass
   static constexpr int STRIDE = N + N / 32 + 2;         // float2 per transform buffer
+  static_assert(NPASS <= 3, "at most three passes");
 };
 
 template <int N>
@@ -251,6 +254,22 @@ __device__ __forceinline__ void pass_compute(float2 (&v)[FftShape<N>::E], const 
   }
 }
 
+// Twiddle + radix-P DFT of the second pass (Ns = E): butterfly j takes
+// exp(+2 pi i k r / (E P)), k = j mod E, from tw2[r E + k] (consecutive k
+// across the transform's threads: one coalesced load per r).
+template <int N, int P>
+__device__ __forceinline__ void pass2_compute(float2 (&v)[FftShape<N>::E], const float2* __restrict__ tw2, int t) {
+  constexpr int E = FftShape<N>::E;
+  constexpr int T = FftShape<N>::T;
+#pragma unroll
+  for (int m = 0; m < E / P; ++m) {
+    const int k = (t + m * T) & (E - 1);
+#pragma unroll
+    for (int r = 1; r < P; ++r) v[m * P + r] = cmul(v[m * P + r], __ldg(tw2 + r * E + k));
+    dft<P>(v + m * P);
+  }
+}
+
 // Store phase of a non-final pass.
 template <int N, int P>
 __device__ __forceinline__ void pass_store(const float2 (&v)[FftShape<N>::E], float2* s, int t, int Ns) {
@@ -266,32 +285,40 @@ __device__ __forceinline__ void pass_store(const float2 (&v)[FftShape<N>::E], fl
   }
 }
 
+// max(a, b, c) in one instruction (a NaN operand is ignored, as by fmaxf).
+__device__ __forceinline__ float fmax3f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
 // Runs the passes after the first-pass load.  On entry v holds the first
-// pass's inputs (v[r] = x[t + r T]); on return the thread holds the outputs
+// pass's inputs (v[r] = x[t + r T]); `tw` is the transform's twiddle table
+// (fft_twiddle_len(N) entries: the N powers of w, then the second pass's
+// table); on return the thread holds the outputs
 // X[o] for o = t + m T + q (N / LAST_P) in v[m LAST_P + dft_perm(q)].
 template <int N>
 __device__ __forceinline__ void fft_inverse_from_regs(float2 (&v)[FftShape<N>::E], float2* s,
                                                       const float2* __restrict__ tw, int t, int xf) {
   using S = FftShape<N>;
-  if (S::NPASS == 1) {
+  if constexpr (S::NPASS == 1) {
     pass_compute<N, S::LAST_P>(v, tw, t, 1);
-    return;
-  }
-  pass_compute<N, S::E>(v, tw, t, 1);
-  pass_store<N, S::E>(v, s, t, 1);
-  fft_sync<S::T>(xf);
-  int Ns = S::E;
-#pragma unroll
-  for (int p = 1; p < S::NPASS - 1; ++p) {
-    pass_load<N, S::E>(v, s, t);
+  } else {
+    pass_compute<N, S::E>(v, tw, t, 1);
+    pass_store<N, S::E>(v, s, t, 1);
     fft_sync<S::T>(xf);
-    pass_compute<N, S::E>(v, tw, t, Ns);
-    pass_store<N, S::E>(v, s, t, Ns);
-    fft_sync<S::T>(xf);
-    Ns *= S::E;
+    pass_load<N, S::P2>(v, s, t);
+    if constexpr (S::NPASS == 2) {
+      pass2_compute<N, S::P2>(v, tw + N, t);
+    } else {
+      fft_sync<S::T>(xf);
+      pass2_compute<N, S::E>(v, tw + N, t);
+      pass_store<N, S::E>(v, s, t, S::E);
+      fft_sync<S::T>(xf);
+      pass_load<N, S::LAST_P>(v, s, t);
+      pass_compute<N, S::LAST_P>(v, tw, t, S::E * S::E);
+    }
   }
-  pass_load<N, S::LAST_P>(v, s, t);
-  pass_compute<N, S::LAST_P>(v, tw, t, Ns);
 }
 
 // The same with the first-pass inputs read from the padded buffer `s`

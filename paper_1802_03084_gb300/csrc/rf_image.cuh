@@ -63,6 +63,7 @@ struct ImgCfg {
   static constexpr int SWZ_SH = CH == 4 ? 1 : (CH == 2 ? 2 : 0);
   __device__ static __forceinline__ int swz(int u, int c) { return c ^ ((u >> SWZ_SH) & (CH - 1)); }
   static_assert(T <= 32 || (XA <= 15 && XB <= 15), "named barriers: at most 15 wide transforms per block");
+  static_assert(FftShape<N>::P2 == fft_pass2_radix(N), "twiddle table layout and FFT passes disagree");
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -345,9 +346,9 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     float mxa[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
     float mya[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
 #pragma unroll
-    for (int e = 0; e < K::E; ++e) {
-      mxa[e & 3] = fmaxf(mxa[e & 3], v[e].x);
-      mya[e & 3] = fmaxf(mya[e & 3], v[e].y);
+    for (int e = 0; e < K::E; e += 2) {
+      mxa[(e >> 1) & 3] = fmax3f(mxa[(e >> 1) & 3], v[e].x, v[e + 1].x);
+      mya[(e >> 1) & 3] = fmax3f(mya[(e >> 1) & 3], v[e].y, v[e + 1].y);
     }
     const float mx = fmaxf(fmaxf(mxa[0], mxa[1]), fmaxf(mxa[2], mxa[3]));
     const float my = fmaxf(fmaxf(mya[0], mya[1]), fmaxf(mya[2], mya[3]));

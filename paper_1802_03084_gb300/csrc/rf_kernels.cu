@@ -7,11 +7,27 @@
 #include <limits.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "rf_async.cuh"
 #include "rf_engine.h"
 
 namespace rf {
+
+void fft_twiddle_table(int n, float2* out) {
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int m = 0; m < n; ++m) {
+    const double a = two_pi * (double)m / (double)n;
+    out[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  const int p2 = fft_pass2_radix(n);
+  const int len = 32 * p2;
+  for (int r = 0; r < p2; ++r)
+    for (int k = 0; k < 32; ++k) {
+      const double a = two_pi * (double)((k * r) % len) / (double)len;
+      out[n + r * 32 + k] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+}
 
 // ----------------------------------------------------------------- ingest --
 // Stokes I (Sec. 3.1: a Stokes I image; Table 1: two polarisations) is the

@@ -36,16 +36,12 @@ constexpr size_t kPartialBytes = 4096 * sizeof(StatPartial);
 constexpr size_t kColsqBytes = (kMaxN / 2 + 64) * sizeof(float);  // Parseval column sums + mean term
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kTBytes + kPartialBytes + kColsqBytes];
 
-// Twiddle tables exp(+2 pi i m / N), m < N, for N = 16, 32, ..., kMaxN, back
-// to back (constants written once per device at set-up, not scratch).
-constexpr int kTwiddleElems = 2 * kMaxN - 16;
+// Twiddle tables of the length-N transforms (fft_twiddle_table) for N = 16,
+// 32, ..., kMaxN, back to back (constants written once per device at
+// set-up, not scratch).
+constexpr int twiddle_offset(int n) { return n <= 16 ? 0 : twiddle_offset(n >> 1) + fft_twiddle_len(n >> 1); }
+constexpr int kTwiddleElems = twiddle_offset(kMaxN) + fft_twiddle_len(kMaxN);
 static __device__ __align__(256) float2 g_noalloc_twiddle[kTwiddleElems];
-
-int twiddle_offset(int n) {
-  int off = 0;
-  for (int m = 16; m < n; m <<= 1) off += m;
-  return off;
-}
 
 struct DeviceSetup {
   bool ready = false;
@@ -77,13 +73,7 @@ rf_status ensure_setup(int dev, DeviceSetup** out) {
     if (e != cudaSuccess) return setup_error(RF_ERR_CUDA, "cudaGetSymbolAddress(twiddle)", e);
     d.twiddle = static_cast<float2*>(p);
     std::vector<float2> tw(kTwiddleElems);
-    for (int n = 16; n <= kMaxN; n <<= 1) {
-      const int off = twiddle_offset(n);
-      for (int m = 0; m < n; ++m) {
-        const double a = 6.283185307179586476925286766559 * (double)m / (double)n;
-        tw[off + m] = make_float2((float)std::cos(a), (float)std::sin(a));
-      }
-    }
+    for (int n = 16; n <= kMaxN; n <<= 1) fft_twiddle_table(n, tw.data() + twiddle_offset(n));
     e = cudaMemcpy(d.twiddle, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return setup_error(RF_ERR_CUDA, "twiddle upload", e);
     d.ready = true;
