@@ -204,7 +204,11 @@ const char* rf_last_error(void);
  * rf_search_segment: search one segment (Sec. 3.1-3.2).
  * vis      [nint][nbl][nchan][npol] complex64 (interleaved float re, im),
  *          host memory (pinned or pageable) or device memory on the plan's
- *          device; the kind is detected.  Host data is copied in chunks.
+ *          device; the kind is detected.  Device memory and page-locked host
+ *          memory the device can address (cudaHostAlloc, cudaHostRegister)
+ *          are read in place by the ingest kernel, the latter over the
+ *          host link; other host data is copied in chunks through a staging
+ *          buffer.  Host data must stay unchanged until the call returns.
  * nint     integrations in the segment, 1 <= nint <= max_nint.
  * stream   cudaStream_t to run on (NULL = default stream).
  * out      host array of `cap` candidates; receives the candidates sorted by

@@ -806,14 +806,22 @@ SegmentGeom geom(const rf_plan* p, int nint) {
   return g;
 }
 
-// Copy (if on the host) and ingest the segment into S.
+// Ingest the segment into S.  Device input is read in place.  Page-locked
+// host input that the device can address (cudaHostAlloc / cudaHostRegister
+// memory, mapped into the device's address space) is also read in place by
+// the ingest kernel, over the host link, with no staging copy.  Other host
+// memory goes through the staging buffer in chunks.
 rf_status ingest(rf_plan* p, const void* vis, int nint, cudaStream_t st) {
   cudaPointerAttributes attr;
   bool on_device = false;
+  const void* mapped = nullptr;
   if (cudaPointerGetAttributes(&attr, vis) == cudaSuccess) {
     on_device = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
     if (on_device && attr.type == cudaMemoryTypeDevice && attr.device != p->device)
       return fail(RF_ERR_INVALID_ARG, "vis is on device %d, plan is on device %d", attr.device, p->device);
+    if (attr.type == cudaMemoryTypeHost && attr.devicePointer != nullptr &&
+        (uintptr_t)attr.devicePointer % 16 == 0)
+      mapped = attr.devicePointer;
   } else {
     cudaGetLastError();
   }
@@ -821,6 +829,9 @@ rf_status ingest(rf_plan* p, const void* vis, int nint, cudaStream_t st) {
   if (on_device) {
     if ((uintptr_t)vis % 16 != 0) return fail(RF_ERR_INVALID_ARG, "device vis must be 16-byte aligned");
     RF_TIMED(p->prof, K_INGEST, st, rf::launch_ingest(static_cast<const float2*>(vis), nint, 0, p->npol, g, p->d_S, st));
+  } else if (mapped) {
+    RF_TIMED(p->prof, K_INGEST, st,
+             rf::launch_ingest(static_cast<const float2*>(mapped), nint, 0, p->npol, g, p->d_S, st));
   } else {
     const size_t per_int = (size_t)p->nbl * p->nchan * p->npol * sizeof(float2);
     const unsigned char* src = static_cast<const unsigned char*>(vis);
