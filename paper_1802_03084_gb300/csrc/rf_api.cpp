@@ -802,6 +802,14 @@ SegmentGeom geom(const rf_plan* p, int nint) {
   g.max_cells = p->max_cells;
   g.ncells = p->n_cells;
   g.nranges = (int)p->ranges.size();
+  g.partial = (p->flags & RF_EDGE_PARTIAL) != 0;
+  {
+    // largest series: rows of dt * ceil(nint_pad / dt) samples
+    uint64_t pitch = 0;
+    for (int k = 0; k < (int)p->sdt_lp.size(); ++k)
+      pitch = std::max<uint64_t>(pitch, (uint64_t)p->dt[k] * p->sdt_lp[k]);
+    g.idx32 = (uint64_t)p->nbl * p->nchan * pitch < (1ull << 32);
+  }
   g.fp16 = (p->flags & RF_STORE_FP16) != 0;
   return g;
 }
@@ -1536,7 +1544,9 @@ rf_status rf_periodicity_search(rf_plan* p, const void* vis, int32_t nint, int32
   const SegmentGeom g = geom(p, nint);
   SegmentGeom gp = g;
   gp.nint = K;
-  gp.fp16 = false;  // the transformed series are FP32 whatever the storage
+  gp.fp16 = false;   // the transformed series are FP32 whatever the storage
+  gp.partial = false;  // every frequency index k - kmin < K of a group is present
+  gp.idx32 = (uint64_t)nrows * kpad < (1ull << 32);
 
   for (int b0 = 0; b0 < ndms; b0 += nb_max) {
     const int nb = std::min(nb_max, ndms - b0);

@@ -85,9 +85,10 @@ struct CandRef {
 
 // Twiddle table of a length-n FFT (n a power of two, 16..8192): entries
 // [0, n) hold exp(+2 pi i m / n); when the transform has a second pass
-// (n >= 64) entries n + r * 32 + k, r < P2, k < 32, hold that pass's
-// twiddles exp(+2 pi i k r / (32 P2)), P2 = fft_pass2_radix(n).  All are
-// computed in FP64 and rounded to FP32.
+// (n >= 64) entries n + (r / 2) 64 + 2 k + (r mod 2), r < P2, k < 32, hold
+// that pass's twiddles exp(+2 pi i k r / (32 P2)), P2 = fft_pass2_radix(n)
+// (the two r of a pair side by side, for 16-byte loads).  All are computed
+// in FP64 and rounded to FP32.
 constexpr int fft_ilog2(int n) { return n <= 1 ? 0 : 1 + fft_ilog2(n >> 1); }
 constexpr int fft_pass2_radix(int n) {
   // radix-E passes (E = 32, 16 for n = 16), the last of radix n / E^k
@@ -142,6 +143,8 @@ struct SegmentGeom {
   int max_cells;  // largest number of occupied cells in one column
   int ncells;     // occupied cells of the half plane
   int nranges;    // gridding ranges
+  bool partial;   // PARTIAL edge rule: a sample at or past nint is absent
+  bool idx32;     // every sample index of every resampled series fits in 32 bits
   bool fp16;      // Stokes-I stored as half2
 };
 

@@ -50,8 +50,31 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)));
   return f2_unpack(d);
 }
+// Packed FP32-pair multiply and fused multiply-add (rounded to nearest).
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+  return f2_unpack(d);
+}
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)), "l"(f2_pack(c)));
+  return f2_unpack(d);
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a times the constant twiddle (c, s) as two packed instructions:
+// (a.x, a.x) (c, s) + (a.y, a.y) (-s, c).
+__device__ __forceinline__ float2 cmul_const(float2 a, float c, float s) {
+  return f2_fma(make_float2(a.y, a.y), make_float2(-s, c), f2_mul(make_float2(a.x, a.x), make_float2(c, s)));
+}
+// t + i u and t - i u as one packed FMA each on the swapped pair (u.y, u.x).
+__device__ __forceinline__ float2 c_add_iu(float2 t, float2 u) {
+  return f2_fma(make_float2(u.y, u.x), make_float2(-1.f, 1.f), t);
+}
+__device__ __forceinline__ float2 c_sub_iu(float2 t, float2 u) {
+  return f2_fma(make_float2(u.y, u.x), make_float2(1.f, -1.f), t);
 }
 __device__ __forceinline__ float2 cmul_i(float2 a) { return make_float2(-a.y, a.x); }  // i * a
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
@@ -70,104 +93,137 @@ __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c
 // Padded shared-memory index: one spare slot every 32 complex values.
 __host__ __device__ __forceinline__ constexpr int padx(int i) { return i + (i >> 5); }
 
+// Two styles of the same arithmetic, picked per kernel at compile time
+// (PK): with PK the products by constant twiddles are packed FP32-pair
+// instructions, cmul_const, and the radix-4 outputs t1 +- i u take one packed
+// FMA each on the swapped pair (u.y, u.x); without it both are scalar.  The
+// packed style issues fewer instructions but needs more registers: it is
+// faster in the column pass and slower in the row pass.
+template <bool PK>
+__device__ __forceinline__ float2 cmul_c(float2 a, float c, float s) {
+  if constexpr (PK) return cmul_const(a, c, s);
+  else return cmul(a, make_float2(c, s));
+}
+
 // In-register inverse radix-4 on v[0], v[S], v[2S], v[3S] (natural order out).
-// The odd outputs t1 +- i u mix the components of u, so they stay scalar.
-template <int S>
+template <int S, bool PK>
 __device__ __forceinline__ void dft4(float2* v) {
   const float2 t0 = cadd(v[0], v[2 * S]);
   const float2 t1 = csub(v[0], v[2 * S]);
   const float2 t2 = cadd(v[S], v[3 * S]);
   const float2 u = csub(v[S], v[3 * S]);
   v[0] = cadd(t0, t2);
-  v[S] = make_float2(t1.x - u.y, t1.y + u.x);
   v[2 * S] = csub(t0, t2);
-  v[3 * S] = make_float2(t1.x + u.y, t1.y - u.x);
+  if constexpr (PK) {
+    v[S] = c_add_iu(t1, u);
+    v[3 * S] = c_sub_iu(t1, u);
+  } else {
+    v[S] = make_float2(t1.x - u.y, t1.y + u.x);
+    v[3 * S] = make_float2(t1.x + u.y, t1.y - u.x);
+  }
 }
 
 // Radix-P inverse DFT of v[0..P) in registers; X[q] ends in v[dft_perm<P>(q)].
-template <int P>
-__device__ __forceinline__ void dft(float2* v);
+template <int P, bool PK>
+struct DftK;
 
-template <>
-__device__ __forceinline__ void dft<1>(float2*) {}
+template <bool PK>
+struct DftK<1, PK> {
+  __device__ static __forceinline__ void run(float2*) {}
+};
 
-template <>
-__device__ __forceinline__ void dft<2>(float2* v) {
-  float2 a = v[0], b = v[1];
-  v[0] = cadd(a, b);
-  v[1] = csub(a, b);
-}
+template <bool PK>
+struct DftK<2, PK> {
+  __device__ static __forceinline__ void run(float2* v) {
+    const float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
 
-template <>
-__device__ __forceinline__ void dft<4>(float2* v) { dft4<1>(v); }
+template <bool PK>
+struct DftK<4, PK> {
+  __device__ static __forceinline__ void run(float2* v) { dft4<1, PK>(v); }
+};
 
 // 8 = 2 x 4: r = 4 r1 + r2, q = q1 + 2 q2.  Radix-2 over r1 for each r2,
 // twiddle w8^(r2 q1), radix-4 over r2; X[q1 + 2 q2] lands in v[4 q1 + q2].
-template <>
-__device__ __forceinline__ void dft<8>(float2* v) {
+template <bool PK>
+struct DftK<8, PK> {
+  __device__ static __forceinline__ void run(float2* v) {
 #pragma unroll
-  for (int r2 = 0; r2 < 4; ++r2) {
-    float2 a = v[r2], b = v[r2 + 4];
-    v[r2] = cadd(a, b);
-    v[r2 + 4] = csub(a, b);
+    for (int r2 = 0; r2 < 4; ++r2) {
+      const float2 a = v[r2], b = v[r2 + 4];
+      v[r2] = cadd(a, b);
+      v[r2 + 4] = csub(a, b);
+    }
+    v[5] = cmul_c<PK>(v[5], RF_R2_2, RF_R2_2);
+    v[6] = cmul_i(v[6]);
+    v[7] = cmul_c<PK>(v[7], -RF_R2_2, RF_R2_2);
+    dft4<1, PK>(v);
+    dft4<1, PK>(v + 4);
   }
-  v[5] = cmul(v[5], make_float2(RF_R2_2, RF_R2_2));
-  v[6] = cmul_i(v[6]);
-  v[7] = cmul(v[7], make_float2(-RF_R2_2, RF_R2_2));
-  dft4<1>(v);
-  dft4<1>(v + 4);
-}
+};
 
 // 16 = 4 x 4: r = 4 r1 + r2, q = q1 + 4 q2.  Radix-4 over r1 for each r2
 // (stride 4) leaves Y[r2][q1] at v[r2 + 4 q1]; twiddle w16^(r2 q1); radix-4
 // over r2, i.e. over the contiguous v[4 q1 .. 4 q1 + 3]; X[q1 + 4 q2] lands
 // in v[4 q1 + q2].
-template <>
-__device__ __forceinline__ void dft<16>(float2* v) {
+template <bool PK>
+struct DftK<16, PK> {
+  __device__ static __forceinline__ void run(float2* v) {
 #pragma unroll
-  for (int r2 = 0; r2 < 4; ++r2) dft4<4>(v + r2);
-  v[5] = cmul(v[5], make_float2(RF_C32_2, RF_S32_2));     // w16^1
-  v[9] = cmul(v[9], make_float2(RF_R2_2, RF_R2_2));       // w16^2
-  v[13] = cmul(v[13], make_float2(RF_S32_2, RF_C32_2));   // w16^3
-  v[6] = cmul(v[6], make_float2(RF_R2_2, RF_R2_2));       // w16^2
-  v[10] = cmul_i(v[10]);                                  // w16^4
-  v[14] = cmul(v[14], make_float2(-RF_R2_2, RF_R2_2));    // w16^6
-  v[7] = cmul(v[7], make_float2(RF_S32_2, RF_C32_2));     // w16^3
-  v[11] = cmul(v[11], make_float2(-RF_R2_2, RF_R2_2));    // w16^6
-  v[15] = cmul(v[15], make_float2(-RF_C32_2, -RF_S32_2)); // w16^9
+    for (int r2 = 0; r2 < 4; ++r2) dft4<4, PK>(v + r2);
+    v[5] = cmul_c<PK>(v[5], RF_C32_2, RF_S32_2);      // w16^1
+    v[9] = cmul_c<PK>(v[9], RF_R2_2, RF_R2_2);        // w16^2
+    v[13] = cmul_c<PK>(v[13], RF_S32_2, RF_C32_2);    // w16^3
+    v[6] = cmul_c<PK>(v[6], RF_R2_2, RF_R2_2);        // w16^2
+    v[10] = cmul_i(v[10]);                            // w16^4
+    v[14] = cmul_c<PK>(v[14], -RF_R2_2, RF_R2_2);     // w16^6
+    v[7] = cmul_c<PK>(v[7], RF_S32_2, RF_C32_2);      // w16^3
+    v[11] = cmul_c<PK>(v[11], -RF_R2_2, RF_R2_2);     // w16^6
+    v[15] = cmul_c<PK>(v[15], -RF_C32_2, -RF_S32_2);  // w16^9
 #pragma unroll
-  for (int q1 = 0; q1 < 4; ++q1) dft4<1>(v + 4 * q1);
-}
+    for (int q1 = 0; q1 < 4; ++q1) dft4<1, PK>(v + 4 * q1);
+  }
+};
 
 // 32 = 2 x 16: r = 16 r1 + r2, q = q1 + 2 q2.  Radix-2 over r1 for each r2
 // leaves Y[r2][q1] at v[r2 + 16 q1]; twiddle w32^(r2 q1); radix-16 over the
 // contiguous halves; X[q1 + 2 q2] lands in v[16 q1 + dft_perm<16>(q2)].
-template <>
-__device__ __forceinline__ void dft<32>(float2* v) {
+template <bool PK>
+struct DftK<32, PK> {
+  __device__ static __forceinline__ void run(float2* v) {
 #pragma unroll
-  for (int r2 = 0; r2 < 16; ++r2) {
-    float2 a = v[r2], b = v[r2 + 16];
-    v[r2] = cadd(a, b);
-    v[r2 + 16] = csub(a, b);
+    for (int r2 = 0; r2 < 16; ++r2) {
+      const float2 a = v[r2], b = v[r2 + 16];
+      v[r2] = cadd(a, b);
+      v[r2 + 16] = csub(a, b);
+    }
+    // w32^r for r = 1..15
+    v[17] = cmul_c<PK>(v[17], RF_C32_1, RF_S32_1);
+    v[18] = cmul_c<PK>(v[18], RF_C32_2, RF_S32_2);
+    v[19] = cmul_c<PK>(v[19], RF_C32_3, RF_S32_3);
+    v[20] = cmul_c<PK>(v[20], RF_R2_2, RF_R2_2);
+    v[21] = cmul_c<PK>(v[21], RF_S32_3, RF_C32_3);
+    v[22] = cmul_c<PK>(v[22], RF_S32_2, RF_C32_2);
+    v[23] = cmul_c<PK>(v[23], RF_S32_1, RF_C32_1);
+    v[24] = cmul_i(v[24]);
+    v[25] = cmul_c<PK>(v[25], -RF_S32_1, RF_C32_1);
+    v[26] = cmul_c<PK>(v[26], -RF_S32_2, RF_C32_2);
+    v[27] = cmul_c<PK>(v[27], -RF_S32_3, RF_C32_3);
+    v[28] = cmul_c<PK>(v[28], -RF_R2_2, RF_R2_2);
+    v[29] = cmul_c<PK>(v[29], -RF_C32_3, RF_S32_3);
+    v[30] = cmul_c<PK>(v[30], -RF_C32_2, RF_S32_2);
+    v[31] = cmul_c<PK>(v[31], -RF_C32_1, RF_S32_1);
+    DftK<16, PK>::run(v);
+    DftK<16, PK>::run(v + 16);
   }
-  // w32^r for r = 1..15
-  v[17] = cmul(v[17], make_float2(RF_C32_1, RF_S32_1));
-  v[18] = cmul(v[18], make_float2(RF_C32_2, RF_S32_2));
-  v[19] = cmul(v[19], make_float2(RF_C32_3, RF_S32_3));
-  v[20] = cmul(v[20], make_float2(RF_R2_2, RF_R2_2));
-  v[21] = cmul(v[21], make_float2(RF_S32_3, RF_C32_3));
-  v[22] = cmul(v[22], make_float2(RF_S32_2, RF_C32_2));
-  v[23] = cmul(v[23], make_float2(RF_S32_1, RF_C32_1));
-  v[24] = cmul_i(v[24]);
-  v[25] = cmul(v[25], make_float2(-RF_S32_1, RF_C32_1));
-  v[26] = cmul(v[26], make_float2(-RF_S32_2, RF_C32_2));
-  v[27] = cmul(v[27], make_float2(-RF_S32_3, RF_C32_3));
-  v[28] = cmul(v[28], make_float2(-RF_R2_2, RF_R2_2));
-  v[29] = cmul(v[29], make_float2(-RF_C32_3, RF_S32_3));
-  v[30] = cmul(v[30], make_float2(-RF_C32_2, RF_S32_2));
-  v[31] = cmul(v[31], make_float2(-RF_C32_1, RF_S32_1));
-  dft<16>(v);
-  dft<16>(v + 16);
+};
+
+template <int P, bool PK = false>
+__device__ __forceinline__ void dft(float2* v) {
+  DftK<P, PK>::run(v);
 }
 
 template <int P>
@@ -238,7 +294,7 @@ __device__ __forceinline__ void pass_load(float2 (&v)[FftShape<N>::E], const flo
 }
 
 // Twiddle + radix-P DFT of each butterfly held by the thread.
-template <int N, int P>
+template <int N, int P, bool PK = false>
 __device__ __forceinline__ void pass_compute(float2 (&v)[FftShape<N>::E], const float2* __restrict__ tw, int t,
                                              int Ns) {
   constexpr int E = FftShape<N>::E;
@@ -250,23 +306,30 @@ __device__ __forceinline__ void pass_compute(float2 (&v)[FftShape<N>::E], const 
       const int k = j & (Ns - 1);
       twiddle_mul<N, P>(v + m * P, tw, k * (N / (Ns * P)));
     }
-    dft<P>(v + m * P);
+    dft<P, PK>(v + m * P);
   }
 }
 
-// Twiddle + radix-P DFT of the second pass (Ns = E): butterfly j takes
-// exp(+2 pi i k r / (E P)), k = j mod E, from tw2[r E + k] (consecutive k
-// across the transform's threads: one coalesced load per r).
-template <int N, int P>
+// Twiddle + radix-P DFT of the second pass (Ns = E = 32): butterfly j takes
+// exp(+2 pi i k r / (32 P)), k = j mod 32, from the pair table
+// tw2[(r / 2) 64 + 2 k + (r mod 2)]: one 16-byte load per pair of r,
+// consecutive across the transform's threads.
+template <int N, int P, bool PK = false>
 __device__ __forceinline__ void pass2_compute(float2 (&v)[FftShape<N>::E], const float2* __restrict__ tw2, int t) {
   constexpr int E = FftShape<N>::E;
   constexpr int T = FftShape<N>::T;
+  static_assert(E == 32 && P % 2 == 0, "pair table of a radix-32 second pass");
 #pragma unroll
   for (int m = 0; m < E / P; ++m) {
     const int k = (t + m * T) & (E - 1);
+    const float4* w4 = reinterpret_cast<const float4*>(tw2) + k;
 #pragma unroll
-    for (int r = 1; r < P; ++r) v[m * P + r] = cmul(v[m * P + r], __ldg(tw2 + r * E + k));
-    dft<P>(v + m * P);
+    for (int rp = 0; rp < P / 2; ++rp) {
+      const float4 w = __ldg(w4 + rp * E);
+      if (rp > 0) v[m * P + 2 * rp] = cmul(v[m * P + 2 * rp], make_float2(w.x, w.y));
+      v[m * P + 2 * rp + 1] = cmul(v[m * P + 2 * rp + 1], make_float2(w.z, w.w));
+    }
+    dft<P, PK>(v + m * P);
   }
 }
 
@@ -297,40 +360,40 @@ __device__ __forceinline__ float fmax3f(float a, float b, float c) {
 // (fft_twiddle_len(N) entries: the N powers of w, then the second pass's
 // table); on return the thread holds the outputs
 // X[o] for o = t + m T + q (N / LAST_P) in v[m LAST_P + dft_perm(q)].
-template <int N>
+template <int N, bool PK = false>
 __device__ __forceinline__ void fft_inverse_from_regs(float2 (&v)[FftShape<N>::E], float2* s,
                                                       const float2* __restrict__ tw, int t, int xf) {
   using S = FftShape<N>;
   if constexpr (S::NPASS == 1) {
-    pass_compute<N, S::LAST_P>(v, tw, t, 1);
+    pass_compute<N, S::LAST_P, PK>(v, tw, t, 1);
   } else {
-    pass_compute<N, S::E>(v, tw, t, 1);
+    pass_compute<N, S::E, PK>(v, tw, t, 1);
     pass_store<N, S::E>(v, s, t, 1);
     fft_sync<S::T>(xf);
     pass_load<N, S::P2>(v, s, t);
     if constexpr (S::NPASS == 2) {
-      pass2_compute<N, S::P2>(v, tw + N, t);
+      pass2_compute<N, S::P2, PK>(v, tw + N, t);
     } else {
       fft_sync<S::T>(xf);
-      pass2_compute<N, S::E>(v, tw + N, t);
+      pass2_compute<N, S::E, PK>(v, tw + N, t);
       pass_store<N, S::E>(v, s, t, S::E);
       fft_sync<S::T>(xf);
       pass_load<N, S::LAST_P>(v, s, t);
-      pass_compute<N, S::LAST_P>(v, tw, t, S::E * S::E);
+      pass_compute<N, S::LAST_P, PK>(v, tw, t, S::E * S::E);
     }
   }
 }
 
 // The same with the first-pass inputs read from the padded buffer `s`
 // (filled and made visible to the transform's threads by the caller).
-template <int N>
+template <int N, bool PK = false>
 __device__ __forceinline__ void fft_inverse_to_regs(float2 (&v)[FftShape<N>::E], float2* s,
                                                     const float2* __restrict__ tw, int t, int xf) {
   using S = FftShape<N>;
   constexpr int P0 = S::NPASS == 1 ? S::LAST_P : S::E;
   pass_load<N, P0>(v, s, t);
   if (S::NPASS > 1) fft_sync<S::T>(xf);  // in place: all loads before the first store
-  fft_inverse_from_regs<N>(v, s, tw, t, xf);
+  fft_inverse_from_regs<N, PK>(v, s, tw, t, xf);
 }
 
 // Output index of register (m, q) after the last pass.

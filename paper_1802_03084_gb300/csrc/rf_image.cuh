@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_A, 2)
           for (int c = t; c < ncells; c += K::T) buf[padx(crow[c])] = cellv[c * PI + 2 * (kc ^ (c & (CPC - 1))) + ko];
         fft_sync<K::T>(xf);
         float2 v[K::E];
-        fft_inverse_to_regs<N>(v, buf, tb.twiddle, t, xf);
+        fft_inverse_to_regs<N, true>(v, buf, tb.twiddle, t, xf);  // packed style (see rf_fft.cuh)
         if (kl < nk) {
           const size_t slot = (size_t)(gr.img0 + kbase + kl - img_base);
           float2* dst = Tbuf + (slot * g.ncol + col) * N;

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "rf_async.cuh"
 #include "rf_engine.h"
@@ -25,7 +26,7 @@ void fft_twiddle_table(int n, float2* out) {
   for (int r = 0; r < p2; ++r)
     for (int k = 0; k < 32; ++k) {
       const double a = two_pi * (double)((k * r) % len) / (double)len;
-      out[n + r * 32 + k] = make_float2((float)std::cos(a), (float)std::sin(a));
+      out[n + (r >> 1) * 64 + 2 * k + (r & 1)] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
 }
 
@@ -205,10 +206,13 @@ cudaError_t launch_resample(const SegmentGeom& g, const void* S, void* Sdt, int 
 // t' dt + delta[d][c] of the dt-resampled series (phase delta mod dt, index
 // t' + delta div dt), so one load instruction reads 32 consecutive samples.
 // Each warp walks one host-made, cell-aligned range of gridding entries
-// (sorted by cell), entry metadata broadcast by shuffle and 16 sample loads
-// in flight per lane, sums every cell in registers in a fixed order
+// (sorted by cell), 32 entries at a time: lane l turns entry l into the
+// series offset of its sample for t' = 0 and a word holding its cell and
+// flags (and, under the PARTIAL edge rule, how many lanes have the sample);
+// those are broadcast by shuffle, with kGatherBatch sample loads in flight
+// per lane.  Every cell is summed in registers in a fixed order
 //   H[cell] = sum_entries (-1)^(iu+iv) R  (or conj R for folded entries)
-// and writes the cell's 32 values to cellbuf[group][cell][k] (one 256-byte
+// and its 32 values are written to cellbuf[group][cell][k] (one 256-byte
 // row).  No atomics: the grid is bitwise reproducible.
 template <bool FP16>
 __device__ __forceinline__ float2 load_s(const unsigned char* __restrict__ S, size_t i) {
@@ -218,9 +222,14 @@ __device__ __forceinline__ float2 load_s(const unsigned char* __restrict__ S, si
 
 constexpr int kGatherBatch = 4;  // samples each lane has in flight (swept: 4 at 6 blocks per SM beat 8-32 at 2-5)
 
-template <bool FP16>
+// Cell index and entry flags in one word: cells < 2^30 (at most (N/2 + 1) N
+// for N <= 8192); bit 30 = ENT_CONJ, bit 31 = ENT_NEG.
+constexpr unsigned kCellMask = (1u << 30) - 1u;
+
+template <bool FP16, bool IDX32, bool PARTIAL>
 __global__ void __launch_bounds__(256, 6) k_grid_cells(SegmentGeom g, DevTables tb, const Group* __restrict__ groups,
                                                     int g_begin, float2* __restrict__ cellbuf) {
+  using Off = typename std::conditional<IDX32, unsigned, unsigned long long>::type;
   extern __shared__ int sdel[];  // [nchan] delays of this group's DM
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -237,13 +246,12 @@ __global__ void __launch_bounds__(256, 6) k_grid_cells(SegmentGeom g, DevTables 
   const int dt = tb.dt_list[gr.s];
   const int lp = tb.sdt_lp[gr.s];
   const unsigned char* __restrict__ Sd = reinterpret_cast<const unsigned char*>(tb.sdt_ptr[gr.s]);
-  const size_t rowpitch = (size_t)dt * lp;
+  const Off rowpitch = (Off)dt * (Off)lp;
   const bool active = lane < gr.nimg;
-  const int tq = gr.t0 + lane;
-  const int lim = g.nint - tq * dt;  // the image has a sample iff delta < lim
+  const Off tq = (Off)(gr.t0 + lane);
   float2* __restrict__ out = cellbuf + (size_t)blockIdx.x * g.ncells * 32 + lane;
   float2 acc = make_float2(0.f, 0.f);
-  int cur = -1;
+  unsigned cur = 0xffffffffu;
   GridEntry nxt = {0, 0, 0, -1};
   if (ebeg + lane < eend) nxt = tb.ent[ebeg + lane];
   for (int base = ebeg; base < eend; base += 32) {
@@ -251,39 +259,54 @@ __global__ void __launch_bounds__(256, 6) k_grid_cells(SegmentGeom g, DevTables 
     const bool mine = base + lane < eend;
     if (base + 32 + lane < eend) nxt = tb.ent[base + 32 + lane];
     const int mydel = mine ? sdel[my.cflags >> 2] : 0;
-    const int mypart = (mydel % dt) * lp + mydel / dt;
+    // sample t' dt + delta lives at phase delta mod dt, index t' + delta div dt
+    const Off myoff = (Off)my.bc * rowpitch + (Off)((mydel % dt) * lp + mydel / dt);
+    const unsigned mycf = ((unsigned)my.cell & kCellMask) | ((unsigned)(my.cflags & 3) << 30);
+    // PARTIAL: lanes k with (t0 + k) dt + delta < nint have the sample
+    int mylim = 32;
+    if (PARTIAL) {
+      const int rem = g.nint - mydel - 1;
+      mylim = rem < 0 ? 0 : max(0, min(32, rem / dt - gr.t0 + 1));
+    }
     const int n = min(32, eend - base);
     for (int i0 = 0; i0 < n; i0 += kGatherBatch) {
       float2 a[kGatherBatch];
 #pragma unroll
       for (int q = 0; q < kGatherBatch; ++q) {
         const int i = (i0 + q) & 31;
-        const int bc = __shfl_sync(0xffffffffu, my.bc, i);
-        const int del = __shfl_sync(0xffffffffu, mydel, i);
-        const int part = __shfl_sync(0xffffffffu, mypart, i);
+        Off off;
+        if (IDX32)
+          off = __shfl_sync(0xffffffffu, myoff, i);
+        else
+          off = (Off)__shfl_sync(0xffffffffu, (unsigned long long)myoff, i);
+        bool ok = active && i0 + q < n;
+        if (PARTIAL) {
+          const int lim = __shfl_sync(0xffffffffu, mylim, i);  // every lane takes part in the shuffle
+          ok = ok && lane < lim;
+        }
         a[q] = make_float2(0.f, 0.f);
-        if (active && i0 + q < n && del < lim) a[q] = load_s<FP16>(Sd, (size_t)bc * rowpitch + part + tq);
+        if (ok) a[q] = load_s<FP16>(Sd, (size_t)(off + tq));
       }
 #pragma unroll
       for (int q = 0; q < kGatherBatch; ++q) {
-        const int i = (i0 + q) & 31;
-        const int cf = __shfl_sync(0xffffffffu, my.cflags, i);
-        const int cell = __shfl_sync(0xffffffffu, my.cell, i);
+        const unsigned cf = __shfl_sync(0xffffffffu, mycf, (i0 + q) & 31);
         if (i0 + q < n) {
-          if (cell != cur) {
-            if (cur >= 0) out[(size_t)cur * 32] = acc;
-            acc = make_float2(0.f, 0.f);
-            cur = cell;
-          }
-          const float sy = (cf & ENT_CONJ) ? -1.f : 1.f;
-          const float sg = (cf & ENT_NEG) ? -1.f : 1.f;
-          acc.x += sg * a[q].x;
-          acc.y += sg * sy * a[q].y;
+          const unsigned cell = cf & kCellMask;
+          const bool flush = cell != cur;  // the same on every lane
+          if (flush && cur != 0xffffffffu) out[(size_t)cur * 32] = acc;
+          acc.x = flush ? 0.f : acc.x;
+          acc.y = flush ? 0.f : acc.y;
+          cur = cell;
+          // sign of the real part: ENT_NEG; of the imaginary part: ENT_NEG ^ ENT_CONJ
+          const unsigned sx = cf & 0x80000000u;
+          const unsigned sy = (cf ^ (cf << 1)) & 0x80000000u;
+          acc.x += __uint_as_float(__float_as_uint(a[q].x) ^ sx);
+          acc.y += __uint_as_float(__float_as_uint(a[q].y) ^ sy);
         }
       }
     }
   }
-  if (cur >= 0) out[(size_t)cur * 32] = acc;
+  if (cur != 0xffffffffu) out[(size_t)cur * 32] = acc;
 }
 
 cudaError_t launch_grid_cells(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin,
@@ -291,10 +314,22 @@ cudaError_t launch_grid_cells(const SegmentGeom& g, const DevTables& tb, const G
   if (ngroups <= 0 || g.nranges <= 0) return cudaSuccess;
   dim3 grid(ngroups, (g.nranges + 7) / 8);
   const int smem = g.nchan * 4;
-  if (g.fp16)
-    k_grid_cells<true><<<grid, 256, smem, st>>>(g, tb, groups, g_begin, cellbuf);
-  else
-    k_grid_cells<false><<<grid, 256, smem, st>>>(g, tb, groups, g_begin, cellbuf);
+#define RF_GRID(F16, I32, PART) \
+  k_grid_cells<F16, I32, PART><<<grid, 256, smem, st>>>(g, tb, groups, g_begin, cellbuf)
+  if (g.fp16) {
+    if (g.idx32) {
+      if (g.partial) RF_GRID(true, true, true); else RF_GRID(true, true, false);
+    } else {
+      if (g.partial) RF_GRID(true, false, true); else RF_GRID(true, false, false);
+    }
+  } else {
+    if (g.idx32) {
+      if (g.partial) RF_GRID(false, true, true); else RF_GRID(false, true, false);
+    } else {
+      if (g.partial) RF_GRID(false, false, true); else RF_GRID(false, false, false);
+    }
+  }
+#undef RF_GRID
   return cudaGetLastError();
 }
 
