@@ -69,6 +69,9 @@ def parse():
                     help="time the periodicity search, stream, mean subtraction and candidate products")
     ap.add_argument("--host-input", action="store_true",
                     help="time the search from pinned host input only (small device footprint for profilers)")
+    ap.add_argument("--nchan", type=int, default=0,
+                    help="search the workload with this many channels over the same band (a smaller device "
+                         "footprint for profilers; 0 = the workload's own)")
     ap.add_argument("--write-traffic", metavar="RAW_CSV",
                     help="write profiles/traffic.json from `ncu -i <rep> --page raw --csv` output of the imaging "
                          "kernels (no GPU needed) and exit")
@@ -605,6 +608,8 @@ def main():
     rf.lib()
 
     spec = synth.config(args.config)
+    if args.nchan:
+        spec.nchan = args.nchan
     spec.seed = rank_seed(spec.seed, rank)   # each rank searches its own segment
     seg = synth.make_segment(spec)
     nint = spec.nint

@@ -49,7 +49,6 @@ rf_status fail(rf_status s, const char* fmt, ...) {
 
 constexpr double kDispConst = 4.1488e-3;  // s GHz^2 per pc cm^-3 (Sec. 2.1 footnote)
 constexpr double kCLight = 299792458.0;   // m/s
-constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr uint32_t kKnownFlags = RF_STORE_FP16 | RF_EDGE_PARTIAL | RF_MEAN_SUBTRACT | RF_NOISE_CLIPPED | RF_HOST_ONLY;
 constexpr size_t kStageBytes = 256ull << 20;   // host->device chunk of raw visibilities
 constexpr size_t kTBudgetBytes = 4096ull << 20;  // column-FFT scratch per wave

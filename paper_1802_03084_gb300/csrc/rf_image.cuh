@@ -474,6 +474,24 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
   }
 }
 
+// The most dynamic shared memory a block of `kern` can have: the device's
+// opt-in per-block limit (227 KB on sm_103a) less the kernel's static shared
+// memory.  Kernels whose request depends on the plan set their attribute to
+// this bound, not to the request: the attribute belongs to the kernel, and
+// plans searched at once on other host threads (the serving runtime) would
+// otherwise lower it under each other's launches.  0 if it cannot be read.
+template <class Kernel>
+int max_dynamic_smem(Kernel kern) {
+  cudaFuncAttributes fa;
+  int dev = 0, optin = 0;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return optin - (int)fa.sharedSizeBytes;
+}
+
 inline int sm_count() {
   static int n = [] {
     int dev = 0, v = 0;
@@ -620,8 +638,9 @@ cudaError_t run_rowfft_power(const SegmentGeom& g, const DevTables& tb, const fl
                              int npairs, StatPartial* partials, cudaStream_t st) {
   using K = ImgCfg<N>;
   const int smem = K::SMEM_B_FIXED + g.ncol * K::CH * 16;
-  if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_rowfft_power<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  static const int smem_max = max_dynamic_smem(k_rowfft_power<N>);
+  if (smem > smem_max) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_rowfft_power<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_rowfft_power<N>, cudaFuncAttributePreferredSharedMemoryCarveout,
                            cudaSharedmemCarveoutMaxShared);
@@ -643,8 +662,9 @@ cudaError_t run_colfft(const SegmentGeom& g, const DevTables& tb, const Group* g
                        cudaStream_t st) {
   using K = ImgCfg<N>;
   const int smem = K::SMEM_A_FIXED + g.max_cells * (K::PART_IMAGES * 8 + 4);
-  if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_colfft<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  static const int smem_max = max_dynamic_smem(k_colfft<N>);
+  if (smem > smem_max) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_colfft<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_colfft<N>, cudaFuncAttributePreferredSharedMemoryCarveout,
                            cudaSharedmemCarveoutMaxShared);
@@ -670,9 +690,10 @@ cudaError_t run_rowfft_stats_k(const SegmentGeom& g, const DevTables& tb, const 
                                const TileMap* tm, int* err, cudaStream_t st, const float2* clip) {
   using K = ImgCfg<N>;
   const int smem = K::SMEM_B_FIXED + (K::TILE_TMA ? 1024 : 0) + rowfft_tile_rows<N>(g.ncol) * K::CH * 16;
-  if (smem > 227 * 1024) return cudaErrorInvalidValue;
   auto kern = k_rowfft_stats<N, CLIP>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  static const int smem_max = max_dynamic_smem(kern);
+  if (smem > smem_max) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;

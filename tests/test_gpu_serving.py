@@ -31,8 +31,10 @@ def _mixed_segments():
                                  dt_list=[1, 2], threshold=6.0, seed=300 + (k % 5), edge="partial")
         spec.pulses = [dict(dm=100.0, t0_s=0.05, width_s=10e-3, amp=0.8, x=npix // 2 + 7, y=npix // 2 - 5)]
         seg = synth.make_segment(spec)
+        # two clipped-noise plans; segments 0 and 5 keep identical descriptions (a resident plan is reused)
+        flags = rf.RF_EDGE_PARTIAL | (rf.RF_NOISE_CLIPPED if k in (2, 6) else 0)
         desc = rf.make_desc(seg["ant_uvw"], seg["freq_hz"], spec.inttime_s, npix, spec.cell_rad, spec.dm_list,
-                            spec.dt_list, spec.threshold, flags=rf.RF_EDGE_PARTIAL, max_nint=nint)
+                            spec.dt_list, spec.threshold, flags=flags, max_nint=nint)
         out.append((spec, seg, desc))
     return out
 

@@ -44,10 +44,11 @@ def _key(r):
     return (int(r["dm_idx"]), int(r["dt_idx"]), int(r["t_idx"]))
 
 
-@pytest.mark.parametrize("edge", ["full", "partial"])
-def test_stream_equals_one_search_bit_for_bit(edge):
+@pytest.mark.parametrize("edge,clipped", [("full", False), ("partial", False), ("full", True)])
+def test_stream_equals_one_search_bit_for_bit(edge, clipped):
     spec = synth.config("tiny")
     spec.edge = edge
+    spec.noise_clipped = clipped
     spec.dt_list = [1, 2, 4]
     seg = synth.make_segment(spec, nint=900)
     gp, _ = plans_for(spec, seg)
