@@ -279,17 +279,27 @@ __device__ __forceinline__ void twiddle_mul(float2* v, const float2* __restrict_
   for (int r = 1; r < P; ++r) v[r] = cmul(v[r], W[r]);
 }
 
-// Load phase of one pass: v[m P + r] = s[j + r N/P], j = t + m T.
+// Load phase of one pass: v[m P + r] = s[j + r N/P], j = t + m T.  When
+// m T and r N/P are multiples of 32 (N >= 1024), padx(t + m T + r N/P) =
+// padx(t) + padx(m T) + padx(r N/P): one index per thread, the rest constant.
 template <int N, int P>
 __device__ __forceinline__ void pass_load(float2 (&v)[FftShape<N>::E], const float2* s, int t) {
   constexpr int E = FftShape<N>::E;
   constexpr int T = FftShape<N>::T;
   constexpr int J = N / P;
+  if constexpr (T % 32 == 0 && J % 32 == 0) {
+    const float2* st = s + padx(t);
 #pragma unroll
-  for (int m = 0; m < E / P; ++m) {
-    const int j = t + m * T;
+    for (int m = 0; m < E / P; ++m)
 #pragma unroll
-    for (int r = 0; r < P; ++r) v[m * P + r] = s[padx(j + r * J)];
+      for (int r = 0; r < P; ++r) v[m * P + r] = st[padx(m * T) + padx(r * J)];
+  } else {
+#pragma unroll
+    for (int m = 0; m < E / P; ++m) {
+      const int j = t + m * T;
+#pragma unroll
+      for (int r = 0; r < P; ++r) v[m * P + r] = s[padx(j + r * J)];
+    }
   }
 }
 
@@ -333,7 +343,9 @@ __device__ __forceinline__ void pass2_compute(float2 (&v)[FftShape<N>::E], const
   }
 }
 
-// Store phase of a non-final pass.
+// Store phase of a non-final pass.  Output q of butterfly j goes to
+// base + q Ns.  When q Ns is a multiple of 32, or Ns = 1 and base is (P = 32),
+// padx(base + q Ns) = padx(base) + padx(q Ns) with the second term constant.
 template <int N, int P>
 __device__ __forceinline__ void pass_store(const float2 (&v)[FftShape<N>::E], float2* s, int t, int Ns) {
   constexpr int E = FftShape<N>::E;
@@ -343,8 +355,14 @@ __device__ __forceinline__ void pass_store(const float2 (&v)[FftShape<N>::E], fl
     const int j = t + m * T;
     const int k = j & (Ns - 1);
     const int base = (j - k) * P + k;
+    if (Ns % 32 == 0 || (Ns == 1 && P % 32 == 0)) {
+      float2* sb = s + padx(base);
 #pragma unroll
-    for (int q = 0; q < P; ++q) s[padx(base + q * Ns)] = v[m * P + dft_perm<P>(q)];
+      for (int q = 0; q < P; ++q) sb[padx(q * Ns)] = v[m * P + dft_perm<P>(q)];
+    } else {
+#pragma unroll
+      for (int q = 0; q < P; ++q) s[padx(base + q * Ns)] = v[m * P + dft_perm<P>(q)];
+    }
   }
 }
 
