@@ -180,8 +180,11 @@ typedef struct rf_plan_info {
  * delay table of Sec. 2.1's dispersion law rounded to integrations, nearest
  * uv cells), upload them and allocate the device buffers for segments of up
  * to max_nint integrations.  On success *out owns all device state.
- * Errors: RF_ERR_INVALID_ARG (bad desc), RF_ERR_NO_DEVICE, RF_ERR_NO_MEMORY,
- * RF_ERR_CUDA.  *out is set to NULL on failure.
+ * Errors: RF_ERR_INVALID_ARG (bad desc; also a uv layout whose busiest
+ * column, or whose number of columns, does not fit the imaging kernels' shared
+ * memory at this npix: possible only for very large npix with many channels
+ * on fine cells), RF_ERR_NO_DEVICE, RF_ERR_NO_MEMORY, RF_ERR_CUDA.  *out is set
+ * to NULL on failure.
  */
 rf_status rf_plan_create(const rf_plan_desc* desc, struct rf_plan** out);
 

@@ -516,6 +516,28 @@ rf_status build_tables(rf_plan* p) {
       ci = cj;
     }
   }
+  // The column pass stages the cells of one column, and the row pass one tile
+  // of ncol rows, in a block's shared memory (at most 227 KB on sm_103a, less
+  // up to 1 KB of the kernels' static shared memory).
+  {
+    const long limit = 227l * 1024 - 1024;
+    const rf::ImageKernelShape& sh = p->shape;
+    const long smem_a = (long)sh.smem_a + (long)p->max_cells * sh.smem_a_per_cell;
+    int tile_rows = p->ncol;
+    if (sh.tile_tma) {
+      int nbox = 0, rows = 0;
+      rf::tile_boxes(p->ncol, &nbox, &rows);
+      tile_rows = nbox * rows;
+    }
+    const long smem_b = (long)sh.smem_b + (sh.tile_tma ? 1024 : 0) + (long)tile_rows * sh.smem_b_per_row;
+    if (smem_a > limit)
+      return fail(RF_ERR_INVALID_ARG,
+                  "a uv column holds %d occupied cells; the column pass fits at most %ld at npix %d "
+                  "(a coarser cell or a smaller npix spreads fewer cells per column)",
+                  p->max_cells, (limit - sh.smem_a) / sh.smem_a_per_cell, N);
+    if (smem_b > limit)
+      return fail(RF_ERR_INVALID_ARG, "%d uv columns do not fit the row pass's shared memory at npix %d", p->ncol, N);
+  }
   return RF_OK;
 }
 

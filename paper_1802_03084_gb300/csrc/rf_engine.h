@@ -238,6 +238,9 @@ struct ImageKernelShape {
   int partials_per_image; // row-pair partials written by pass B (N / 2)
   int threads_b;
   int smem_b;
+  int smem_a_per_cell;  // column pass: shared bytes per occupied cell of the largest column
+  int smem_b_per_row;   // row pass: shared bytes per tile row (one per column imaged)
+  bool tile_tma;        // row-pass tiles arrive by tensor copies (boxes, 1 KB alignment)
 };
 bool image_kernel_shape(int npix, ImageKernelShape* out);
 

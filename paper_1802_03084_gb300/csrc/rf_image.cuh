@@ -733,6 +733,9 @@ void fill_shape(ImageKernelShape* o) {
   o->partials_per_image = N / 2;
   o->threads_b = K::THREADS_B;
   o->smem_b = K::SMEM_B_FIXED;
+  o->smem_a_per_cell = K::PART_IMAGES * 8 + 4;
+  o->smem_b_per_row = K::CH * 16;
+  o->tile_tma = K::TILE_TMA;
 }
 
 #define RF_INSTANTIATE_IMAGE(N)                                                                              \

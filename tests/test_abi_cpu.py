@@ -183,3 +183,22 @@ def test_clipped_noise_flag_accepted_and_sized(L):
     b1 = rf.rf_plan_estimate_bytes(rf.make_desc(**kw), wave_images=1024)
     # one clipping window (two floats) per image slot of a wave
     assert b1 - b0 == 1024 * 8
+
+
+def test_plan_whose_column_overflows_shared_memory_is_rejected(L):
+    # one north-south baseline: every channel lands in column u = 0, spread over
+    # more than two thousand v cells at npix 8192 -- more than the column pass
+    # can stage in a block's shared memory
+    ant = np.array([[0.0, 0.0, 0.0], [0.0, 1000.0, 0.0]])
+    f = np.linspace(1.0e9, 3.0e9, 2048)
+    cell = 4000.0 * 299792458.0 / (1000.0 * 3.0e9 * 8192)
+    kw = dict(ant_uvw=ant, freq_hz=f, inttime_s=5e-3, npix=8192, cell_rad=cell, dm_list=[0.0], dt_list=[1],
+              threshold=6.0, flags=rf.RF_HOST_ONLY, max_nint=16)
+    with pytest.raises(rf.RfError) as e:
+        rf.rf_plan_create(rf.make_desc(**kw))
+    assert e.value.status == rf.RF_ERR_INVALID_ARG
+    assert "column" in rf.rf_last_error()
+    # the same geometry with 64 channels fits
+    kw["freq_hz"] = np.linspace(1.0e9, 3.0e9, 64)
+    with rf.Plan(**kw) as p:
+        assert p.info().n_cells > 0

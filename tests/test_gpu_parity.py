@@ -237,3 +237,25 @@ def test_autotune_keeps_results(tiny, tmp_path):
         assert np.array_equal(s0, s1) and np.array_equal(c0, c1)
         again = gp.autotune(seg["vis"], cache_path=cache)
         assert again["cached"] is True and again["wave_images"] == res["wave_images"]
+
+
+def test_maximum_image_size():
+    # npix 8192: one transform per block in the column pass, row-pass tiles of
+    # one 16-byte chunk per column in several tensor-copy boxes
+    rng = np.random.default_rng(8192)
+    seg = small_random_segment(rng, 5, 2, 2, 8192)
+    umax = 600.0 * seg["freq_hz"].max() / oracle.C_LIGHT
+    spec = synth.SegmentSpec(name="max", nchan=2, f_lo_hz=1e9, bw_hz=1e9, nint=2, inttime_s=2e-3, npix=8192,
+                             dm_list=np.array([0.0]), dt_list=[1], threshold=3.0, nant=5, cell_rad=0.47 / umax,
+                             edge="full")
+    gp, op = plans_for(spec, seg)
+    with gp:
+        assert gp.info().iu_max > 1024          # many columns: several tensor-copy boxes
+        gc, gst = gp.search_stats(seg["vis"])
+        oc, ost = oracle.search_segment(op, seg["vis"], with_stats=True)
+        assert len(gst) == len(ost) == 2
+        oim = oracle_images(op, seg["vis"], list(ost))
+        compare_stats(gst, ost, oim)
+        compare_candidates(gc, oc, spec.threshold, ost)
+        g = gp.render(seg["vis"], [(0, 0, 1)])
+        assert rel_rms(g[0], oim[(0, 0, 1)]) < IMG_RMS_FP32
