@@ -1438,11 +1438,14 @@ rf_status rf_candidate_products(rf_plan* p, const void* vis, int32_t nint, void*
   float2* d_spec32 = nullptr;
   double* d_smom = nullptr;
   double* d_imom = nullptr;
+  double* d_mpart = nullptr;
   float* d_img = nullptr;
   if ((s = sc.get(&d_refs, n)) != RF_OK || (s = sc.get(&d_spec, n * nch)) != RF_OK ||
       (s = sc.get(&d_wch, n * nch)) != RF_OK || (s = sc.get(&d_smom, (size_t)n * 6)) != RF_OK ||
       (s = sc.get(&d_imom, (size_t)n * 4)) != RF_OK || (s = sc.get(&d_img, (size_t)chunk * npx)) != RF_OK)
     return s;
+  const int mslices = rf::image_moment_slices(chunk, npx);
+  if ((s = sc.get(&d_mpart, (size_t)chunk * mslices * 4)) != RF_OK) return s;
   if (spectra && (s = sc.get(&d_spec32, n * nch)) != RF_OK) return s;
   RF_CUDA(cudaMemcpyAsync(d_refs, refs.data(), n * sizeof(rf::CandRef), cudaMemcpyHostToDevice, st));
   const SegmentGeom g = geom(p, nint);
@@ -1451,7 +1454,7 @@ rf_status rf_candidate_products(rf_plan* p, const void* vis, int32_t nint, void*
     const int m = std::min(chunk, n - k0);
     s = render_core(p, nint, trials.data() + 3 * (size_t)k0, m, d_img, st);
     if (s != RF_OK) return s;
-    RF_CUDA(rf::launch_image_moments(d_img, m, npx, d_imom + (size_t)k0 * 4, st));
+    RF_CUDA(rf::launch_image_moments(d_img, m, npx, mslices, d_mpart, d_imom + (size_t)k0 * 4, st));
     if (images)
       RF_CUDA(cudaMemcpyAsync(images + (size_t)k0 * npx, d_img, (size_t)m * npx * sizeof(float),
                               cudaMemcpyDeviceToHost, st));

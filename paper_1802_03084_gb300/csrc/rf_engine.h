@@ -253,8 +253,12 @@ void set_last_error(const char* msg);
 cudaError_t launch_cand_spectrum(const SegmentGeom& g, const DevTables& tb, const int2* cellbc, const CandRef* refs,
                                  int n, double2* spec, double* wch, float2* spec_out, double* spec_mom,
                                  cudaStream_t st);
-// out: [n][4] {mean, std, skew, excess kurtosis} of each image's npx pixels.
-cudaError_t launch_image_moments(const float* images, int n, size_t npx, double* out, cudaStream_t st);
+// out: [n][4] {mean, std, skew, excess kurtosis} of each image's npx pixels,
+// in nslices slices per image (image_moment_slices); part: [n][nslices][4]
+// scratch.
+int image_moment_slices(int n, size_t npx);
+cudaError_t launch_image_moments(const float* images, int n, size_t npx, int nslices, double* part, double* out,
+                                 cudaStream_t st);
 
 // Periodicity search.  Time transform of the dedispersed windows of nb DM
 // trials (dms[j] indexes delays) into out[(2 j + q) nrows + row][kk].

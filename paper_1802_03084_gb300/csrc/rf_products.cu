@@ -12,6 +12,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "rf_engine.h"
 
 namespace rf {
@@ -147,33 +149,106 @@ __device__ double block_sum(double v, double* sh) {
   return r;
 }
 
-// Population moments of all pixels of one image per block.
-// out[k] = {mean, std, skew, excess kurtosis}.
-__global__ void __launch_bounds__(kMomThreads) k_image_moments(const float* __restrict__ images, size_t npx,
-                                                               double* __restrict__ out) {
+// Population moments of all pixels of each image, in two passes over slices
+// of the image so that every SM takes part: block (slice, image) sums its
+// pixels (FP32 over 32 pixels per thread step, FP64 above), then around the
+// image mean (combined from the slice sums in a fixed order) the sums of d^2,
+// d^3 and d^4, d = pixel - mean, in the same way; a warp per image combines
+// the slices in a fixed order.  out[k] = {mean, std, skew, excess kurtosis}.
+__device__ __forceinline__ void slice_range(size_t npx, int nslices, int s, size_t* b, size_t* e) {
+  const size_t per = (npx + nslices - 1) / nslices;
+  *b = min(npx, (size_t)s * per);
+  *e = min(npx, *b + per);
+}
+
+__global__ void __launch_bounds__(kMomThreads) k_moments_sum(const float* __restrict__ images, size_t npx,
+                                                             int nslices, double* __restrict__ part) {
   __shared__ double sh[kMomThreads];
-  const float* im = images + (size_t)blockIdx.x * npx;
-  double s = 0.0;
-  for (size_t i = threadIdx.x; i < npx; i += kMomThreads) s += (double)im[i];
-  const double mu = block_sum(s, sh) / (double)npx;
+  const int sl = blockIdx.x, k = blockIdx.y;
+  const float* im = images + (size_t)k * npx;
+  size_t b, e;
+  slice_range(npx, nslices, sl, &b, &e);
+  double acc = 0.0;
+  for (size_t i0 = b + threadIdx.x; i0 < e; i0 += (size_t)kMomThreads * 32) {
+    float f = 0.f;
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) {
+      const size_t i = i0 + (size_t)j * kMomThreads;
+      if (i < e) f += im[i];
+    }
+    acc += (double)f;
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[((size_t)k * nslices + sl) * 4] = acc;
+}
+
+__global__ void __launch_bounds__(kMomThreads) k_moments_central(const float* __restrict__ images, size_t npx,
+                                                                 int nslices, double* __restrict__ part) {
+  __shared__ double sh[kMomThreads];
+  const int sl = blockIdx.x, k = blockIdx.y;
+  const float* im = images + (size_t)k * npx;
+  double* pk = part + (size_t)k * nslices * 4;
+  double sum = 0.0;
+  for (int q = 0; q < nslices; ++q) sum += pk[(size_t)q * 4];
+  const float mu = (float)(sum / (double)npx);
+  size_t b, e;
+  slice_range(npx, nslices, sl, &b, &e);
   double m2 = 0.0, m3 = 0.0, m4 = 0.0;
-  for (size_t i = threadIdx.x; i < npx; i += kMomThreads) {
-    const double d = (double)im[i] - mu;
-    const double d2 = d * d;
-    m2 += d2;
-    m3 += d2 * d;
-    m4 += d2 * d2;
+  for (size_t i0 = b + threadIdx.x; i0 < e; i0 += (size_t)kMomThreads * 32) {
+    float f2 = 0.f, f3 = 0.f, f4 = 0.f;
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) {
+      const size_t i = i0 + (size_t)j * kMomThreads;
+      if (i < e) {
+        const float d = im[i] - mu;
+        const float d2 = d * d;
+        f2 += d2;
+        f3 = fmaf(d2, d, f3);
+        f4 = fmaf(d2, d2, f4);
+      }
+    }
+    m2 += (double)f2;
+    m3 += (double)f3;
+    m4 += (double)f4;
   }
-  m2 = block_sum(m2, sh) / (double)npx;
-  m3 = block_sum(m3, sh) / (double)npx;
-  m4 = block_sum(m4, sh) / (double)npx;
+  m2 = block_sum(m2, sh);
+  m3 = block_sum(m3, sh);
+  m4 = block_sum(m4, sh);
   if (threadIdx.x == 0) {
-    double* o = out + (size_t)blockIdx.x * 4;
-    o[0] = mu;
-    o[1] = sqrt(m2);
-    o[2] = m2 > 0 ? m3 / (m2 * sqrt(m2)) : 0.0;
-    o[3] = m2 > 0 ? m4 / (m2 * m2) - 3.0 : 0.0;
+    double* o = pk + (size_t)sl * 4;
+    o[1] = m2;
+    o[2] = m3;
+    o[3] = m4;
   }
+}
+
+__global__ void k_moments_final(const double* __restrict__ part, size_t npx, int nslices, int n,
+                                double* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double* pk = part + (size_t)k * nslices * 4;
+  double sum = 0.0, m2 = 0.0, m3 = 0.0, m4 = 0.0;
+  for (int q = 0; q < nslices; ++q) {
+    sum += pk[(size_t)q * 4];
+    m2 += pk[(size_t)q * 4 + 1];
+    m3 += pk[(size_t)q * 4 + 2];
+    m4 += pk[(size_t)q * 4 + 3];
+  }
+  const double np = (double)npx;
+  const double mean = sum / np;
+  // the central sums were taken about the FP32-rounded mean mu_f; move them to
+  // the mean itself (e = mean - mu_f, central moments about mean from those
+  // about mu_f)
+  const double e = mean - (double)(float)mean;
+  const double a2 = m2 / np, a3 = m3 / np, a4 = m4 / np;
+  const double c2 = a2 - e * e;
+  const double c3 = a3 - 3.0 * e * a2 + 2.0 * e * e * e;
+  const double c4 = a4 - 4.0 * e * a3 + 6.0 * e * e * a2 - 3.0 * e * e * e * e;
+  double* o = out + (size_t)k * 4;
+  o[0] = mean;
+  o[1] = c2 > 0 ? sqrt(c2) : 0.0;
+  o[2] = c2 > 0 ? c3 / (c2 * sqrt(c2)) : 0.0;
+  o[3] = c2 > 0 ? c4 / (c2 * c2) - 3.0 : 0.0;
 }
 
 }  // namespace
@@ -194,9 +269,23 @@ cudaError_t launch_cand_spectrum(const SegmentGeom& g, const DevTables& tb, cons
   return cudaGetLastError();
 }
 
-cudaError_t launch_image_moments(const float* images, int n, size_t npx, double* out, cudaStream_t st) {
+int image_moment_slices(int n, size_t npx) {
+  // about four blocks per SM in all, slices of at least 64K pixels
+  const long want = (4L * 152 + n - 1) / std::max(n, 1);
+  const long most = (long)std::max<size_t>(1, npx / 65536);
+  return (int)std::max(1L, std::min(std::min(want, most), 256L));
+}
+
+cudaError_t launch_image_moments(const float* images, int n, size_t npx, int nslices, double* part, double* out,
+                                 cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_image_moments<<<n, kMomThreads, 0, st>>>(images, npx, out);
+  const dim3 grid(nslices, n);
+  k_moments_sum<<<grid, kMomThreads, 0, st>>>(images, npx, nslices, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_moments_central<<<grid, kMomThreads, 0, st>>>(images, npx, nslices, part);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_moments_final<<<(n + 31) / 32, 32, 0, st>>>(part, npx, nslices, n, out);
   return cudaGetLastError();
 }
 
