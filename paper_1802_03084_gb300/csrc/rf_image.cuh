@@ -557,19 +557,40 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     const int pj = item / nrb;
     const int y = (item - pj * nrb) * K::XB + xf;
     float2 v[K::E];
+    if constexpr (K::E == 32 && K::T % K::CH == 0) {
+      // as in the search's row pass: u = t + r T (or N - t - r T) has the
+      // swizzle term of t (N - t), and the loads are predicated, not branched
+      const int rd_end = ncol > t ? (ncol - t + K::T - 1) / K::T : 0;
+      const int rm_beg = (N - ncol - t) / K::T + 1;
+      const float4* pd = tile + t * K::CH + (xf ^ (t & (K::CH - 1)));
+      const float4* pm = tile + (size_t)(N - t) * K::CH + (xf ^ ((N - t) & (K::CH - 1)));
 #pragma unroll
-    for (int r = 0; r < K::E; ++r) {
-      const int u = t + r * K::T;
-      float2 z = make_float2(0.f, 0.f);
-      if (u < ncol) {
-        const float4 ab = tile[u * K::CH + (xf ^ (u & (K::CH - 1)))];
-        z = (u == 0) ? make_float2(ab.x, ab.z) : make_float2(ab.x - ab.w, ab.y + ab.z);
-      } else if (N - u < ncol) {
-        const int uu = N - u;
-        const float4 ab = tile[uu * K::CH + (xf ^ (uu & (K::CH - 1)))];
-        z = make_float2(ab.x + ab.w, ab.z - ab.y);
+      for (int r = 0; r < 16; ++r) {
+        float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < rd_end) ab = pd[r * K::T * K::CH];
+        v[r] = (r == 0 && t == 0) ? make_float2(ab.x, ab.z) : make_float2(ab.x - ab.w, ab.y + ab.z);
       }
-      v[r] = z;
+#pragma unroll
+      for (int r = 16; r < 32; ++r) {
+        float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r >= rm_beg) ab = pm[-r * K::T * K::CH];
+        v[r] = make_float2(ab.x + ab.w, ab.z - ab.y);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < K::E; ++r) {
+        const int u = t + r * K::T;
+        float2 z = make_float2(0.f, 0.f);
+        if (u < ncol) {
+          const float4 ab = tile[u * K::CH + (xf ^ (u & (K::CH - 1)))];
+          z = (u == 0) ? make_float2(ab.x, ab.z) : make_float2(ab.x - ab.w, ab.y + ab.z);
+        } else if (N - u < ncol) {
+          const int uu = N - u;
+          const float4 ab = tile[uu * K::CH + (xf ^ (uu & (K::CH - 1)))];
+          z = make_float2(ab.x + ab.w, ab.z - ab.y);
+        }
+        v[r] = z;
+      }
     }
     __syncthreads();  // tile consumed: prefetch the next item
     if (item + (int)gridDim.x < nitems) prefetch(item + gridDim.x);

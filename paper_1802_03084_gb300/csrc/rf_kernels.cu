@@ -100,7 +100,8 @@ cudaError_t launch_ingest(const float2* vis, int nt, int t_begin, int npol, cons
 // Mean-visibility subtraction over the segment (Sec. 3.1): every row of S
 // (one baseline and channel) loses its mean over t < nint, which removes
 // sources that are constant over the segment.  One warp per row; lane l sums
-// t = l, l + 32, ... in FP64 and a fixed xor-shuffle tree combines the lanes,
+// t = l, l + 32, ... (FP32 over runs of 32 samples, FP64 above) and a fixed
+// xor-shuffle tree combines the lanes in FP64,
 // so the mean does not depend on scheduling.  The difference is formed in
 // FP32 and stored back in the storage precision.
 template <bool FP16>
@@ -109,15 +110,26 @@ __global__ void __launch_bounds__(256) k_mean_subtract(void* __restrict__ S, int
   const int lane = threadIdx.x & 31;
   if (row >= nrows) return;
   const size_t base = (size_t)row * nint_pad;
+  // FP32 over each lane's runs of 32 samples, FP64 above (the FP64 pipe is
+  // narrow on this part)
   double sr = 0.0, si = 0.0;
-  for (int t = lane; t < nint; t += 32) {
-    float2 v;
-    if (FP16)
-      v = __half22float2(reinterpret_cast<const __half2*>(S)[base + t]);
-    else
-      v = reinterpret_cast<const float2*>(S)[base + t];
-    sr += (double)v.x;
-    si += (double)v.y;
+  for (int t0 = lane; t0 < nint; t0 += 32 * 32) {
+    float fr = 0.f, fi = 0.f;
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) {
+      const int t = t0 + 32 * j;
+      if (t < nint) {
+        float2 v;
+        if (FP16)
+          v = __half22float2(reinterpret_cast<const __half2*>(S)[base + t]);
+        else
+          v = reinterpret_cast<const float2*>(S)[base + t];
+        fr += v.x;
+        fi += v.y;
+      }
+    }
+    sr += (double)fr;
+    si += (double)fi;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
