@@ -206,7 +206,8 @@ __device__ __forceinline__ void max_merge(float& m, int& i, float m2, int i2) {
 // With tma_boxes > 0 (N >= 1024 only) thread 0 fetches each item's tile with
 // tma_boxes tensor copies of tma_rows u rows from `tmap` ([slot][u][2N
 // floats]) and every thread waits on an mbarrier; a wait that gives up sets
-// *err and the block returns.  Otherwise the threads copy it with cp.async.
+// *err, waits once more (bounded) for the copy in flight, and the block
+// returns.  Otherwise the threads copy it with cp.async.
 // CLIP (the one-pass clipped noise): clip[slot] = {mean0, r} in raw pixel
 // units, and each row pair also sums d = J - mean0 and d^2 over its pixels J
 // with |d| <= r and counts them (FP32 per thread and across the transform's
@@ -268,11 +269,18 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
   for (; item < nitems; item += gridDim.x) {
     if (use_tma) {
       const bool ok = mbar_wait(&tbar, phase);
-      phase ^= 1u;
       if (__syncthreads_or(!ok)) {
-        if (tid == 0) atomicExch(err, 1);
+        // the item's tile copy has not completed: give it one more bounded
+        // wait, so that it does not land in shared memory after the block
+        // has left, then report the timeout and leave
+        if (tid == 0) {
+          atomicExch(err, 1);
+          mbar_wait(&tbar, phase);
+        }
+        __syncthreads();
         return;
       }
+      phase ^= 1u;
     } else {
       cp_async_wait_all();
       __syncthreads();
