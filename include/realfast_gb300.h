@@ -264,6 +264,12 @@ rf_status rf_plan_set_form(struct rf_plan* plan, int32_t form);
  *                      launches once per segment length as a CUDA graph and
  *                      replays it; 0: direct launches. */
 #define RF_TUNE_GRAPHS 2
+/* RF_TUNE_WIDE_INDEX   0 (default): gridding addresses a resampled series
+ *                      with 32-bit sample offsets whenever every index fits,
+ *                      64-bit ones otherwise; 1: always 64-bit.  Both give
+ *                      the same images; the knob lets a test run the 64-bit
+ *                      variant on a small plan. */
+#define RF_TUNE_WIDE_INDEX 3
 rf_status rf_plan_set_tuning(struct rf_plan* plan, int32_t key, int64_t value);
 rf_status rf_plan_get_tuning(const struct rf_plan* plan, int32_t key, int64_t* value);
 

@@ -29,7 +29,7 @@ __all__ = [
     "Stream", "RfStreamInfo", "RfCandidateFeatures", "FEATURES_DTYPE", "rf_candidate_products",
     "RfPeriodicCandidate", "PERIODIC_DTYPE", "rf_periodicity_search", "rf_selftest_bounded_wait",
     "Plan", "CANDIDATE_DTYPE", "STAT_DTYPE", "declared_symbols",
-    "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_MEAN_SUBTRACT", "RF_NOISE_CLIPPED", "RF_STREAM_KEEP_STATS", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
+    "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_MEAN_SUBTRACT", "RF_NOISE_CLIPPED", "RF_TUNE_WIDE_INDEX", "RF_STREAM_KEEP_STATS", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
 ]
 
 RF_OK = 0
@@ -56,6 +56,7 @@ RF_FORM_PLAIN = 1
 RF_NOALLOC_MAX_NPIX = 1024
 RF_TUNE_WAVE_IMAGES = 1
 RF_TUNE_GRAPHS = 2
+RF_TUNE_WIDE_INDEX = 3
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
                       "realfast_gb300.h")
@@ -640,6 +641,10 @@ class Plan:
 
     def set_graphs(self, enable: bool):
         rf_plan_set_tuning(self.handle, RF_TUNE_GRAPHS, 1 if enable else 0)
+
+    def set_wide_index(self, enable: bool):
+        """Gridding with 64-bit sample offsets even where 32-bit ones fit."""
+        rf_plan_set_tuning(self.handle, RF_TUNE_WIDE_INDEX, 1 if enable else 0)
 
     def autotune(self, vis, nint=None, stream=None, cache_path=None, key_extra=""):
         """Apply a cached tuning for this shape, or run the autotuner and cache it.

@@ -255,6 +255,7 @@ struct rf_plan {
 
   // CUDA graph of the batched wave loop for the current image list
   bool use_graphs = true;
+  bool wide_index = false;      // RF_TUNE_WIDE_INDEX: 64-bit gridding sample offsets always
   bool graph_pending = false;  // a replay with profiling events awaits collection
   struct GraphCache {
     bool valid = false;
@@ -829,7 +830,7 @@ SegmentGeom geom(const rf_plan* p, int nint) {
     uint64_t pitch = 0;
     for (int k = 0; k < (int)p->sdt_lp.size(); ++k)
       pitch = std::max<uint64_t>(pitch, (uint64_t)p->dt[k] * p->sdt_lp[k]);
-    g.idx32 = (uint64_t)p->nbl * p->nchan * pitch < (1ull << 32);
+    g.idx32 = !p->wide_index && (uint64_t)p->nbl * p->nchan * pitch < (1ull << 32);
   }
   g.fp16 = (p->flags & RF_STORE_FP16) != 0;
   return g;
@@ -1725,6 +1726,15 @@ rf_status rf_plan_set_tuning(rf_plan* p, int32_t key, int64_t value) {
     p->drop_graph();
     return RF_OK;
   }
+  if (key == RF_TUNE_WIDE_INDEX) {
+    if (value != 0 && value != 1) return fail(RF_ERR_INVALID_ARG, "RF_TUNE_WIDE_INDEX takes 0 or 1");
+    BusyGuard bg(&p->busy);
+    if (!bg.owned) return fail(RF_ERR_BUSY, "plan is in use by another call");
+    DeviceGuard dg(p->device);
+    p->wide_index = value != 0;
+    p->drop_graph();  // captured launches carry the variant
+    return RF_OK;
+  }
   if (key != RF_TUNE_WAVE_IMAGES) return fail(RF_ERR_INVALID_ARG, "unknown tuning key %d", key);
   if (p->host_only) return fail(RF_ERR_INVALID_ARG, "plan was created with RF_HOST_ONLY");
   if (value < p->shape.images_per_group || value > 32768)
@@ -1834,6 +1844,10 @@ rf_status rf_plan_get_tuning(const rf_plan* p, int32_t key, int64_t* value) {
   if (!p || !value) return fail(RF_ERR_INVALID_ARG, "NULL argument");
   if (key == RF_TUNE_GRAPHS) {
     *value = p->use_graphs ? 1 : 0;
+    return RF_OK;
+  }
+  if (key == RF_TUNE_WIDE_INDEX) {
+    *value = p->wide_index ? 1 : 0;
     return RF_OK;
   }
   if (key != RF_TUNE_WAVE_IMAGES) return fail(RF_ERR_INVALID_ARG, "unknown tuning key %d", key);

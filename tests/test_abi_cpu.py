@@ -202,3 +202,14 @@ def test_plan_whose_column_overflows_shared_memory_is_rejected(L):
     kw["freq_hz"] = np.linspace(1.0e9, 3.0e9, 64)
     with rf.Plan(**kw) as p:
         assert p.info().n_cells > 0
+
+
+def test_wide_index_tuning_key(L):
+    kw = _desc_kwargs(synth.config("tiny"))
+    with rf.Plan(**kw) as p:
+        assert rf.rf_plan_get_tuning(p.handle, rf.RF_TUNE_WIDE_INDEX) == 0
+        p.set_wide_index(True)
+        assert rf.rf_plan_get_tuning(p.handle, rf.RF_TUNE_WIDE_INDEX) == 1
+        with pytest.raises(rf.RfError) as e:
+            rf.rf_plan_set_tuning(p.handle, rf.RF_TUNE_WIDE_INDEX, 2)
+        assert e.value.status == rf.RF_ERR_INVALID_ARG

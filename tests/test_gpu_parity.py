@@ -259,3 +259,21 @@ def test_maximum_image_size():
         compare_candidates(gc, oc, spec.threshold, ost)
         g = gp.render(seg["vis"], [(0, 0, 1)])
         assert rel_rms(g[0], oim[(0, 0, 1)]) < IMG_RMS_FP32
+
+
+@pytest.mark.parametrize("edge,store", [("partial", "fp32"), ("full", "fp16")])
+def test_wide_sample_offsets_give_the_same_images(tiny, edge, store):
+    # the gridding kernel's 64-bit offset variant (for series of 2^32 samples
+    # and more) on a small plan: bit-identical to the 32-bit one
+    spec, seg, _, _, _, _ = tiny
+    s2 = synth.config("tiny")
+    s2.edge = edge
+    s2.store = store
+    gp, _ = plans_for(s2, seg)
+    with gp:
+        gp.set_graphs(False)
+        c0, s0 = gp.search_stats(seg["vis"])
+        gp.set_wide_index(True)
+        assert rf.rf_plan_get_tuning(gp.handle, rf.RF_TUNE_WIDE_INDEX) == 1
+        c1, s1 = gp.search_stats(seg["vis"])
+        assert np.array_equal(s0, s1) and np.array_equal(c0, c1)
