@@ -972,7 +972,8 @@ rf_status alloc_plain(rf_plan* p) {
   if (p->plain.cap > 0) return RF_OK;
   const size_t N = p->npix;
   const size_t per = (size_t)p->nbl * p->nchan * sizeof(float2) + N * (N / 2 + 1) * sizeof(float2) +
-                     (N / 2) * N * sizeof(float2) + N * N * sizeof(float) + (N / 2) * sizeof(StatPartial);
+                     (N / 2) * N * sizeof(float2) + N * N * sizeof(float) +
+                     (size_t)p->shape.partials_per_image * sizeof(StatPartial);
   const int cap = (int)std::max<size_t>(1, std::min<size_t>(kPlainBudgetBytes / per, 4096));
   rf_status s;
   rf::PlainBuffers& b = p->plain;
@@ -980,7 +981,7 @@ rf_status alloc_plain(rf_plan* p) {
   if ((s = p->dalloc(&b.grid, (size_t)cap * N * (N / 2 + 1))) != RF_OK) return s;
   if ((s = p->dalloc(&b.T, (size_t)cap * (N / 2) * N)) != RF_OK) return s;
   if ((s = p->dalloc(&b.images, (size_t)cap * N * N)) != RF_OK) return s;
-  if ((s = p->dalloc(&b.partials, (size_t)cap * (N / 2))) != RF_OK) return s;
+  if ((s = p->dalloc(&b.partials, (size_t)cap * p->shape.partials_per_image)) != RF_OK) return s;
   int4* d_ent = nullptr;
   if ((s = p->dalloc(&d_ent, p->plain_ent.size())) != RF_OK) return s;
   if (!p->plain_ent.empty())

@@ -212,7 +212,7 @@ struct PlainBuffers {
   float2* grid;           // [cap][N][N/2 + 1] dense half planes
   float2* T;              // [cap][N/2][N] column-FFT output
   float* images;          // [cap][N][N]
-  StatPartial* partials;  // [cap][N/2] (row pass output, unused)
+  StatPartial* partials;  // [cap][partials per image] (row pass output, unused)
   const int4* ent;        // [nent] {bc, col, row, flags}
   int nent;
   int cap;
@@ -235,7 +235,7 @@ struct ImageKernelShape {
   int smem_a;
   int warps_per_col;      // WPC: warps sharing one column's gridding (pass A)
   int rows_per_cta;       // RB (pass B)
-  int partials_per_image; // row-pair partials written by pass B (N / 2)
+  int partials_per_image; // partials written by pass B per image: N/2 row pairs x warps per transform
   int threads_b;
   int smem_b;
   int smem_a_per_cell;  // column pass: shared bytes per occupied cell of the largest column

@@ -52,6 +52,7 @@ struct ImgCfg {
   static constexpr int XB = cmin(256 / T, N / 2);
   static constexpr int THREADS_B = T * XB;
   static constexpr int RB = 2 * XB;
+  static constexpr int PARTIALS = (N / 2) * (T > 32 ? T / 32 : 1);  // row-pass partials per image
   static constexpr int CH = XB;                                  // 16-byte chunks per tile row
   static constexpr int STRIDE = fft_stride<N>();
   static constexpr int SMEM_B_FIXED = XB * STRIDE * 8;
@@ -199,10 +200,11 @@ __device__ __forceinline__ void max_merge(float& m, int& i, float m2, int i2) {
 // tile T[slot][u][y0 .. y0+RB) of the next item is copied to shared memory
 // with cp.async (16-byte chunks, XOR-swizzled per row so the strided reads
 // are free of bank conflicts) while the current item is transformed.  Each
-// row pair writes one StatPartial: pixel sum and sum of squares of its two
-// rows (FP32 per thread and pairwise across the transform's threads; the
-// N/2 partials of an image are added in FP64 by the finalisation) and the
-// max pixel with its lowest index.
+// warp of a row pair's transform writes one StatPartial (one per row pair
+// when the transform fits a warp, T/32 of them when it spans several): the
+// max pixel of its part of the two rows with its lowest index, and under
+// CLIP the kept-pixel sums (FP32 per thread and across the warp's lanes; the
+// finalisation combines an image's partials in FP64).
 // With tma_boxes > 0 (N >= 1024 only) thread 0 fetches each item's tile with
 // tma_boxes tensor copies of tma_rows u rows from `tmap` ([slot][u][2N
 // floats]) and every thread waits on an mbarrier; a wait that gives up sets
@@ -219,20 +221,13 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
                    float* __restrict__ images, const __grid_constant__ CUtensorMap tmap, int tma_boxes,
                    int tma_rows, int* __restrict__ err, const float2* __restrict__ clip) {
   using K = ImgCfg<N>;
-  constexpr int NWB = (K::THREADS_B + 31) / 32;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* fbuf = reinterpret_cast<float2*>(smraw);  // [XB][STRIDE]
   unsigned char* tb0 = smraw + K::XB * K::STRIDE * 8;
   if constexpr (K::TILE_TMA) tb0 += (1024u - (smem_u32(tb0) & 1023u)) & 1023u;  // swizzle atom alignment
   float4* tile = reinterpret_cast<float4*>(tb0);    // [rows][CH]
-  __shared__ float w_max[32];
-  __shared__ int w_idx[32];
-  __shared__ float w_s1[CLIP ? 32 : 1], w_s2[CLIP ? 32 : 1];
-  __shared__ int w_cn[CLIP ? 32 : 1];
   __shared__ __align__(8) unsigned long long tbar;
   const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const int wid = tid >> 5;
   const int ncol = g.ncol;
   constexpr int nrb = N / K::RB;
   const int nitems = nimg * nrb;
@@ -428,48 +423,10 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
         cn += __shfl_xor_sync(MASK, cn, off);
       }
     }
-    if (K::T > 32) {
-      // wide transforms: combine the warps of one transform in shared memory
-      constexpr int WPT = K::T / 32;
-      const int wi = t >> 5;
-      if (lane == 0) {
-        w_max[wid] = wmax;
-        w_idx[wid] = best;
-        if constexpr (CLIP) {
-          w_s1[wid] = s1;
-          w_s2[wid] = s2;
-          w_cn[wid] = cn;
-        }
-      }
-      fft_sync<K::T>(xf);
-      if (t == 0) {
-        const int w0 = wid - wi;
-        float mx = -FLT_MAX;
-        int mi = INT_MAX;
-        for (int w = 0; w < WPT; ++w) max_merge(mx, mi, w_max[w0 + w], w_idx[w0 + w]);
-        StatPartial sp;
-        sp.sum = 0.0;
-        sp.sumsq = 0.0;
-        sp.kept = 0;
-        if constexpr (CLIP) {
-          float a = 0.f, q = 0.f;
-          int n = 0;
-          for (int w = 0; w < WPT; ++w) {
-            a += w_s1[w0 + w];
-            q += w_s2[w0 + w];
-            n += w_cn[w0 + w];
-          }
-          sp.sum = a;
-          sp.sumsq = q;
-          sp.kept = n;
-        }
-        sp.max = mx;
-        sp.idx = mi;
-        sp.pad = 0;
-        partials[(size_t)slot * (N / 2) + (y0 >> 1) + xf] = sp;
-      }
-      fft_sync<K::T>(xf);
-    } else if (t == 0) {
+    // one partial per warp of the transform (WPT of them when a transform
+    // spans several warps; the finalisation combines them): no barrier
+    if ((t & 31) == 0) {
+      constexpr int WPT = K::T > 32 ? K::T / 32 : 1;
       StatPartial sp;
       sp.sum = s1;
       sp.sumsq = s2;
@@ -477,7 +434,7 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
       sp.max = wmax;
       sp.idx = best;
       sp.pad = 0;
-      partials[(size_t)slot * (N / 2) + (y0 >> 1) + xf] = sp;
+      partials[(size_t)slot * K::PARTIALS + ((y0 >> 1) + xf) * WPT + (t >> 5)] = sp;
     }
   }
 }
@@ -759,7 +716,7 @@ void fill_shape(ImageKernelShape* o) {
   o->smem_a = K::SMEM_A_FIXED;
   o->warps_per_col = 0;
   o->rows_per_cta = K::RB;
-  o->partials_per_image = N / 2;
+  o->partials_per_image = K::PARTIALS;
   o->threads_b = K::THREADS_B;
   o->smem_b = K::SMEM_B_FIXED;
   o->smem_a_per_cell = K::PART_IMAGES * 8 + 4;
