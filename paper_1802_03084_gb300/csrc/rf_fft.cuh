@@ -77,7 +77,6 @@ __device__ __forceinline__ float2 c_sub_iu(float2 t, float2 u) {
   return f2_fma(make_float2(u.y, u.x), make_float2(1.f, -1.f), t);
 }
 __device__ __forceinline__ float2 cmul_i(float2 a) { return make_float2(-a.y, a.x); }  // i * a
-__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 
 // cos and sin of 2 pi k / 32, k = 1..7 (the others follow by symmetry).
 #define RF_C32_1 0.98078528040323044913f

@@ -75,20 +75,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 
-template <bool FP16>
-__device__ __forceinline__ float2 load_sample(const void* __restrict__ S, size_t i);
-
-template <>
-__device__ __forceinline__ float2 load_sample<false>(const void* __restrict__ S, size_t i) {
-  return __ldg(reinterpret_cast<const float2*>(S) + i);
-}
-
-template <>
-__device__ __forceinline__ float2 load_sample<true>(const void* __restrict__ S, size_t i) {
-  const __half2 h = __ldg(reinterpret_cast<const __half2*>(S) + i);
-  return __half22float2(h);
-}
-
 // Pass A2: the column FFTs of one group (up to 32 consecutive t' of a
 // trial) and one half-plane column u.  The column's cell sums for the
 // group's images (cellbuf row per cell, 32 images) are copied to shared
