@@ -298,10 +298,10 @@ TRAFFIC_KERNELS = (("k_grid_cells", "grid_cells"), ("k_colfft", "grid_colfft"), 
 _BYTE_UNITS = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "tbyte": 1e12}
 
 
-def write_traffic(raw_csv, images_per_launch, command, workload):
-    """profiles/traffic.json from an ncu raw-page CSV (header row, unit row,
-    one row per captured launch): DRAM read + write bytes per launch of each
-    imaging kernel, averaged over its captured launches, and per image."""
+def write_traffic(raw_csv, images_per_launch, command, workload, path=None):
+    """profiles/traffic.json (or `path`) from an ncu raw-page CSV (header row,
+    unit row, one row per captured launch): DRAM read + write bytes per launch
+    of each imaging kernel, averaged over its captured launches, and per image."""
     import csv
     with open(raw_csv, newline="") as f:
         rows = [r for r in csv.reader(f) if r]
@@ -322,7 +322,7 @@ def write_traffic(raw_csv, images_per_launch, command, workload):
             out[key] = {"dram_bytes_per_launch": b, "images_per_launch": images_per_launch,
                         "dram_bytes_per_image": b / images_per_launch, "launches_captured": len(per)}
     doc = {"source_hash": source_hash(), "workload": workload, "command": command, "kernels": out}
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = path or os.path.join(ROOT, "profiles", "traffic.json")
     with open(path, "w") as f:
         json.dump(doc, f, indent=1)
         f.write("\n")
