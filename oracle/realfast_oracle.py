@@ -27,6 +27,13 @@ silent are listed with each function; in short:
   iv (y - N/2)) / N)),  W = sum_{on-grid b,c} n_c (samples summed).
 * stats  mu = mean(I), sigma = population std of all N^2 pixels, peak = max I
   (lowest y N + x on ties), snr = peak / sigma, candidate iff snr >= threshold.
+  Optionally (clipped noise) mu and sigma are recomputed once over the pixels
+  within 5 sigma of mu.
+
+Around the search (their docstrings give the readings): mean-visibility
+subtraction over the segment, a stream of segments overlapping by the longest
+sweep, candidate spectra and moments, and the periodicity search (a time
+Fourier transform of dedispersed windows, each frequency imaged).
 """
 
 from __future__ import annotations
