@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--serving-slots", type=int, default=3)
     ap.add_argument("--serving-load", type=float, default=1.0, help="offered load in units of real time")
     ap.add_argument("--next-rows", action="store_true",
-                    help="time the periodicity search, stream, mean subtraction and candidate products")
+                    help="time the periodicity search, stream, mean subtraction, clipped noise and candidate products")
     ap.add_argument("--host-input", action="store_true",
                     help="time the search from pinned host input only (small device footprint for profilers)")
     ap.add_argument("--nchan", type=int, default=0,
@@ -516,11 +516,21 @@ def run_next_rows(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps, out
 
+    def kernel_ms(p, name):
+        """CUDA-event time of one kind of launch in one profiled search (graph bypassed)."""
+        p.set_profiling(True)
+        p.search(vis, nint)
+        torch.cuda.synchronize()
+        launches, total = p.profile().get(name, (0, 0.0))
+        p.set_profiling(False)
+        return total
+
     line = {"metric": "rows around the search", "config": {"workload": workload_name(spec)}, "n_gpus": 1}
     plan = rf.Plan.from_spec(spec, seg["ant_uvw"], seg["freq_hz"], max_nint=nint)
     n_images = plan.count_images(nint)
     ms, cands = timed(lambda: plan.search(vis, nint), 3)
     line["search_ms"] = ms
+    line["rowfft_stats_kernel_ms"] = kernel_ms(plan, "rowfft_stats")
     # periodicity: L = 64, k = 1 .. 32 over every DM trial whose window fits
     L, kmin, kmax = 64, 1, 32
     pms, (pc, pst) = timed(lambda: plan.periodicity_search(vis, L, kmin, kmax, 7.0, nint, with_stats=True), 3)
@@ -537,7 +547,8 @@ def run_next_rows(args):
     spec_m.mean_subtract = True
     plan_m = rf.Plan.from_spec(spec_m, seg["ant_uvw"], seg["freq_hz"], max_nint=nint)
     mms, _ = timed(lambda: plan_m.search(vis, nint), 3)
-    line["mean_subtract"] = {"ms": mms, "overhead_ms": mms - ms}
+    line["mean_subtract"] = {"ms": mms, "overhead_ms": mms - ms,
+                             "kernel_ms": kernel_ms(plan_m, "mean_subtract")}
     plan_m.close()
     # clipped noise (one 5-sigma clipping pass) on the same search
     spec_c = synth.config(args.config)
@@ -545,7 +556,9 @@ def run_next_rows(args):
     plan_c = rf.Plan.from_spec(spec_c, seg["ant_uvw"], seg["freq_hz"], max_nint=nint)
     cms_, cc = timed(lambda: plan_c.search(vis, nint), 3)
     line["noise_clipped"] = {"ms": cms_, "overhead_ms": cms_ - ms, "candidates": int(len(cc)),
-                             "candidates_plain_noise": int(len(cands))}
+                             "candidates_plain_noise": int(len(cands)),
+                             "clip_window_kernel_ms": kernel_ms(plan_c, "clip_window"),
+                             "rowfft_stats_kernel_ms": kernel_ms(plan_c, "rowfft_stats")}
     plan_c.close()
     # stream: segments of nint integrations overlapping by the longest sweep,
     # fed the same segment repeatedly in chunks of 128 integrations
