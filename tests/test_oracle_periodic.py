@@ -88,3 +88,62 @@ def test_injected_pulse_train_is_found_at_its_harmonics():
     hits = {(c["dm_idx"], c["k"]) for c in cands if (c["x"], c["y"]) == (12, 20)}
     assert (2, 4) in hits and (2, 8) in hits
     assert stats[(2, 4)].snr > stats[(2, 5)].snr
+
+
+def test_periodic_noise_of_a_hand_built_quadrature_pair():
+    # I_U: 1 everywhere but 5 at (x=2, y=1) and -3 at (x=0, y=3): mean 1,
+    # population variance (16 + 16) / 16 = 2.  I_Q: +-2 at four pixels, 0
+    # elsewhere: mean 0, variance 4 * 4 / 16 = 1.  The per-quadrature noise is
+    # sqrt((2 + 1) / 2) = sqrt(1.5); the power peaks at (2, 1) with
+    # 5^2 + 0^2 = 25, so the amplitude is 5.  (A max of the two variances
+    # would give sqrt(2), their sum sqrt(3), a mean square in place of the
+    # variance sqrt(2).)
+    IU = np.ones((4, 4))
+    IU[1, 2] = 5.0
+    IU[3, 0] = -3.0
+    IQ = np.zeros((4, 4))
+    IQ[0, 0], IQ[0, 1], IQ[2, 3], IQ[3, 3] = 2.0, -2.0, 2.0, -2.0
+    st = oracle.periodic_stats(IU, IQ)
+    assert (st.x, st.y) == (2, 1)
+    assert st.amplitude == 5.0
+    assert abs(st.sigma - np.sqrt(1.5)) < 1e-15
+    assert abs(st.snr - 5.0 / np.sqrt(1.5)) < 1e-14
+
+
+def test_periodic_noise_matches_the_closed_form_on_noise():
+    """Per-quadrature noise of a noise-only segment against its expectation.
+
+    Stokes I of one (b, c) sample is complex with independent real and
+    imaginary parts of variance 1/4 (each polarisation has E|n|^2 = 1, and
+    the two are averaged).  With U_k = (1/L) sum_t x_t cos(2 pi k t / L) and
+    sum_t cos^2 = L/2 for 1 <= k < L/2 (L at k = L/2, where the sine sum
+    vanishes), Re U_k and Im U_k have variance 1/(8L), and so do those of
+    Q_k; at k = L/2, U carries 1/(4L) and Q nothing.  A pixel of I_U is
+    (1/W) sum over the W on-grid pairs of Re(U e^{i phi}), whose variance is
+    W / (8 L W^2) = 1/(8 L W) (twice that for U at k = L/2, with I_Q = 0).
+    Either way (var I_U + var I_Q) / 2 has expectation 1/(8 L W), and the
+    population variance over the pixels estimates it (the mean term of the
+    (0, 0) cell is negligible).  The spread between (DM, k) cases comes from
+    the finite number of occupied cells (a few per cent at this size).
+    """
+    spec = synth.SegmentSpec(name="periodic-noise", nchan=16, f_lo_hz=1.0e9, bw_hz=1.0e9, nint=120,
+                             inttime_s=5e-3, npix=128, dm_list=np.array([0.0, 150.0]), dt_list=[1],
+                             threshold=7.0, seed=5)
+    seg = synth.make_segment(spec)
+    op = oracle.OraclePlan(seg["ant_uvw"], seg["freq_hz"], spec.inttime_s, spec.npix, spec.cell_rad,
+                           spec.dm_list, spec.dt_list, spec.threshold, edge="full", npol=spec.npol)
+    S = op.stokes(seg["vis"])
+    W = float(op.ongrid.sum())
+    assert W > 5000
+    ratios = []
+    for L in (16, 32):
+        expect = 1.0 / (8.0 * L * W)
+        ks = list(range(1, L // 2 + 1))
+        for d in (0, 1):
+            U, Q = oracle.periodic_series_transform(op, S, d, L, ks)
+            for j in range(len(ks)):
+                IU, IQ, _ = oracle.periodic_image(op, U[j], Q[j])
+                ratios.append(oracle.periodic_stats(IU, IQ).sigma ** 2 / expect)
+    ratios = np.asarray(ratios)
+    assert np.all(np.abs(ratios - 1.0) < 0.10), ratios
+    assert abs(ratios.mean() - 1.0) < 0.03, ratios.mean()
