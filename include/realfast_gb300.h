@@ -344,8 +344,12 @@ rf_status rf_plan_get_profile(const struct rf_plan* plan, rf_kernel_profile* out
  *             device array sized for RF_NOALLOC_MAX_NPIX.
  * weight      W > 0, the normalisation of the image (samples gridded).
  * stream      cudaStream_t (NULL = default stream); the call is asynchronous.
- * stat        device pointer to one rf_image_stat; dm_idx, dt_idx and t_idx
- *             are written as 0.
+ * stat        device pointer to one rf_image_stat (8-byte aligned); dm_idx,
+ *             dt_idx and t_idx are written as 0.
+ * Both pointers must be device memory of the current device: host memory
+ * (pageable or pinned) and memory of another GPU are rejected with
+ * RF_ERR_INVALID_ARG before anything is launched (checked with
+ * cudaPointerGetAttributes, which allocates nothing).
  * It runs on the current CUDA device and calls no cudaMalloc or cudaFree.
  * Its scratch (the column-FFT intermediate and row partials, about 4 MiB
  * for RF_NOALLOC_MAX_NPIX = 1024) is one static device array per GPU, held

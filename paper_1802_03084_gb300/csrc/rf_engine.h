@@ -244,6 +244,10 @@ struct ImageKernelShape {
 };
 bool image_kernel_shape(int npix, ImageKernelShape* out);
 
+// Streaming multiprocessors of the current device (cached per device: launch
+// shapes are sized from it, and another GPU of the process may differ).
+int sm_count();
+
 // Sets the thread-local message returned by rf_last_error().
 void set_last_error(const char* msg);
 

@@ -443,15 +443,6 @@ int max_dynamic_smem(Kernel kern) {
   return optin - (int)fa.sharedSizeBytes;
 }
 
-inline int sm_count() {
-  static int n = [] {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    return v > 0 ? v : 1;
-  }();
-  return n;
-}
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -610,7 +601,7 @@ cudaError_t run_rowfft_power(const SegmentGeom& g, const DevTables& tb, const fl
                              int npairs, StatPartial* partials, cudaStream_t st) {
   using K = ImgCfg<N>;
   const int smem = K::SMEM_B_FIXED + g.ncol * K::CH * 16;
-  static const int smem_max = max_dynamic_smem(k_rowfft_power<N>);
+  const int smem_max = max_dynamic_smem(k_rowfft_power<N>);
   if (smem > smem_max) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_rowfft_power<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   if (e != cudaSuccess) return e;
@@ -634,7 +625,7 @@ cudaError_t run_colfft(const SegmentGeom& g, const DevTables& tb, const Group* g
                        cudaStream_t st) {
   using K = ImgCfg<N>;
   const int smem = K::SMEM_A_FIXED + g.max_cells * (K::PART_IMAGES * 8 + 4);
-  static const int smem_max = max_dynamic_smem(k_colfft<N>);
+  const int smem_max = max_dynamic_smem(k_colfft<N>);
   if (smem > smem_max) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_colfft<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   if (e != cudaSuccess) return e;
@@ -663,7 +654,7 @@ cudaError_t run_rowfft_stats_k(const SegmentGeom& g, const DevTables& tb, const 
   using K = ImgCfg<N>;
   const int smem = K::SMEM_B_FIXED + (K::TILE_TMA ? 1024 : 0) + rowfft_tile_rows<N>(g.ncol) * K::CH * 16;
   auto kern = k_rowfft_stats<N, CLIP>;
-  static const int smem_max = max_dynamic_smem(kern);
+  const int smem_max = max_dynamic_smem(kern);
   if (smem > smem_max) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   if (e != cudaSuccess) return e;

@@ -7,6 +7,7 @@
 #include <limits.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <type_traits>
 
@@ -28,6 +29,24 @@ void fft_twiddle_table(int n, float2* out) {
       const double a = two_pi * (double)((k * r) % len) / (double)len;
       out[n + (r >> 1) * 64 + 2 * k + (r & 1)] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
+}
+
+int sm_count() {
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> cache[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return 1;
+  }
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+    cudaGetLastError();
+    return 1;
+  }
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
 }
 
 // ----------------------------------------------------------------- ingest --
@@ -203,7 +222,7 @@ __global__ void __launch_bounds__(256) k_resample(const void* __restrict__ S, vo
 cudaError_t launch_resample(const SegmentGeom& g, const void* S, void* Sdt, int dt, int lp, cudaStream_t st) {
   const int nrows = g.nbl * g.nchan;
   const size_t total = (size_t)nrows * dt * lp;
-  const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)sm_count() * 16);
   if (g.fp16)
     k_resample<true><<<blocks, 256, 0, st>>>(S, Sdt, nrows, g.nint, g.nint_pad, dt, lp);
   else

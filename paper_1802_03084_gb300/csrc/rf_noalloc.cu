@@ -32,7 +32,7 @@ constexpr int kMaxDevices = 64;
 // the statistics kernel, the per-column Parseval sums and the (0, 0) term.  Every byte a call reads is written by
 // the same call first, so nothing has to start at zero.
 constexpr size_t kTBytes = (size_t)kMaxN * (kMaxN / 2) * sizeof(float2);
-constexpr size_t kPartialBytes = 4096 * sizeof(StatPartial);
+constexpr size_t kPartialBytes = (size_t)ImgCfg<kMaxN>::PARTIALS * sizeof(StatPartial);
 constexpr size_t kColsqBytes = (kMaxN / 2 + 64) * sizeof(float);  // Parseval column sums + mean term
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kTBytes + kPartialBytes + kColsqBytes];
 
@@ -180,7 +180,15 @@ template <int N>
 cudaError_t run_noalloc(const float2* grid, double weight, const DeviceSetup& d, cudaStream_t st,
                         rf_image_stat* out) {
   using K = ImgCfg<N>;
-  static const cudaError_t attr =
+  // The column-FFT scratch holds one image of at most kMaxN, the partials
+  // area ImgCfg<kMaxN>::PARTIALS records; the Parseval sum of k_colfft_dense
+  // and the finalisation reduce within one warp per column, which holds
+  // while a transform fits one warp.
+  static_assert(N <= kMaxN, "image larger than the static scratch");
+  static_assert(K::PARTIALS <= ImgCfg<kMaxN>::PARTIALS, "partials area too small");
+  static_assert(K::T <= 32, "the Parseval reduction of k_colfft_dense spans one warp");
+  // set on every call: the attribute belongs to the current device's context
+  const cudaError_t attr =
       cudaFuncSetAttribute(k_colfft_dense<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM_A_FIXED);
   if (attr != cudaSuccess) return attr;
   float2* T = reinterpret_cast<float2*>(d.scratch);
@@ -199,11 +207,10 @@ cudaError_t run_noalloc(const float2* grid, double weight, const DeviceSetup& d,
   tb.twiddle = tw;
   e = launch_rowfft_stats(g, tb, T, 1, 0, nullptr, partials, nullptr, nullptr, nullptr, st);
   if (e != cudaSuccess) return e;
-  k_noalloc_finalize<<<1, 32, 0, st>>>(partials, N / 2, colsq, mean0, N, weight, out);
+  k_noalloc_finalize<<<1, 32, 0, st>>>(partials, K::PARTIALS, colsq, mean0, N, weight, out);
   return cudaGetLastError();
 }
 
-static_assert((size_t)kMaxN / 2 <= 4096, "partials area too small");
 
 }  // namespace
 }  // namespace rf
@@ -227,14 +234,30 @@ extern "C" rf_status rf_image_stats_noalloc(const void* half_plane, int32_t npix
     set_last_error("rf_image_stats_noalloc: weight must be > 0");
     return RF_ERR_INVALID_ARG;
   }
-  if ((uintptr_t)half_plane % 8 != 0) {
-    set_last_error("rf_image_stats_noalloc: half_plane must be 8-byte aligned");
+  if ((uintptr_t)half_plane % 8 != 0 || (uintptr_t)stat % alignof(rf_image_stat) != 0) {
+    snprintf(buf, sizeof(buf), "rf_image_stats_noalloc: half_plane must be 8-byte and stat %zu-byte aligned",
+             alignof(rf_image_stat));
+    set_last_error(buf);
     return RF_ERR_INVALID_ARG;
   }
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    set_last_error("rf_image_stats_noalloc: no current CUDA device");
+  // Both pointers must be device memory of the current device: a kernel
+  // given host memory would fault (or, where the device can reach host
+  // memory, silently read and write it).  The query allocates nothing.
+  int dev = -1;
+  const bool have_dev = cudaGetDevice(&dev) == cudaSuccess && dev >= 0;
+  for (const void* ptr : {half_plane, static_cast<const void*>(stat)}) {
+    cudaPointerAttributes attr;
+    const bool ok = have_dev && cudaPointerGetAttributes(&attr, ptr) == cudaSuccess &&
+                    (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) && attr.device == dev;
+    if (!ok) {
+      cudaGetLastError();
+      set_last_error("rf_image_stats_noalloc: half_plane and stat must be device memory of the current device");
+      return RF_ERR_INVALID_ARG;
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  if (dev >= kMaxDevices) {
+    set_last_error("rf_image_stats_noalloc: device ordinal beyond the set-up table");
     return RF_ERR_NO_DEVICE;
   }
   DeviceSetup* d = nullptr;

@@ -257,7 +257,8 @@ __global__ void __launch_bounds__(256) k_plain_stats(int npix, const float* __re
 template <int N>
 cudaError_t run_plain_colfft(const float2* grid, float2* T, const float2* tw, int nk, cudaStream_t st) {
   using K = ImgCfg<N>;
-  static const cudaError_t attr =
+  // set on every call: the attribute belongs to the current device's context
+  const cudaError_t attr =
       cudaFuncSetAttribute(k_plain_colfft<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM_A_FIXED);
   if (attr != cudaSuccess) return attr;
   dim3 grid_dim((N / 2 + K::XA - 1) / K::XA, nk);
@@ -271,14 +272,14 @@ cudaError_t launch_plain_chunk(const SegmentGeom& g, const DevTables& tb, const 
                                double threshold, DevCand* cands, int* ncand, int cand_cap, DevStat* stats,
                                cudaStream_t st, bool clip) {
   const size_t rows = (size_t)g.nbl * g.nchan;
-  const int blocks = (int)std::min<size_t>((rows * nk + 255) / 256, 152 * 32);
+  const int blocks = (int)std::min<size_t>((rows * nk + 255) / 256, (size_t)sm_count() * 32);
   k_plain_dedisperse<<<blocks, 256, 0, st>>>(g, tb, pb.S, d, s, t0, nk, pb.R);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int W = g.npix / 2 + 1;
   e = cudaMemsetAsync(pb.grid, 0, (size_t)nk * g.npix * W * sizeof(float2), st);
   if (e != cudaSuccess) return e;
-  const int gblocks = (int)std::min<size_t>(((size_t)pb.nent * nk + 255) / 256, 152 * 32);
+  const int gblocks = (int)std::min<size_t>(((size_t)pb.nent * nk + 255) / 256, (size_t)sm_count() * 32);
   k_plain_grid<<<gblocks, 256, 0, st>>>(g, pb.ent, pb.nent, pb.R, nk, pb.grid);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   switch (g.npix) {

@@ -271,7 +271,7 @@ cudaError_t launch_cand_spectrum(const SegmentGeom& g, const DevTables& tb, cons
 
 int image_moment_slices(int n, size_t npx) {
   // about four blocks per SM in all, slices of at least 64K pixels
-  const long want = (4L * 152 + n - 1) / std::max(n, 1);
+  const long want = (4L * sm_count() + n - 1) / std::max(n, 1);
   const long most = (long)std::max<size_t>(1, npx / 65536);
   return (int)std::max(1L, std::min(std::min(want, most), 256L));
 }

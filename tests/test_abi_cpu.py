@@ -213,3 +213,15 @@ def test_wide_index_tuning_key(L):
         with pytest.raises(rf.RfError) as e:
             rf.rf_plan_set_tuning(p.handle, rf.RF_TUNE_WIDE_INDEX, 2)
         assert e.value.status == rf.RF_ERR_INVALID_ARG
+
+
+def test_noalloc_rejects_host_memory(L):
+    # a host (numpy) buffer is not device memory of a current device: the call
+    # rejects it before any launch (on a machine without a GPU as on one with)
+    import numpy as np
+    grid = np.zeros((256, 129), dtype=np.complex64)
+    stat = np.zeros(rf.STAT_DTYPE.itemsize, dtype=np.uint8)
+    with pytest.raises(rf.RfError) as e:
+        rf.rf_image_stats_noalloc(grid, 256, 1.0, stat)
+    assert e.value.status == rf.RF_ERR_INVALID_ARG
+    assert "device memory" in e.value.message

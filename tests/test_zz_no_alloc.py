@@ -77,3 +77,57 @@ def test_noalloc_rejects_images_beyond_its_scratch(torch_cuda):
         rf.rf_image_stats_noalloc(grid, big, 1.0, stat)
     assert e.value.status == rf.RF_ERR_INVALID_ARG
     assert "1024" in e.value.message
+
+
+def _random_half_plane(npix, seed):
+    """A half plane gridded by the oracle from a random segment whose longest
+    baseline lands near the edge of an npix grid, with its weight W."""
+    from gpu_common import small_random_segment
+    rng = np.random.default_rng(seed)
+    seg = small_random_segment(rng, nant=10, nchan=6, nint=3, npix=npix)
+    bl = oracle.baseline_uvw(seg["ant_uvw"])
+    umax = np.abs(bl[:, :2]).max() * seg["freq_hz"].max() / oracle.C_LIGHT
+    cell = 1.0 / (umax * 2.2)                 # the longest baseline at about N/2.2 cells
+    op = oracle.OraclePlan(seg["ant_uvw"], seg["freq_hz"], 5e-3, npix, cell, [0.0], [1], 6.0, edge="full")
+    S = op.stokes(seg["vis"])
+    R, n = oracle.dedisperse_resample(S, op.delays[0], 1, 1, S.shape[0])
+    G = oracle.grid_full_plane(R, op.iu, op.iv, op.ongrid, npix)
+    W = op.weight(n)
+    I = oracle.dirty_image_fft(G, W)
+    return np.ascontiguousarray(G[:, : npix // 2 + 1]).astype(np.complex64), W, I
+
+
+@pytest.mark.parametrize("npix", [16, 512, 1024])
+def test_noalloc_against_the_oracle_at_its_size_limits(torch_cuda, npix):
+    # 16: one transform per warp part, no cross-lane Parseval shuffle beyond
+    # it; 512 and 1024 need more than 48 KB of dynamic shared memory, and
+    # 1024 is the largest image the static scratch holds
+    torch = torch_cuda
+    stat = torch.zeros(rf.STAT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    for seed in (1, 2):
+        H, W, I = _random_half_plane(npix, seed)
+        o = oracle.image_stats(I)
+        Hd = torch.from_numpy(H).cuda()
+        for _ in range(2):                       # two calls in a row on the shared scratch
+            rf.rf_image_stats_noalloc(Hd, npix, W, stat)
+            torch.cuda.synchronize()
+            got = np.frombuffer(stat.cpu().numpy().tobytes(), dtype=rf.STAT_DTYPE)[0]
+            x, y = int(got["x"]), int(got["y"])
+            if (x, y) != (o.x, o.y):             # a tie within rounding: the pixel must be a maximum too
+                assert o.peak - I[y, x] <= STAT_RTOL * abs(o.peak), ((x, y), (o.x, o.y))
+            assert abs(float(got["peak"]) - o.peak) <= STAT_RTOL * abs(o.peak), (npix, seed)
+            assert abs(float(got["sigma"]) - o.sigma) <= STAT_RTOL * o.sigma, (npix, seed)
+            assert abs(float(got["snr"]) - o.snr) <= 2 * STAT_RTOL * abs(o.snr), (npix, seed)
+            assert float(got["weight"]) == W
+
+
+def test_noalloc_rejects_host_pointers(torch_cuda):
+    torch = torch_cuda
+    grid = torch.zeros((256, 129), dtype=torch.complex64)
+    stat_dev = torch.zeros(rf.STAT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    for g, s in ((grid, stat_dev), (grid.pin_memory(), stat_dev),
+                 (grid.cuda(), torch.zeros(rf.STAT_DTYPE.itemsize, dtype=torch.uint8).pin_memory())):
+        with pytest.raises(rf.RfError) as e:
+            rf.rf_image_stats_noalloc(g, 256, 1.0, s)
+        assert e.value.status == rf.RF_ERR_INVALID_ARG
+        assert "device memory" in e.value.message
