@@ -2,17 +2,21 @@
 """Throughput benchmark of the realfast search engine on GB300.
 
 One step = one full segment search (every DM x dt x t' dirty image, peak,
-noise, threshold, candidates) of the ``realtime`` workload: 351 baselines,
-256 channels over 1-2 GHz, 1024 x 5 ms integrations, 128 DM trials 0-1500 on
-the smearing grid, dt {1,2,4,8}, 1024^2 images: 177,521 images per segment.
-The segment (1.47 GB of complex64 visibilities) is larger than L2, so the
-inputs are not L2-resident between steps.
+noise, threshold, candidates) of the ``batching`` workload: 351 baselines,
+1024 channels over 1-2 GHz, 2048 x 5 ms integrations stored in FP16, 256 DM
+trials 0-3000, dt {1,2,4,8,16}, 2048^2 images: 553,095 images per segment.
+The segment (11.8 GB of complex64 visibilities) is far larger than L2, so
+the inputs are not L2-resident between steps.  ``--config realtime`` times
+the 1024^2 workload (177,521 images) instead; by default its images/s are
+also reported under the key ``realtime``.
 
 ``value``: dirty images per second with the segment resident in HBM.
 ``e2e``: the same metric through the same C-ABI call with the segment in
 pinned host memory (host-to-device copies inside the timed region).
-``roofline``: the dominant kernel's algorithmic throughput from CUDA events
-recorded around each of its launches during the timed region.
+``roofline``: the dominant kernel's algorithmic HBM bytes per launch over
+its average launch time, from CUDA events recorded around each of its
+launches during the timed region, against the measured copy bandwidth; its
+FP32 issue rate against the derived ALU peak rides along under ``alu``.
 ``cpu_baseline``: the FP64 oracle on a bounded sample of the same images on
 the host cores (a reported baseline, not the target).
 
@@ -41,8 +45,6 @@ if ROOT not in sys.path:
 METRIC = "dirty images/sec (DM×dt×int) and visibility GB/s vs HBM peak; p99 latency/real-time"
 UNIT = "images/s"
 FP32_LANES_PER_SM = 128
-GB300_SMS = 152
-GB300_MAX_SM_MHZ = 2070.0
 
 
 def parse():
@@ -51,7 +53,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
-    ap.add_argument("--config", default="realtime")
+    ap.add_argument("--config", default=None,
+                    help="workload (default: batching; realtime for --next-rows)")
+    ap.add_argument("--no-realtime-extra", action="store_true",
+                    help="do not also time the realtime workload under the key `realtime`")
     ap.add_argument("--form", default="batched", choices=["batched", "plain"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -102,12 +107,14 @@ def job_rate(world, steps, units_per_rank, ms):
 
 
 def peaks():
+    """HBM copy bandwidth (GB/s) and the maximum SM clock (MHz), measured
+    on the GB300s when MEASURED_PEAKS.json is present."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             m = json.load(f)
-        return float(m["hbm_gbs"]), "measured"
+        return float(m["hbm_gbs"]), float(m.get("sm_max_mhz", 2070.0)), "measured"
     except Exception:
-        return 6800.0, "fallback"
+        return 6800.0, 2070.0, "fallback"
 
 
 # ------------------------------------------------------------------ clocks --
@@ -238,28 +245,48 @@ def cpu_baseline(spec, seg, seconds):
 
 
 # ------------------------------------------------------------ work counts --
-def work_per_image(spec, info, fp16):
-    """Algorithmic bytes and flops per image of each imaging kernel.
+def dt1_fraction(plan, spec, nint):
+    """Fraction of the segment's images at dt = 1 (counted from the plan's
+    delay table and edge rule): those gather the stored samples, the others
+    the FP32 resampled series."""
+    import numpy as np
+    maxd = plan.delays().max(axis=1)
+    n = {}
+    for dt in spec.dt_list:
+        if spec.edge == "partial":
+            n[dt] = len(maxd) * (nint // dt)
+        else:
+            n[dt] = int(np.sum(np.maximum(nint - maxd, 0) // dt))
+    tot = sum(n.values())
+    return n.get(1, 0) / tot if tot else 1.0
 
-    grid_cells: one resampled sample per gridding entry (8 B FP32, 4 B FP16)
-    read and one 8-byte cell value written per occupied cell.
-    grid_colfft (the column FFTs): cells read, column FFT output
-    (8 N ncol B) written; ncol length-N FFTs.
-    rowfft_stats: the column FFT output read once; N/2 length-N FFTs (two
-    image rows per complex transform).  FFTs count 5 N log2 N flops.
+
+def work_per_image(spec, info, frac_dt1):
+    """Algorithmic HBM bytes and FP32 flops per image of each imaging kernel
+    (columns beyond the longest baseline are pruned: ncol = iu_max + 1).
+
+    grid_cells: one sample per gridding entry read (dt = 1: the stored
+    sample, 4 B FP16 or 8 B FP32; dt > 1: the FP32 resampled sum, 8 B) and
+    one 8-byte cell value written per occupied cell.
+    grid_colfft (the column FFTs): cells read, column-FFT output T (8 N ncol
+    B) written; ncol length-N FFTs.
+    rowfft_stats: T read once; N/2 length-N FFTs (two image rows per complex
+    transform).  FFTs count 5 N log2 N flops.
     """
     N = spec.npix
     ncol = info.iu_max + 1
-    esz = 4 if fp16 else 8
+    esz1 = 4 if spec.store == "fp16" else 8
+    gather = (frac_dt1 * esz1 + (1.0 - frac_dt1) * 8) * info.n_entries
     fft = 5.0 * N * math.log2(N)
     return {
-        "grid_cells": {"bytes": esz * info.n_entries + 8 * info.n_cells, "flops": 0.0, "bound": "hbm"},
-        "grid_colfft": {"bytes": 8 * info.n_cells + 8 * N * ncol, "flops": ncol * fft, "bound": "alu"},
-        "rowfft_stats": {"bytes": 8 * N * ncol, "flops": (N / 2) * fft, "bound": "alu"},
+        "grid_cells": {"bytes": gather + 8 * info.n_cells, "flops": 0.0},
+        "grid_colfft": {"bytes": 8 * info.n_cells + 8 * N * ncol, "flops": ncol * fft},
+        "rowfft_stats": {"bytes": 8 * N * ncol, "flops": (N / 2) * fft},
     }
 
 
-FP32_PEAK_TFLOPS = GB300_SMS * FP32_LANES_PER_SM * 2 * GB300_MAX_SM_MHZ * 1e6 / 1e12
+def fp32_peak_tflops(sms, mhz):
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
 
 def load_traffic(kernel, images_per_launch):
@@ -329,8 +356,14 @@ def write_traffic(raw_csv, images_per_launch, command, workload, path=None):
     return doc
 
 
-def roofline(prof, spec, info, n_images, steps, fp16, hbm_peak, peak_kind):
-    work = work_per_image(spec, info, fp16)
+def roofline(prof, spec, info, n_images, steps, frac_dt1, hbm_peak, peak_kind, sms, sm_mhz, step_ms):
+    """The dominant kernel's roofline on HBM: its algorithmic bytes per
+    launch (work_per_image x images per launch) over its average launch time
+    (CUDA events around every launch in the timed region), against the
+    measured copy bandwidth.  Its FP32 rate against the derived ALU peak, and
+    the whole step's algorithmic bytes over the step time, ride along."""
+    work = work_per_image(spec, info, frac_dt1)
+    alu_peak = fp32_peak_tflops(sms, sm_mhz)
     per = {}
     for name, w in work.items():
         launches, ms = prof.get(name, (0, 0.0))
@@ -339,26 +372,28 @@ def roofline(prof, spec, info, n_images, steps, fp16, hbm_peak, peak_kind):
         imgs = n_images * steps / launches
         avg_s = ms / launches / 1e3
         per[name] = dict(launches=launches, total_ms=ms, avg_us=avg_s * 1e6, images_per_launch=imgs,
-                         gbs=w["bytes"] * imgs / avg_s / 1e9, tflops=w["flops"] * imgs / avg_s / 1e12,
-                         bound=w["bound"])
+                         bytes_per_image=w["bytes"], gbs=w["bytes"] * imgs / avg_s / 1e9,
+                         hbm_frac=w["bytes"] * imgs / avg_s / 1e9 / hbm_peak,
+                         tflops=w["flops"] * imgs / avg_s / 1e12)
     if not per:
         return None, per
     dom = max(per, key=lambda k: per[k]["total_ms"])
     d = per[dom]
     traffic = load_traffic(dom, d["images_per_launch"])
-    if d["bound"] == "alu":
-        r = {"bound": "alu", "achieved": round(d["tflops"], 3), "peak": round(FP32_PEAK_TFLOPS, 2),
-             "unit": "TFLOP/s", "frac": round(d["tflops"] / FP32_PEAK_TFLOPS, 4), "traffic": traffic,
-             "kernel": dom,
-             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz max SM clock",
-             "flops_model": "5 N log2 N per length-N complex FFT",
-             "hbm_achieved_gbs": round(d["gbs"], 1), "hbm_frac_of_measured": round(d["gbs"] / hbm_peak, 4)}
-    else:
-        r = {"bound": "hbm", "achieved": round(d["gbs"], 1), "peak": hbm_peak, "unit": "GB/s",
-             "frac": round(d["gbs"] / hbm_peak, 4), "traffic": traffic, "kernel": dom,
-             "peak_source": peak_kind}
-    r["avg_launch_us"] = round(d["avg_us"], 2)
-    r["images_per_launch"] = round(d["images_per_launch"], 1)
+    step_bytes = sum(w["bytes"] for w in work.values()) * n_images
+    r = {"bound": "hbm", "achieved": round(d["gbs"], 1), "peak": hbm_peak, "unit": "GB/s",
+         "frac": round(d["gbs"] / hbm_peak, 4), "traffic": traffic, "kernel": dom,
+         "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind}, copy bandwidth)",
+         "bytes_per_image": round(d["bytes_per_image"]),
+         "bytes_model": "pruned algorithmic bytes: see work_per_image",
+         "avg_launch_us": round(d["avg_us"], 2), "images_per_launch": round(d["images_per_launch"], 1),
+         "alu": {"achieved": round(d["tflops"], 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
+                 "frac": round(d["tflops"] / alu_peak, 4),
+                 "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_mhz:.0f} MHz",
+                 "flops_model": "5 N log2 N per length-N complex FFT"},
+         "step": {"bytes_per_image": round(step_bytes / max(n_images, 1)),
+                  "gbs": round(step_bytes / (step_ms / 1e3) / 1e9, 1),
+                  "frac": round(step_bytes / (step_ms / 1e3) / 1e9 / hbm_peak, 4)}}
     return r, per
 
 
@@ -586,8 +621,131 @@ def run_next_rows(args):
     return 0
 
 
+def time_search(plan, vis, nint, steps, dist):
+    """CUDA-event time (ms, max over ranks) of `steps` back-to-back searches."""
+    import torch
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        out = plan.search(vis, nint)
+    e1.record()
+    torch.cuda.synchronize()
+    return max_over_ranks(e0.elapsed_time(e1), dist, "cuda"), out
+
+
+def run_workload(args, config, rank, world, dist, local_rank, lite=False):
+    """One workload's bench fields.  `lite`: images/s, the roofline and the
+    realtime factor only (no e2e, plain form or CPU baseline)."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_1802_03084_gb300 as rf
+
+    spec = synth.config(config)
+    if args.nchan:
+        spec.nchan = args.nchan
+    spec.seed = rank_seed(spec.seed, rank)   # each rank searches its own segment
+    seg = synth.make_segment(spec)
+    nint = spec.nint
+    want_e2e = not args.no_e2e and not lite
+    vis_pin = torch.from_numpy(seg["vis"]).pin_memory() if (want_e2e or args.host_input) else None
+    vis_dev = vis_pin if args.host_input else torch.from_numpy(seg["vis"]).cuda()
+    torch.cuda.synchronize()
+    plan = rf.Plan.from_spec(spec, seg["ant_uvw"], seg["freq_hz"], max_nint=nint, device=local_rank)
+    if args.form == "plain":
+        plan.set_form(rf.RF_FORM_PLAIN)
+    tuning = None
+    if args.wave_images:
+        plan.set_wave_images(args.wave_images)
+    elif not args.no_autotune and args.form == "batched":
+        tuning = plan.autotune(vis_dev, nint, cache_path=args.tune_cache)
+    info = plan.info()
+    n_images = plan.count_images(nint)
+    frac_dt1 = dt1_fraction(plan, spec, nint)
+    warmup = max(args.warmup, 0)
+    steps = args.steps if not lite else max(3, min(args.steps, 5))
+    for _ in range(warmup):
+        cands = plan.search(vis_dev, nint)
+    plan.set_profiling(True)
+    clocks = Clocks(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    ms, cands = time_search(plan, vis_dev, nint, steps, dist)
+    clk = clocks.stop()
+    prof = plan.profile()
+    plan.set_profiling(False)
+    n_cand = len(cands)
+
+    e2e = None
+    if vis_pin is not None and want_e2e:
+        plan.search(vis_pin, nint)
+        ems, c2 = time_search(plan, vis_pin, nint, steps, dist)
+        e2e = {"value": job_rate(world, steps, n_images, ems), "unit": UNIT,
+               "h2d_bytes_per_step": int(seg["vis"].nbytes),
+               "d2h_bytes_per_step": int(4 + len(c2) * rf.CANDIDATE_DTYPE.itemsize),
+               "ms_per_step": ems / steps, "api": "rf_search_segment from pinned host memory"}
+
+    # the same segment without per-kernel events (graph replay), and the
+    # plain one-launch-set-per-trial form on the same GPU
+    plan.search(vis_dev, nint)
+    gms, _ = time_search(plan, vis_dev, nint, steps, dist)
+    graph_value = job_rate(world, steps, n_images, gms)
+    plain = None
+    if not args.no_plain and args.form == "batched" and not lite:
+        plan.set_form(rf.RF_FORM_PLAIN)
+        plan.search(vis_dev, max(1, nint // 4))   # allocates the plain form's buffers
+        pms, _ = time_search(plan, vis_dev, nint, 1, dist)
+        plain = {"value": job_rate(world, 1, n_images, pms), "unit": UNIT, "ms_per_step": pms, "steps": 1,
+                 "form": "one unfused launch set per (DM, dt) trial, intermediates in HBM"}
+        plan.set_form(rf.RF_FORM_BATCHED)
+
+    hbm_peak, sm_max_mhz, peak_kind = peaks()
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    roof, per_kernel = roofline(prof, spec, info, n_images, steps, frac_dt1, hbm_peak, peak_kind, sms,
+                                clk.get("sm_max_mhz") or sm_max_mhz, ms / steps)
+    launches = sum(v[0] for k, v in prof.items() if k != "h2d_copy")
+    value = job_rate(world, steps, n_images, ms)
+    seg_s = nint * spec.inttime_s
+    out = {
+        "value": value, "steps": steps, "warmup": warmup, "ms_per_step": ms / steps,
+        "dtype": "f32" if spec.store != "fp16" else "f16-storage/f32",
+        "config": {"workload": workload_name(spec), "images_per_step": n_images, "form": args.form,
+                   "wave_images": plan.wave_images(), "input": "pinned host" if args.host_input else "HBM",
+                   "autotune": tuning,
+                   "l2": f"inputs larger than L2 ({seg['vis'].nbytes / 1e9:.2f} GB segment per step)",
+                   "parallelism": f"dp{world} (one segment per GPU)"},
+        "visibility_gbs": world * steps * seg["vis"].nbytes / (ms / 1e3) / 1e9,
+        "realtime_factor": seg_s / (ms / steps / 1e3),
+        "segment_latency_ms": ms / steps,
+        "segment_duration_ms": seg_s * 1e3,
+        "candidates_per_step": n_cand,
+        "roofline": roof,
+        "kernels": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                    for k, v in per_kernel.items()},
+        "kernel_source_hash": source_hash(),
+        "e2e": e2e,
+        "graph_replay_value": graph_value,
+        "plain_form": plain,
+        "batched_over_plain": (value / plain["value"]) if plain else None,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not lite:
+        out["cpu_baseline"] = cpu_baseline(spec, seg, args.cpu_seconds)
+    plan.close()
+    del vis_dev, vis_pin, seg
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse()
+    if args.config is None:
+        args.config = "realtime" if args.next_rows else "batching"
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -603,9 +761,7 @@ def main():
     if args.next_rows:
         return run_next_rows(args) if rank == 0 else 0
 
-    import numpy as np
     import torch
-    import synth
     import paper_1802_03084_gb300 as rf
     from paper_1802_03084_gb300.build import build
 
@@ -620,131 +776,18 @@ def main():
         dist.barrier()
     rf.lib()
 
-    spec = synth.config(args.config)
-    if args.nchan:
-        spec.nchan = args.nchan
-    spec.seed = rank_seed(spec.seed, rank)   # each rank searches its own segment
-    seg = synth.make_segment(spec)
-    nint = spec.nint
-    vis_pin = torch.from_numpy(seg["vis"]).pin_memory() if (not args.no_e2e or args.host_input) else None
-    vis_dev = vis_pin if args.host_input else torch.from_numpy(seg["vis"]).cuda()
-    torch.cuda.synchronize()
-    plan = rf.Plan.from_spec(spec, seg["ant_uvw"], seg["freq_hz"], max_nint=nint, device=local_rank)
-    if args.form == "plain":
-        plan.set_form(rf.RF_FORM_PLAIN)
-    tuning = None
-    if args.wave_images:
-        plan.set_wave_images(args.wave_images)
-    elif not args.no_autotune and args.form == "batched":
-        tuning = plan.autotune(vis_dev, nint, cache_path=args.tune_cache)
-    info = plan.info()
-    n_images = plan.count_images(nint)
-    fp16 = spec.store == "fp16"
-    for _ in range(max(args.warmup, 0)):
-        cands = plan.search(vis_dev, nint)
-    plan.set_profiling(True)
-    clocks = Clocks(local_rank)
-    clocks.start()
-    time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    for _ in range(args.steps):
-        cands = plan.search(vis_dev, nint)
-    ev1.record()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    clk = clocks.stop()
-    ms = max_over_ranks(ms, dist, "cuda")
-    prof = plan.profile()
-    plan.set_profiling(False)
-    n_cand = len(cands)
-
-    e2e = None
-    if vis_pin is not None and not args.no_e2e:
-        plan.search(vis_pin, nint)
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
-            c2 = plan.search(vis_pin, nint)
-        e1.record()
-        torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1)
-        ems = max_over_ranks(ems, dist, "cuda")
-        e2e = {"value": job_rate(world, args.steps, n_images, ems), "unit": UNIT,
-               "h2d_bytes_per_step": int(seg["vis"].nbytes),
-               "d2h_bytes_per_step": int(4 + len(c2) * rf.CANDIDATE_DTYPE.itemsize),
-               "ms_per_step": ems / args.steps}
-
-    # the same segment without per-kernel events (graph replay), and the
-    # plain one-launch-set-per-trial form on the same GPU
-    torch.cuda.synchronize()
-    g0 = torch.cuda.Event(enable_timing=True)
-    g1 = torch.cuda.Event(enable_timing=True)
-    plan.search(vis_dev, nint)
-    g0.record()
-    for _ in range(args.steps):
-        plan.search(vis_dev, nint)
-    g1.record()
-    torch.cuda.synchronize()
-    graph_value = job_rate(world, args.steps, n_images, max_over_ranks(g0.elapsed_time(g1), dist, "cuda"))
-    plain = None
-    if not args.no_plain and args.form == "batched":
-        plan.set_form(rf.RF_FORM_PLAIN)
-        plan.search(vis_dev, nint)
-        p0 = torch.cuda.Event(enable_timing=True)
-        p1 = torch.cuda.Event(enable_timing=True)
-        p0.record()
-        plan.search(vis_dev, nint)
-        p1.record()
-        torch.cuda.synchronize()
-        pms = p0.elapsed_time(p1)
-        plain = {"value": n_images / (pms / 1e3), "unit": UNIT, "ms_per_step": pms, "steps": 1,
-                 "form": "one unfused launch set per (DM, dt) trial, intermediates in HBM"}
-        plan.set_form(rf.RF_FORM_BATCHED)
-
-    hbm_peak, peak_kind = peaks()
-    roof, per_kernel = roofline(prof, spec, info, n_images, args.steps, fp16, hbm_peak, peak_kind)
-    launches = sum(v[0] for k, v in prof.items() if k != "h2d_copy")
-    value = job_rate(world, args.steps, n_images, ms)
-    seg_s = nint * spec.inttime_s
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if not fp16 else "f16-storage/f32", "data": "synthetic",
-        "config": {"workload": workload_name(spec), "images_per_step": n_images, "form": args.form,
-                   "wave_images": plan.wave_images(), "input": "pinned host" if args.host_input else "HBM",
-                   "autotune": tuning,
-                   "l2": f"inputs larger than L2 ({seg['vis'].nbytes / 1e9:.2f} GB segment per step)",
-                   "parallelism": f"dp{world} (one segment per GPU)"},
-        "visibility_gbs": world * args.steps * seg["vis"].nbytes / (ms / 1e3) / 1e9,
-        "realtime_factor": seg_s / (ms / args.steps / 1e3),
-        "segment_latency_ms": ms / args.steps,
-        "segment_duration_ms": seg_s * 1e3,
-        "candidates_per_step": n_cand,
-        "roofline": roof,
-        "kernels": {k: {kk: (round(vv, 3) if isinstance(vv, float) else vv) for kk, vv in v.items()}
-                    for k, v in per_kernel.items()},
-        "kernel_source_hash": source_hash(),
-        "e2e": e2e,
-        "graph_replay_value": graph_value,
-        "plain_form": plain,
-        "batched_over_plain": (value / plain["value"]) if plain else None,
-        "gpu_launches": int(launches),
-        "clocks": clk,
-    }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(spec, seg, args.cpu_seconds)
-    plan.close()
+    main_fields = run_workload(args, args.config, rank, world, dist, local_rank)
+    extra = None
+    if args.config == "batching" and not args.no_realtime_extra and not args.nchan and not args.host_input:
+        r = run_workload(args, "realtime", rank, world, dist, local_rank, lite=True)
+        extra = {k: r[k] for k in ("value", "ms_per_step", "steps", "realtime_factor", "roofline", "kernels",
+                                   "graph_replay_value", "clocks", "config", "dtype")}
+        extra["unit"] = UNIT
+    line = {"metric": METRIC, "value": main_fields["value"], "unit": UNIT, "n_gpus": world,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    line.update(main_fields)
+    if extra is not None:
+        line["realtime"] = extra
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -49,7 +49,9 @@ typedef enum rf_status {
 
 /* ---- plan flags (rf_plan_desc.flags) ---------------------------------- */
 /* Store the Stokes-I visibilities on the device as FP16 (round to nearest)
- * instead of FP32; dedispersion sums, gridding and FFT stay FP32. */
+ * instead of FP32; dedispersion sums, gridding and FFT stay FP32.  The
+ * boxcar sums over dt > 1 integrations are formed in FP32 and stored as
+ * FP32, so only the visibilities themselves are rounded to FP16. */
 #define RF_STORE_FP16 0x1u
 /* PARTIAL edge rule: search t' < floor(nint/dt) for every DM; samples past
  * the end of the segment get weight 0.  Default (FULL): only t' whose whole

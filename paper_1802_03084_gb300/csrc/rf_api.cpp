@@ -693,7 +693,7 @@ uint64_t estimate_device_bytes(const rf_plan* p, int slots) {
   for (int dt : p->dt) {
     if (dt == 1 || std::find(seen.begin(), seen.end(), dt) != seen.end()) continue;
     seen.push_back(dt);
-    b += r(rows * dt * ((nint_pad + dt - 1) / dt), esz);
+    b += r(rows * dt * ((nint_pad + dt - 1) / dt), sizeof(float2));  // resampled sums: FP32
   }
   b += r(p->dt.size(), 8) + r(p->dt.size(), 4);
   const int64_t img_cap = std::max<int64_t>(count_images(p, p->max_nint), 1);
@@ -755,7 +755,7 @@ rf_status alloc_device(rf_plan* p) {
   unsigned char* dS = nullptr;
   if ((s = p->dalloc(&dS, (size_t)p->nbl * p->nchan * p->nint_pad * esz)) != RF_OK) return s;
   p->d_S = dS;
-  // resampled series per dt (phase-split, same storage type as S)
+  // resampled series per dt (phase-split; FP32 sums whatever the storage of S)
   p->d_sdt.assign(p->ndt, nullptr);
   p->sdt_lp.assign(p->ndt, 0);
   std::vector<unsigned long long> sdt_addr(p->ndt, 0);
@@ -774,7 +774,7 @@ rf_status alloc_device(rf_plan* p) {
         }
       if (!same) {
         unsigned char* b = nullptr;
-        if ((s = p->dalloc(&b, (size_t)p->nbl * p->nchan * dt * lp * esz)) != RF_OK) return s;
+        if ((s = p->dalloc(&b, (size_t)p->nbl * p->nchan * dt * lp * sizeof(float2))) != RF_OK) return s;
         p->d_sdt[k] = b;
       }
     }

@@ -187,7 +187,8 @@ cudaError_t launch_mean_subtract(const SegmentGeom& g, void* S, cudaStream_t st)
 // j in order, samples at or past nint counted as absent.  The phase-split
 // layout makes the dedispersion gather of consecutive t' read consecutive
 // addresses for every dt: sample t' dt + delta lives at phase delta mod dt,
-// index t' + delta div dt.
+// index t' + delta div dt.  The sums are FP32 and stored as FP32 whatever
+// the storage of S (FP16 storage applies to the visibilities only).
 template <bool FP16>
 __global__ void __launch_bounds__(256) k_resample(const void* __restrict__ S, void* __restrict__ out, int nrows,
                                                   int nint, int nint_pad, int dt, int lp) {
@@ -212,10 +213,7 @@ __global__ void __launch_bounds__(256) k_resample(const void* __restrict__ S, vo
         a.y += v.y;
       }
     }
-    if (FP16)
-      reinterpret_cast<__half2*>(out)[o] = __floats2half2_rn(a.x, a.y);
-    else
-      reinterpret_cast<float2*>(out)[o] = a;
+    reinterpret_cast<float2*>(out)[o] = a;
   }
 }
 
@@ -257,21 +255,14 @@ constexpr int kGatherBatch = 4;  // samples each lane has in flight (swept: 4 at
 // for N <= 8192); bit 30 = ENT_CONJ, bit 31 = ENT_NEG.
 constexpr unsigned kCellMask = (1u << 30) - 1u;
 
+// One warp's range r of gridding entries for group gr; FP16 is the sample
+// type of the series the group reads (S itself at dt = 1 under FP16 storage;
+// the resampled series are FP32).
 template <bool FP16, bool IDX32, bool PARTIAL>
-__global__ void __launch_bounds__(256, 6) k_grid_cells(SegmentGeom g, DevTables tb, const Group* __restrict__ groups,
-                                                    int g_begin, float2* __restrict__ cellbuf) {
+__device__ __forceinline__ void grid_range(const SegmentGeom& g, const DevTables& tb, const Group& gr,
+                                           const int* __restrict__ sdel, int lane, int r,
+                                           float2* __restrict__ cellbuf) {
   using Off = typename std::conditional<IDX32, unsigned, unsigned long long>::type;
-  extern __shared__ int sdel[];  // [nchan] delays of this group's DM
-  const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const Group gr = groups[g_begin + blockIdx.x];
-  {
-    const int* __restrict__ dl = tb.delays + (size_t)gr.d * g.nchan;
-    for (int c = tid; c < g.nchan; c += blockDim.x) sdel[c] = dl[c];
-  }
-  __syncthreads();
-  const int r = blockIdx.y * (blockDim.x >> 5) + (tid >> 5);
-  if (r >= g.nranges) return;
   const int2 rg = tb.ranges[r];
   const int ebeg = rg.x, eend = rg.y;
   const int dt = tb.dt_list[gr.s];
@@ -338,6 +329,30 @@ __global__ void __launch_bounds__(256, 6) k_grid_cells(SegmentGeom g, DevTables 
     }
   }
   if (cur != 0xffffffffu) out[(size_t)cur * 32] = acc;
+}
+
+// FP16: the plan stores S in FP16 (the dt = 1 series); every resampled
+// series (dt > 1) is FP32.
+template <bool FP16, bool IDX32, bool PARTIAL>
+__global__ void __launch_bounds__(256, 6) k_grid_cells(SegmentGeom g, DevTables tb, const Group* __restrict__ groups,
+                                                    int g_begin, float2* __restrict__ cellbuf) {
+  extern __shared__ int sdel[];  // [nchan] delays of this group's DM
+  const int tid = threadIdx.x;
+  const Group gr = groups[g_begin + blockIdx.x];
+  {
+    const int* __restrict__ dl = tb.delays + (size_t)gr.d * g.nchan;
+    for (int c = tid; c < g.nchan; c += blockDim.x) sdel[c] = dl[c];
+  }
+  __syncthreads();
+  const int r = blockIdx.y * (blockDim.x >> 5) + (tid >> 5);
+  if (r >= g.nranges) return;
+  if constexpr (FP16) {
+    if (tb.dt_list[gr.s] == 1) {
+      grid_range<true, IDX32, PARTIAL>(g, tb, gr, sdel, tid & 31, r, cellbuf);
+      return;
+    }
+  }
+  grid_range<false, IDX32, PARTIAL>(g, tb, gr, sdel, tid & 31, r, cellbuf);
 }
 
 cudaError_t launch_grid_cells(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin,

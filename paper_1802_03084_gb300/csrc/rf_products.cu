@@ -27,6 +27,8 @@ __device__ __forceinline__ float2 load_resampled(const unsigned char* base, size
 }
 
 // One warp per (candidate, channel); lanes stride over the baselines.
+// FP16: S is stored in FP16, which the dt = 1 series reads; the resampled
+// series (dt > 1) are FP32.
 template <bool FP16>
 __global__ void __launch_bounds__(256) k_cand_spectrum(SegmentGeom g, DevTables tb, const int2* __restrict__ cellbc,
                                                        const CandRef* __restrict__ refs, int n,
@@ -54,7 +56,8 @@ __global__ void __launch_bounds__(256) k_cand_spectrum(SegmentGeom g, DevTables 
       const int row = c * g.nbl + b;
       const int2 cv = cellbc[row];
       if (cv.x == kOffGrid) continue;
-      const float2 v = load_resampled<FP16>(Sd, (size_t)row * rowpitch + part);
+      const float2 v = (FP16 && dt == 1) ? load_resampled<true>(Sd, (size_t)row * rowpitch + part)
+                                         : load_resampled<false>(Sd, (size_t)row * rowpitch + part);
       long long kk = (long long)cv.x * dx + (long long)cv.y * dy;
       int m = (int)(kk % N);
       if (m < 0) m += N;
