@@ -84,7 +84,7 @@ def test_results_same_alone_and_in_the_mix():
     op = oracle.OraclePlan(seg["ant_uvw"], seg["freq_hz"], spec.inttime_s, spec.npix, spec.cell_rad,
                            spec.dm_list, spec.dt_list, spec.threshold, edge="partial")
     S = op.stokes(seg["vis"])
-    pick = cands[np.argsort(-cands["snr"])[:4]].tolist() + cands[:: max(1, len(cands) // 4)][:4].tolist()
+    pick = np.concatenate([cands[np.argsort(-cands["snr"])[:4]], cands[:: max(1, len(cands) // 4)][:4]])
     for c in pick:
         key = (int(c["dm_idx"]), int(c["dt_idx"]), int(c["t_idx"]))
         I, W = op.image(S, *key, nint=spec.nint)
