@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--wave-images", type=int, default=0, help="images per wave (0 = engine default)")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain per-trial form")
     ap.add_argument("--no-autotune", action="store_true", help="keep the engine's default tuning")
+    ap.add_argument("--fused", type=int, default=-1, choices=[-1, 0, 1],
+                    help="force the fused imaging pass off (0) or on (1); -1: the autotuner's or default choice")
+    ap.add_argument("--ring", type=int, default=0, help="chunk slots of the fused pass's ring (0: default)")
     ap.add_argument("--tune-cache", default=os.path.expanduser("~/.cache/realfast_gb300/tune.json"))
     ap.add_argument("--serving", action="store_true",
                     help="Poisson stream of mixed-shape segments at 1.0x real time through rf_server_*")
@@ -272,6 +275,11 @@ def work_per_image(spec, info, frac_dt1):
     B) written; ncol length-N FFTs.
     rowfft_stats: T read once; N/2 length-N FFTs (two image rows per complex
     transform).  FFTs count 5 N log2 N flops.
+    image_fused (the column and row passes in one launch): the same bytes and
+    flops as grid_colfft and rowfft_stats together -- T counted written and
+    read once, as the byte model of a two-pass FFT does, although the fused
+    pass keeps it in an L2-resident ring (its DRAM traffic, from ncu, is far
+    lower).
     """
     N = spec.npix
     ncol = info.iu_max + 1
@@ -282,6 +290,7 @@ def work_per_image(spec, info, frac_dt1):
         "grid_cells": {"bytes": gather + 8 * info.n_cells, "flops": 0.0},
         "grid_colfft": {"bytes": 8 * info.n_cells + 8 * N * ncol, "flops": ncol * fft},
         "rowfft_stats": {"bytes": 8 * N * ncol, "flops": (N / 2) * fft},
+        "image_fused": {"bytes": 8 * info.n_cells + 16 * N * ncol, "flops": (ncol + N / 2) * fft},
     }
 
 
@@ -306,7 +315,7 @@ def load_traffic(kernel, images_per_launch):
 
 
 KERNEL_SOURCES = ("rf_async.cuh", "rf_fft.cuh", "rf_image.cuh", "rf_image_small.cu", "rf_image_large.cu",
-                  "rf_kernels.cu")
+                  "rf_image_fused.cu", "rf_kernels.cu")
 
 
 def source_hash():
@@ -321,7 +330,8 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-TRAFFIC_KERNELS = (("k_grid_cells", "grid_cells"), ("k_colfft", "grid_colfft"), ("k_rowfft_stats", "rowfft_stats"))
+TRAFFIC_KERNELS = (("k_grid_cells", "grid_cells"), ("k_colfft", "grid_colfft"), ("k_rowfft_stats", "rowfft_stats"),
+                   ("k_image_fused", "image_fused"))
 _BYTE_UNITS = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "tbyte": 1e12}
 
 
@@ -380,7 +390,9 @@ def roofline(prof, spec, info, n_images, steps, frac_dt1, hbm_peak, peak_kind, s
     dom = max(per, key=lambda k: per[k]["total_ms"])
     d = per[dom]
     traffic = load_traffic(dom, d["images_per_launch"])
-    step_bytes = sum(w["bytes"] for w in work.values()) * n_images
+    # the step's bytes: gridding, then the fused pass or the two passes it replaces
+    step_kernels = ["grid_cells"] + (["image_fused"] if "image_fused" in per else ["grid_colfft", "rowfft_stats"])
+    step_bytes = sum(work[k]["bytes"] for k in step_kernels) * n_images
     r = {"bound": "hbm", "achieved": round(d["gbs"], 1), "peak": hbm_peak, "unit": "GB/s",
          "frac": round(d["gbs"] / hbm_peak, 4), "traffic": traffic, "kernel": dom,
          "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind}, copy bandwidth)",
@@ -663,6 +675,10 @@ def run_workload(args, config, rank, world, dist, local_rank, lite=False):
         plan.set_wave_images(args.wave_images)
     elif not args.no_autotune and args.form == "batched":
         tuning = plan.autotune(vis_dev, nint, cache_path=args.tune_cache)
+    if args.fused >= 0:
+        plan.set_fused(bool(args.fused))
+    if args.ring:
+        plan.set_ring(args.ring)
     info = plan.info()
     n_images = plan.count_images(nint)
     frac_dt1 = dt1_fraction(plan, spec, nint)

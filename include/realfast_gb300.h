@@ -272,17 +272,36 @@ rf_status rf_plan_set_form(struct rf_plan* plan, int32_t form);
  *                      the same images; the knob lets a test run the 64-bit
  *                      variant on a small plan. */
 #define RF_TUNE_WIDE_INDEX 3
+/* RF_TUNE_FUSED        1: for npix 1024 .. 4096 the search runs
+ *                      each wave's column and row FFTs as one persistent
+ *                      launch whose column-FFT output passes through a small
+ *                      ring of chunk slots (RF_TUNE_RING of them, each one
+ *                      round of column transforms: 8 images at 1024^2, 4 at
+ *                      2048^2, 2 at 4096^2) that stays in L2; 0 (default):
+ *                      separate column and row launches through a wave-sized
+ *                      buffer (always so for other sizes, with
+ *                      RF_NOISE_CLIPPED and for rendered images).  The
+ *                      autotuner times both. */
+#define RF_TUNE_FUSED 4
+/* RF_TUNE_RING         chunk slots of the fused pass's ring, 2 .. 8
+ *                      (default 2). */
+#define RF_TUNE_RING 5
 rf_status rf_plan_set_tuning(struct rf_plan* plan, int32_t key, int64_t value);
 rf_status rf_plan_get_tuning(const struct rf_plan* plan, int32_t key, int64_t* value);
 
 /*
- * rf_plan_autotune: pick the tuning (RF_TUNE_WAVE_IMAGES from a ladder of
- * wave sizes that fit in half the free device memory, RF_TUNE_GRAPHS on or
- * off) that searches `vis` fastest, timing one full search per candidate
- * with CUDA events on `stream` after one warm-up, and apply it.  vis and
- * nint as for rf_search_segment.  `report` (may be NULL) receives what was
- * tried.  Results of the search do not depend on the tuning.
- * Errors: as rf_search_segment.
+ * rf_plan_autotune: pick the tuning that searches `vis` fastest and apply
+ * it.  Candidates: where the fused pass exists (npix 1024 .. 4096, no
+ * clipped noise), RF_TUNE_FUSED on with RF_TUNE_RING 2, 3 and 4 and off, at
+ * waves of 2048 and 8192 images, graphs on; elsewhere a ladder of wave sizes
+ * (256 .. 8192 images) with RF_TUNE_GRAPHS on and off.  Wave sizes whose
+ * column-FFT buffer would not fit in half the free device memory are
+ * skipped.  Each candidate is timed with CUDA events on `stream`, after one
+ * warm-up, on a search of the segment in which every (DM, dt) is limited to
+ * its first nint/4 integrations (the full search for short segments).  vis
+ * and nint as for rf_search_segment.  `report` (may be NULL) receives what
+ * was tried (at most 16 entries).  Results of the search do not depend on
+ * the tuning.  Errors: as rf_search_segment.
  */
 typedef struct rf_tune_report {
   int32_t best_wave_images;
@@ -291,6 +310,10 @@ typedef struct rf_tune_report {
   int32_t tried_wave_images[16];
   int32_t tried_graphs[16];
   float tried_ms[16];
+  int32_t best_fused;
+  int32_t best_ring;
+  int32_t tried_fused[16];
+  int32_t tried_ring[16];
 } rf_tune_report;
 rf_status rf_plan_autotune(struct rf_plan* plan, const void* vis, int32_t nint, void* stream,
                            rf_tune_report* report);

@@ -29,7 +29,7 @@ __all__ = [
     "Stream", "RfStreamInfo", "RfCandidateFeatures", "FEATURES_DTYPE", "rf_candidate_products",
     "RfPeriodicCandidate", "PERIODIC_DTYPE", "rf_periodicity_search", "rf_selftest_bounded_wait",
     "Plan", "CANDIDATE_DTYPE", "STAT_DTYPE", "declared_symbols",
-    "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_MEAN_SUBTRACT", "RF_NOISE_CLIPPED", "RF_TUNE_WIDE_INDEX", "RF_STREAM_KEEP_STATS", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
+    "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_MEAN_SUBTRACT", "RF_NOISE_CLIPPED", "RF_TUNE_WIDE_INDEX", "RF_TUNE_FUSED", "RF_TUNE_RING", "RF_STREAM_KEEP_STATS", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
 ]
 
 RF_OK = 0
@@ -57,6 +57,8 @@ RF_NOALLOC_MAX_NPIX = 1024
 RF_TUNE_WAVE_IMAGES = 1
 RF_TUNE_GRAPHS = 2
 RF_TUNE_WIDE_INDEX = 3
+RF_TUNE_FUSED = 4
+RF_TUNE_RING = 5
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
                       "realfast_gb300.h")
@@ -107,7 +109,8 @@ class RfPlanInfo(ctypes.Structure):
 class RfTuneReport(ctypes.Structure):
     _fields_ = [("best_wave_images", ctypes.c_int32), ("best_graphs", ctypes.c_int32), ("ntried", ctypes.c_int32),
                 ("tried_wave_images", ctypes.c_int32 * 16), ("tried_graphs", ctypes.c_int32 * 16),
-                ("tried_ms", ctypes.c_float * 16)]
+                ("tried_ms", ctypes.c_float * 16), ("best_fused", ctypes.c_int32), ("best_ring", ctypes.c_int32),
+                ("tried_fused", ctypes.c_int32 * 16), ("tried_ring", ctypes.c_int32 * 16)]
 
 
 class RfServerDesc(ctypes.Structure):
@@ -432,9 +435,10 @@ def rf_plan_autotune(plan, vis, nint: int, stream=None) -> dict:
     """Time the tuning ladder on this segment, apply the fastest, return what was tried."""
     rep = RfTuneReport()
     _check(lib().rf_plan_autotune(plan, _ptr(vis), nint, _stream(stream), ctypes.byref(rep)))
-    return {"wave_images": rep.best_wave_images, "graphs": rep.best_graphs,
-            "tried": [(rep.tried_wave_images[i], rep.tried_graphs[i], float(rep.tried_ms[i]))
-                      for i in range(rep.ntried)]}
+    return {"wave_images": rep.best_wave_images, "graphs": rep.best_graphs, "fused": rep.best_fused,
+            "ring": rep.best_ring,
+            "tried": [(rep.tried_wave_images[i], rep.tried_graphs[i], rep.tried_fused[i], rep.tried_ring[i],
+                       float(rep.tried_ms[i])) for i in range(rep.ntried)]}
 
 
 def rf_image_stats_noalloc(half_plane, npix: int, weight: float, stat, stream=None) -> None:
@@ -646,6 +650,14 @@ class Plan:
         """Gridding with 64-bit sample offsets even where 32-bit ones fit."""
         rf_plan_set_tuning(self.handle, RF_TUNE_WIDE_INDEX, 1 if enable else 0)
 
+    def set_fused(self, enable: bool):
+        """The fused column + row pass (npix 1024 .. 4096) on or off."""
+        rf_plan_set_tuning(self.handle, RF_TUNE_FUSED, 1 if enable else 0)
+
+    def set_ring(self, slots: int):
+        """Chunk slots of the fused pass's L2-resident ring (2 .. 8)."""
+        rf_plan_set_tuning(self.handle, RF_TUNE_RING, slots)
+
     def autotune(self, vis, nint=None, stream=None, cache_path=None, key_extra=""):
         """Apply a cached tuning for this shape, or run the autotuner and cache it.
 
@@ -669,13 +681,16 @@ class Plan:
                     cache = json.load(f)
             except (OSError, ValueError):
                 cache = {}
-        if key in cache:
+        if key in cache and "fused" in cache[key]:
             rf_plan_set_tuning(self.handle, RF_TUNE_WAVE_IMAGES, int(cache[key]["wave_images"]))
             rf_plan_set_tuning(self.handle, RF_TUNE_GRAPHS, int(cache[key]["graphs"]))
+            rf_plan_set_tuning(self.handle, RF_TUNE_FUSED, int(cache[key]["fused"]))
+            rf_plan_set_tuning(self.handle, RF_TUNE_RING, int(cache[key]["ring"]))
             return dict(cache[key], cached=True)
         res = rf_plan_autotune(self.handle, vis, n, stream)
         if cache_path:
-            cache[key] = {"wave_images": res["wave_images"], "graphs": res["graphs"]}
+            cache[key] = {"wave_images": res["wave_images"], "graphs": res["graphs"], "fused": res["fused"],
+                          "ring": res["ring"]}
             os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
             with open(cache_path, "w") as f:
                 json.dump(cache, f, indent=1)

@@ -55,6 +55,7 @@ constexpr size_t kTBudgetBytes = 4096ull << 20;  // column-FFT scratch per wave
 constexpr int kRangeEntries = 64;                // target entries per gridding warp
 constexpr size_t kPeriodicBudgetBytes = 1ull << 30;  // transformed series per DM batch
 constexpr size_t kPlainBudgetBytes = 4096ull << 20;  // plain form: intermediates of one chunk
+constexpr int kDefaultRing = 2;                      // fused pass: chunk slots of the ring
 
 // Round half away from zero: sign(x) floor(|x| + 1/2).
 inline double round_half_away(double x) { return x >= 0.0 ? std::floor(x + 0.5) : -std::floor(-x + 0.5); }
@@ -93,12 +94,12 @@ struct BusyGuard {
 
 enum KernelKind {
   K_H2D = 0, K_INGEST, K_RESAMPLE, K_WEIGHTS, K_GRID_CELLS, K_GRID_COLFFT, K_ROWFFT_STATS, K_FINALIZE,
-  K_PLAIN_TRIAL, K_MEAN_SUBTRACT, K_CLIP_WINDOW, K_NKINDS
+  K_PLAIN_TRIAL, K_MEAN_SUBTRACT, K_CLIP_WINDOW, K_IMAGE_FUSED, K_NKINDS
 };
 const char* const kKindNames[K_NKINDS] = {"h2d_copy",    "ingest",       "resample",
                                            "weights",     "grid_cells",   "grid_colfft",
                                            "rowfft_stats", "finalize",    "plain_trial_chunk",
-                                           "mean_subtract", "clip_window"};
+                                           "mean_subtract", "clip_window", "image_fused"};
 
 // Event-pair timing of every launch a plan issues while profiling is on.
 struct Profiler {
@@ -205,6 +206,7 @@ struct rf_plan {
   std::vector<int32_t> iu, iv;     // [nbl][nchan]
   std::vector<uint8_t> ongrid;     // [nbl][nchan]
   std::vector<int32_t> col_ent_ptr, col_cell_ptr, cell_row;
+  std::vector<int32_t> col_run_ptr, col_runs;  // runs of each column (see DevTables::col_runs)
   std::vector<int2> ranges;
   std::vector<int4> plain_ent;  // {bc, col, row, flags} for the plain form
   std::vector<GridEntry> ent;
@@ -252,6 +254,20 @@ struct rf_plan {
   float* d_mean0 = nullptr;     // [slots] Re H(0, 0)
   float2* d_clip = nullptr;     // [slots] clipping window (RF_NOISE_CLIPPED only)
   rf::PlainBuffers plain{};     // allocated on the first plain-form search
+
+  // fused column + row pass (npix 1024 .. 4096): chunks of the image list,
+  // the chunks of each wave, and the L2-resident ring of column-FFT output
+  bool fused = false;           // RF_TUNE_FUSED (the autotuner turns it on where it wins)
+  int ring = 2;                 // RF_TUNE_RING
+  int chunk_images = 0;         // images per chunk (0: no fused pass at this size)
+  std::vector<rf::FusedChunk> chunks;
+  std::vector<int2> wave_chunks;  // per wave: [first, last) chunk
+  rf::FusedChunk* d_chunks = nullptr;
+  int* d_fcount = nullptr;      // 1 + 2 x (most chunks of a wave) counters
+  int fcount_cap = 0;
+  float2* d_Tring = nullptr;
+  int ring_alloc = 0;
+  rf::TileMap tmap_ring{};
 
   // CUDA graph of the batched wave loop for the current image list
   bool use_graphs = true;
@@ -462,8 +478,15 @@ rf_status build_tables(rf_plan* p) {
         es.push_back({0, mod(-v), bc, rf::ENT_CONJ | neg});
       }
     }
-  std::sort(es.begin(), es.end(), [](const E& a, const E& b2) {
+  // Within a column, rows sort by (v mod L, v div L), L = N / col_split(N):
+  // the batched column pass finds the rows that share v mod L (combined by
+  // its decimation-in-frequency gather) next to each other.  For N <= 1024,
+  // L = N and this is plain row order.
+  const int Lc = N / rf::col_split(N);
+  std::sort(es.begin(), es.end(), [Lc](const E& a, const E& b2) {
     if (a.col != b2.col) return a.col < b2.col;
+    const int ka = a.row % Lc, kb = b2.row % Lc;
+    if (ka != kb) return ka < kb;
     if (a.row != b2.row) return a.row < b2.row;
     if (a.bc != b2.bc) return a.bc < b2.bc;
     return a.flags < b2.flags;
@@ -503,6 +526,21 @@ rf_status build_tables(rf_plan* p) {
   }
   p->col_ent_ptr[p->ncol] = (int)p->ent.size();
   p->col_cell_ptr[p->ncol] = p->n_cells;
+  // runs of each column for the column pass's scatter
+  p->col_run_ptr.assign(p->ncol + 1, 0);
+  p->col_runs.clear();
+  for (int col = 0; col < p->ncol; ++col) {
+    const int c0 = p->col_cell_ptr[col], c1 = p->col_cell_ptr[col + 1];
+    p->col_run_ptr[col] = (int)p->col_runs.size();
+    for (int c = c0; c < c1;) {
+      const int v1 = p->cell_row[c] % Lc;
+      int n = 1;
+      while (c + n < c1 && p->cell_row[c + n] % Lc == v1) ++n;
+      p->col_runs.push_back(((c - c0) << 4) | n);
+      c += n;
+    }
+  }
+  p->col_run_ptr[p->ncol] = (int)p->col_runs.size();
   cell_start.push_back((int)p->ent.size());
   // Cell-aligned entry ranges of about kRangeEntries entries (a range holds
   // whole cells; a cell with more entries is a range of its own).
@@ -575,9 +613,26 @@ void build_lists(rf_plan* p, int nint) {
   w.g_end = (int)p->groups.size();
   w.img_end = (int)p->img_info.size();
   if (w.img_end > w.img_begin) p->waves.push_back(w);
+  // chunks of the fused pass: each group's images in runs of chunk_images
+  p->chunks.clear();
+  p->wave_chunks.clear();
+  if (p->chunk_images > 0) {
+    for (const Wave& wv : p->waves) {
+      const int c0 = (int)p->chunks.size();
+      for (int gi = wv.g_begin; gi < wv.g_end; ++gi)
+        for (int k = 0; k < p->groups[gi].nimg; k += p->chunk_images)
+          p->chunks.push_back({gi, k, std::min(p->chunk_images, p->groups[gi].nimg - k), 0});
+      p->wave_chunks.push_back(make_int2(c0, (int)p->chunks.size()));
+    }
+  }
   p->cached_nint = nint;
   p->cached_span = p->t_span;
   p->drop_graph();
+}
+
+// Whether the search's waves take the fused column + row pass.
+bool use_fused(const rf_plan* p) {
+  return p->fused && p->chunk_images > 0 && p->tmap_ring.nbox > 0 && !(p->flags & RF_NOISE_CLIPPED);
 }
 
 // cuTensorMapEncodeTiled from the driver, looked up once.
@@ -600,17 +655,16 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // work item's 2 XB rows (XB 16-byte chunks) by `rows` columns u, swizzled so
 // that chunk c of column u lands at c ^ ((u >> sh) & (XB - 1)).  Where the
 // encoder is unavailable the row pass copies with cp.async (nbox = 0).
-void encode_tile_map(rf_plan* p) {
-  rf::TileMap& tm = p->tmap_T;
+void encode_tile_map(rf_plan* p, rf::TileMap& tm, float2* base, int slots) {
   tm.nbox = 0;
   const int N = p->npix;
-  if (N < 1024 || !p->d_T) return;
+  if (N < 1024 || !base || slots <= 0) return;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return;
   const int xb = std::min(256 / (N / 32), N / 2);
   int nbox, rows;
   rf::tile_boxes(p->ncol, &nbox, &rows);
-  const cuuint64_t dims[3] = {(cuuint64_t)2 * N, (cuuint64_t)p->ncol, (cuuint64_t)p->slots_max};
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * N, (cuuint64_t)p->ncol, (cuuint64_t)slots};
   const cuuint64_t strides[2] = {(cuuint64_t)N * 8, (cuuint64_t)p->ncol * N * 8};
   const cuuint32_t box[3] = {(cuuint32_t)(4 * xb), (cuuint32_t)rows, 1};
   const cuuint32_t es[3] = {1, 1, 1};
@@ -618,7 +672,7 @@ void encode_tile_map(rf_plan* p) {
                                 : xb == 4 ? CU_TENSOR_MAP_SWIZZLE_64B
                                 : xb == 2 ? CU_TENSOR_MAP_SWIZZLE_32B
                                           : CU_TENSOR_MAP_SWIZZLE_NONE;
-  const CUresult r = enc(&tm.map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p->d_T, dims, strides, box, es,
+  const CUresult r = enc(&tm.map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r == CUDA_SUCCESS) {
@@ -672,7 +726,36 @@ rf_status alloc_wave_scratch(rf_plan* p, int slots) {
   if ((s = p->dalloc(&p->d_colsq, (size_t)slots * p->ncol)) != RF_OK) return s;
   if ((s = p->dalloc(&p->d_mean0, (size_t)slots)) != RF_OK) return s;
   if ((p->flags & RF_NOISE_CLIPPED) && (s = p->dalloc(&p->d_clip, (size_t)slots)) != RF_OK) return s;
-  encode_tile_map(p);
+  encode_tile_map(p, p->tmap_T, p->d_T, p->slots_max);
+  // fused pass: counters for the most chunks a wave can hold
+  if (p->chunk_images > 0) {
+    const int cap = 1 + 2 * p->gslots_max * ((p->shape.images_per_group + p->chunk_images - 1) / p->chunk_images);
+    if (p->d_fcount) {
+      p->device_bytes -= (uint64_t)p->fcount_cap * sizeof(int);
+      p->dfree(p->d_fcount);
+      p->d_fcount = nullptr;
+    }
+    if ((s = p->dalloc(&p->d_fcount, (size_t)cap)) != RF_OK) return s;
+    p->fcount_cap = cap;
+  }
+  return RF_OK;
+}
+
+// (Re)allocate the fused pass's ring of `ring` chunk slots and its tensor map.
+rf_status alloc_ring(rf_plan* p, int ring) {
+  if (p->chunk_images <= 0) return RF_OK;
+  const size_t per_ring = (size_t)p->chunk_images * p->ncol * p->npix;
+  p->tmap_ring.nbox = 0;
+  p->drop_graph();
+  if (p->d_Tring) {
+    p->device_bytes -= (uint64_t)p->ring_alloc * per_ring * sizeof(float2);
+    p->dfree(p->d_Tring);
+    p->d_Tring = nullptr;
+  }
+  rf_status s = p->dalloc(&p->d_Tring, (size_t)ring * per_ring);
+  if (s != RF_OK) return s;
+  p->ring = p->ring_alloc = ring;
+  encode_tile_map(p, p->tmap_ring, p->d_Tring, ring * p->chunk_images);
   return RF_OK;
 }
 
@@ -684,7 +767,8 @@ uint64_t estimate_device_bytes(const rf_plan* p, int slots) {
   auto r = [](size_t n, size_t sz) { return (uint64_t)std::max<size_t>(n, 1) * sz; };
   uint64_t b = 0;
   b += r(p->delays.size(), 4) + r(p->dt.size(), 4) + r(p->ranges.size(), 8) + r(p->col_cell_ptr.size(), 4) +
-       r(p->cell_row.size(), 4) + r(p->ent.size(), sizeof(GridEntry)) + r(p->ongrid_chan.size(), 4) + r(rf::fft_twiddle_len((int)N), 8);
+       r(p->cell_row.size(), 4) + r(p->col_run_ptr.size(), 4) + r(p->col_runs.size(), 4) + r(p->ent.size(), sizeof(GridEntry)) + r(p->ongrid_chan.size(), 4) + r(rf::fft_twiddle_len((int)N), 8);
+  if (rf::col_split((int)N) > 1) b += r(rf::fft_twiddle_len((int)N / rf::col_split((int)N)), 8);
   const size_t nint_pad = (p->max_nint + 31) / 32 * 32;
   const size_t esz = (p->flags & RF_STORE_FP16) ? 4 : 8;
   const size_t rows = (size_t)p->nbl * p->nchan;
@@ -707,6 +791,11 @@ uint64_t estimate_device_bytes(const rf_plan* p, int slots) {
        r((size_t)gslots * std::max(p->n_cells, 1) * 32, sizeof(float2)) + r((size_t)slots * p->ncol, 4) +
        r(slots, 4);
   if (p->flags & RF_NOISE_CLIPPED) b += r(slots, sizeof(float2));
+  const int ci = rf::fused_chunk_images((int)N);
+  if (ci > 0) {
+    b += r(img_cap, sizeof(rf::FusedChunk)) + r(1 + 2 * gslots * ((B + ci - 1) / ci), 4);
+    b += r((size_t)kDefaultRing * ci * per_slot, 1);
+  }
   const size_t per_int = rows * p->npol * sizeof(float2);
   const size_t stage_nint = std::max<size_t>(1, std::min<size_t>(kStageBytes / per_int, (size_t)p->max_nint));
   b += r(stage_nint * per_int, 1);
@@ -724,7 +813,8 @@ rf_status alloc_device(rf_plan* p) {
     *dst = d;
     return RF_OK;
   };
-  int32_t *d_delays = nullptr, *d_dt = nullptr, *d_ogc = nullptr, *d_ccp = nullptr, *d_crow = nullptr;
+  int32_t *d_delays = nullptr, *d_dt = nullptr, *d_ogc = nullptr, *d_ccp = nullptr, *d_crow = nullptr,
+          *d_rptr = nullptr, *d_runs = nullptr;
   int2* d_ranges = nullptr;
   GridEntry* d_ent = nullptr;
   rf_status s;
@@ -734,20 +824,32 @@ rf_status alloc_device(rf_plan* p) {
   if ((s = up(&d_ranges, p->ranges)) != RF_OK) return s;
   if ((s = up(&d_ccp, p->col_cell_ptr)) != RF_OK) return s;
   if ((s = up(&d_crow, p->cell_row)) != RF_OK) return s;
+  if ((s = up(&d_rptr, p->col_run_ptr)) != RF_OK) return s;
+  if ((s = up(&d_runs, p->col_runs)) != RF_OK) return s;
   if ((s = up(&d_ent, p->ent)) != RF_OK) return s;
   if ((s = up(&d_ogc, p->ongrid_chan)) != RF_OK) return s;
   std::vector<float2> tw(rf::fft_twiddle_len(N));
   rf::fft_twiddle_table(N, tw.data());
   float2* d_tw = nullptr;
   if ((s = up(&d_tw, tw)) != RF_OK) return s;
+  float2* d_twc = d_tw;  // the column pass's sub-transform table
+  if (rf::col_split(N) > 1) {
+    const int L = N / rf::col_split(N);
+    std::vector<float2> twc(rf::fft_twiddle_len(L));
+    rf::fft_twiddle_table(L, twc.data());
+    if ((s = up(&d_twc, twc)) != RF_OK) return s;
+  }
   p->tb.delays = d_delays;
   p->tb.dt_list = d_dt;
   p->tb.ranges = d_ranges;
   p->tb.col_cell_ptr = d_ccp;
   p->tb.cell_row = d_crow;
+  p->tb.col_run_ptr = d_rptr;
+  p->tb.col_runs = d_runs;
   p->tb.ent = d_ent;
   p->tb.ongrid_chan = d_ogc;
   p->tb.twiddle = d_tw;
+  p->tb.twiddle_col = d_twc;
 
   // Stokes-I time series S[c * nbl + b][t]
   p->nint_pad = (p->max_nint + 31) / 32 * 32;
@@ -801,9 +903,12 @@ rf_status alloc_device(rf_plan* p) {
   RF_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
 
   // column-FFT scratch, whole groups per wave
+  p->chunk_images = rf::fused_chunk_images(N);
+  if (p->chunk_images > 0 && (s = p->dalloc(&p->d_chunks, (size_t)p->img_cap)) != RF_OK) return s;
   const size_t per_slot = (size_t)p->ncol * N * sizeof(float2);
   int slots = (int)std::min<size_t>(kTBudgetBytes / per_slot, (size_t)p->img_cap);
   if ((s = alloc_wave_scratch(p, slots)) != RF_OK) return s;
+  if ((s = alloc_ring(p, kDefaultRing)) != RF_OK) return s;
 
   // host->device staging of raw visibilities
   const size_t per_int = (size_t)p->nbl * p->nchan * p->npol * sizeof(float2);
@@ -833,6 +938,7 @@ SegmentGeom geom(const rf_plan* p, int nint) {
     g.idx32 = !p->wide_index && (uint64_t)p->nbl * p->nchan * pitch < (1ull << 32);
   }
   g.fp16 = (p->flags & RF_STORE_FP16) != 0;
+  g.tsplit = rf::col_split(p->npix);
   return g;
 }
 
@@ -897,11 +1003,25 @@ rf_status run_waves(rf_plan* p, int nint, const std::vector<Wave>& waves, int ni
   RF_TIMED(p->prof, K_WEIGHTS, st,
            rf::launch_weights(p->d_img_info, nimg_total, (p->flags & RF_EDGE_PARTIAL) != 0, g, p->tb,
                               (double)p->n_on, p->d_weight, st));
-  for (const Wave& w : waves) {
+  const bool fused = d_images == nullptr && &waves == &p->waves && use_fused(p);
+  for (size_t wi = 0; wi < waves.size(); ++wi) {
+    const Wave& w = waves[wi];
     const int ng = w.g_end - w.g_begin;
     const int ni = w.img_end - w.img_begin;
     RF_TIMED(p->prof, K_GRID_CELLS, st,
              rf::launch_grid_cells(g, p->tb, p->d_groups, w.g_begin, ng, p->d_cellbuf, st));
+    if (fused) {
+      const int2 wc = p->wave_chunks[wi];
+      RF_TIMED(p->prof, K_IMAGE_FUSED, st,
+               rf::launch_image_fused(g, p->tb, p->d_groups, w.g_begin, p->d_chunks + wc.x, wc.y - wc.x,
+                                      w.img_begin, p->d_cellbuf, p->d_Tring, p->ring, p->tmap_ring, p->d_colsq,
+                                      p->d_mean0, p->d_partials, p->d_fcount, p->d_err, st));
+      RF_TIMED(p->prof, K_FINALIZE, st,
+               rf::launch_finalize(g, p->d_partials, p->d_colsq, p->d_mean0, p->d_img_info, p->d_weight, ni,
+                                   w.img_begin, p->threshold, p->d_cands, p->d_ncand, p->img_cap, d_stats, st,
+                                   false));
+      continue;
+    }
     RF_TIMED(p->prof, K_GRID_COLFFT, st,
              rf::launch_colfft(g, p->tb, p->d_groups, w.g_begin, ng, w.img_begin, p->d_cellbuf, p->d_T,
                                p->d_colsq, p->d_mean0, st));
@@ -1054,6 +1174,9 @@ rf_status search_impl(rf_plan* p, const void* vis, int nint, void* stream, rf_ca
                               cudaMemcpyHostToDevice, st));
       RF_CUDA(cudaMemcpyAsync(p->d_groups, p->groups.data(), p->groups.size() * sizeof(Group),
                               cudaMemcpyHostToDevice, st));
+      if (!p->chunks.empty())
+        RF_CUDA(cudaMemcpyAsync(p->d_chunks, p->chunks.data(), p->chunks.size() * sizeof(rf::FusedChunk),
+                                cudaMemcpyHostToDevice, st));
     }
   }
   const int nimg = (int)p->img_info.size();
@@ -1081,7 +1204,7 @@ rf_status search_impl(rf_plan* p, const void* vis, int nint, void* stream, rf_ca
   RF_CUDA(cudaStreamSynchronize(st));
   if (kerr) {
     cudaMemset(p->d_err, 0, sizeof(int));
-    return fail(RF_ERR_TIMEOUT, "a row-pass tile copy did not complete within its wait limit");
+    return fail(RF_ERR_TIMEOUT, "a bounded device-side wait (a tile copy, or a fused-pass dependency) gave up");
   }
   ncand = std::min(ncand, p->img_cap);
   std::vector<DevCand> dc(ncand);
@@ -1736,6 +1859,27 @@ rf_status rf_plan_set_tuning(rf_plan* p, int32_t key, int64_t value) {
     p->drop_graph();  // captured launches carry the variant
     return RF_OK;
   }
+  if (key == RF_TUNE_FUSED) {
+    if (value != 0 && value != 1) return fail(RF_ERR_INVALID_ARG, "RF_TUNE_FUSED takes 0 or 1");
+    BusyGuard bg(&p->busy);
+    if (!bg.owned) return fail(RF_ERR_BUSY, "plan is in use by another call");
+    DeviceGuard dg(p->device);
+    p->fused = value != 0;
+    p->drop_graph();
+    return RF_OK;
+  }
+  if (key == RF_TUNE_RING) {
+    if (value < 2 || value > 8) return fail(RF_ERR_INVALID_ARG, "RF_TUNE_RING takes 2 .. 8");
+    if (p->host_only) return fail(RF_ERR_INVALID_ARG, "plan was created with RF_HOST_ONLY");
+    BusyGuard bg(&p->busy);
+    if (!bg.owned) return fail(RF_ERR_BUSY, "plan is in use by another call");
+    DeviceGuard dg(p->device);
+    if (p->chunk_images <= 0) {
+      p->ring = (int)value;
+      return RF_OK;
+    }
+    return alloc_ring(p, (int)value);
+  }
   if (key != RF_TUNE_WAVE_IMAGES) return fail(RF_ERR_INVALID_ARG, "unknown tuning key %d", key);
   if (p->host_only) return fail(RF_ERR_INVALID_ARG, "plan was created with RF_HOST_ONLY");
   if (value < p->shape.images_per_group || value > 32768)
@@ -1760,14 +1904,31 @@ rf_status rf_plan_autotune(rf_plan* p, const void* vis, int32_t nint, void* stre
   size_t free_b = 0, total_b = 0;
   RF_CUDA(cudaMemGetInfo(&free_b, &total_b));
   const size_t have = free_b / 2 + (size_t)p->slots_max * per_slot;  // the current scratch is reusable
-  std::vector<int> ladder;
-  for (int w : {256, 512, 1024, 2048, 4096, 8192}) {
-    const int wc = std::max(w, B);
-    if ((size_t)wc * per_slot > have) continue;
-    if (!ladder.empty() && ladder.back() >= nimg) break;
-    ladder.push_back(wc);
+  struct Cand {
+    int wave, graphs, fused, ring;
+  };
+  std::vector<Cand> cands;
+  auto fits = [&](int w) { return (size_t)std::max(w, B) * per_slot <= have; };
+  const bool can_fuse = p->chunk_images > 0 && !(p->flags & RF_NOISE_CLIPPED);
+  if (can_fuse) {
+    for (int w : {2048, 8192}) {
+      if (!fits(w)) continue;
+      for (int ring : {2, 3, 4}) cands.push_back({w, 1, 1, ring});
+      cands.push_back({w, 1, 0, p->ring});
+      if (w >= nimg) break;
+    }
+  } else {
+    for (int w : {256, 512, 1024, 2048, 4096, 8192}) {
+      const int wc = std::max(w, B);
+      if (!fits(wc)) continue;
+      if (!cands.empty() && cands.back().wave >= nimg) break;
+      cands.push_back({wc, 1, 0, p->ring});
+      cands.push_back({wc, 0, 0, p->ring});
+    }
   }
-  if (ladder.empty()) ladder.push_back(p->slots_max);
+  if (cands.empty()) cands.push_back({p->slots_max, p->use_graphs ? 1 : 0, p->fused ? 1 : 0, p->ring});
+  // timing search: every (DM, dt) limited to its first nint/4 integrations
+  const int span = nint >= 256 ? nint / 4 : 0;
   const bool prof_was = p->prof.on;
   p->prof.on = false;
   cudaEvent_t e0, e1;
@@ -1775,50 +1936,52 @@ rf_status rf_plan_autotune(rf_plan* p, const void* vis, int32_t nint, void* stre
   RF_CUDA(cudaEventCreate(&e1));
   std::vector<rf_candidate> scratch_out(1);
   float best_ms = 1e30f;
-  int best_w = p->slots_max, best_g = p->use_graphs ? 1 : 0, ntried = 0;
+  Cand best = cands[0];
+  int ntried = 0;
   rf_status s = RF_OK;
-  for (int w : ladder) {
-    for (int gmode = 1; gmode >= 0 && s == RF_OK; --gmode) {
-      {
-        BusyGuard bg(&p->busy);
-        if (!bg.owned) {
-          s = fail(RF_ERR_BUSY, "plan is in use by another call");
-          break;
-        }
-        if (p->slots_max != w) s = alloc_wave_scratch(p, w);
-        p->use_graphs = gmode != 0;
-        p->drop_graph();
-      }
-      if (s != RF_OK) break;
-      size_t n_out = 0;
-      rf_status r = search_impl(p, vis, nint, stream, scratch_out.data(), 0, &n_out, false, nullptr, 0, nullptr);
-      if (r != RF_OK && r != RF_ERR_CAPACITY) {
-        s = r;
+  for (const Cand& c : cands) {
+    {
+      BusyGuard bg(&p->busy);
+      if (!bg.owned) {
+        s = fail(RF_ERR_BUSY, "plan is in use by another call");
         break;
       }
-      cudaEventRecord(e0, st);
-      r = search_impl(p, vis, nint, stream, scratch_out.data(), 0, &n_out, false, nullptr, 0, nullptr);
-      cudaEventRecord(e1, st);
-      cudaEventSynchronize(e1);
-      if (r != RF_OK && r != RF_ERR_CAPACITY) {
-        s = r;
-        break;
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ntried < 16 && report) {
-        report->tried_wave_images[ntried] = w;
-        report->tried_graphs[ntried] = gmode;
-        report->tried_ms[ntried] = ms;
-      }
-      ++ntried;
-      if (ms < best_ms) {
-        best_ms = ms;
-        best_w = w;
-        best_g = gmode;
-      }
+      if (p->slots_max != c.wave) s = alloc_wave_scratch(p, c.wave);
+      if (s == RF_OK && c.fused && p->ring != c.ring) s = alloc_ring(p, c.ring);
+      p->use_graphs = c.graphs != 0;
+      p->fused = c.fused != 0;
+      p->drop_graph();
     }
     if (s != RF_OK) break;
+    size_t n_out = 0;
+    rf_status r =
+        search_impl(p, vis, nint, stream, scratch_out.data(), 0, &n_out, false, nullptr, 0, nullptr, span);
+    if (r != RF_OK && r != RF_ERR_CAPACITY) {
+      s = r;
+      break;
+    }
+    cudaEventRecord(e0, st);
+    r = search_impl(p, vis, nint, stream, scratch_out.data(), 0, &n_out, false, nullptr, 0, nullptr, span);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    if (r != RF_OK && r != RF_ERR_CAPACITY) {
+      s = r;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ntried < 16 && report) {
+      report->tried_wave_images[ntried] = c.wave;
+      report->tried_graphs[ntried] = c.graphs;
+      report->tried_fused[ntried] = c.fused;
+      report->tried_ring[ntried] = c.ring;
+      report->tried_ms[ntried] = ms;
+    }
+    ++ntried;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1826,16 +1989,17 @@ rf_status rf_plan_autotune(rf_plan* p, const void* vis, int32_t nint, void* stre
   if (s != RF_OK) return s;
   {
     BusyGuard bg(&p->busy);
-    if (p->slots_max != best_w) {
-      s = alloc_wave_scratch(p, best_w);
-      if (s != RF_OK) return s;
-    }
-    p->use_graphs = best_g != 0;
+    if (p->slots_max != best.wave && (s = alloc_wave_scratch(p, best.wave)) != RF_OK) return s;
+    if (best.fused && p->ring != best.ring && (s = alloc_ring(p, best.ring)) != RF_OK) return s;
+    p->use_graphs = best.graphs != 0;
+    p->fused = best.fused != 0;
     p->drop_graph();
   }
   if (report) {
-    report->best_wave_images = best_w;
-    report->best_graphs = best_g;
+    report->best_wave_images = best.wave;
+    report->best_graphs = best.graphs;
+    report->best_fused = best.fused;
+    report->best_ring = p->ring;
     report->ntried = std::min(ntried, 16);
   }
   return RF_OK;
@@ -1849,6 +2013,14 @@ rf_status rf_plan_get_tuning(const rf_plan* p, int32_t key, int64_t* value) {
   }
   if (key == RF_TUNE_WIDE_INDEX) {
     *value = p->wide_index ? 1 : 0;
+    return RF_OK;
+  }
+  if (key == RF_TUNE_FUSED) {
+    *value = p->fused ? 1 : 0;
+    return RF_OK;
+  }
+  if (key == RF_TUNE_RING) {
+    *value = p->ring;
     return RF_OK;
   }
   if (key != RF_TUNE_WAVE_IMAGES) return fail(RF_ERR_INVALID_ARG, "unknown tuning key %d", key);

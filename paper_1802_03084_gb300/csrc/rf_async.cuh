@@ -38,4 +38,26 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// Global-memory flags shared by the blocks of one persistent launch.
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// Orders this thread's generic-proxy global accesses before (and after)
+// async-proxy (tensor copy) accesses to global memory.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+// Bounded wait until *p >= target (acquire), polling with a short sleep;
+// gives up after `polls` polls, or at once when *abort is set.
+__device__ __forceinline__ bool wait_count(const int* p, int target, const int* abort, int polls = 1 << 22) {
+  for (int i = 0; i < polls; ++i) {
+    if (ld_acquire_gpu(p) >= target) return true;
+    if (ld_acquire_gpu(abort) != 0) return false;
+    __nanosleep(64);
+  }
+  return false;
+}
+
 }  // namespace rf

@@ -36,7 +36,16 @@ struct DevTables {
   const int32_t* cell_row;      // [ncells] row (iv mod N) of each cell
   const GridEntry* ent;         // [nent] sorted by (column, row)
   const int32_t* ongrid_chan;   // [nchan] on-grid baselines per channel
-  const float2* twiddle;        // [npix] exp(+2 pi i m / N)
+  const float2* twiddle;        // length-N FFT table (fft_twiddle_table(N)): [0, N) exp(+2 pi i m / N)
+  // twiddle table of the column pass's sub-transforms, fft_twiddle_table(L)
+  // with L = N / col_split(N) (the same table as `twiddle` when N <= 1024)
+  const float2* twiddle_col;
+  // runs of every imaged column: the column's cells at rows v1 + L v2 for one
+  // v1 (cells sort by (v mod L, v div L) within a column, so a run is
+  // consecutive); col_runs[col_run_ptr[col] + j] = (first cell << 4) | cells,
+  // the first cell counted within the column
+  const int32_t* col_run_ptr;   // [ncol + 1]
+  const int32_t* col_runs;
   // boxcar-resampled Stokes I per dt index s, phase-split: element (row, p, i)
   // at sdt_ptr[s] + row * dt * sdt_lp[s] + p * sdt_lp[s] + i holds
   // sum_{j < dt, i dt + p + j < nint} S[row][i dt + p + j]
@@ -53,6 +62,16 @@ struct Group {
   int32_t nimg;
   int32_t img0;  // index of the group's first image in the image list
   int32_t pad[3];
+};
+
+// One chunk of the fused imaging pass: nk consecutive images from image
+// kbase of group g (absolute group index), whose column-FFT output shares one
+// slot of the ring.
+struct FusedChunk {
+  int32_t g;
+  int32_t kbase;
+  int32_t nk;
+  int32_t pad;
 };
 
 // Tensor map of a column-FFT output buffer T[slot][u][N] (as FP32 pairs) for
@@ -146,7 +165,18 @@ struct SegmentGeom {
   bool partial;   // PARTIAL edge rule: a sample at or past nint is absent
   bool idx32;     // every sample index of every resampled series fits in 32 bits
   bool fp16;      // Stokes-I stored as half2
+  // Row order of the column-FFT output T[slot][u][i]: with tsplit = R > 1,
+  // index i = p L + k (L = N / R) holds image row y = R k + p (the column
+  // pass's R sub-transforms of length L, one per residue p of y mod R, are
+  // stored one after the other); tsplit <= 1: i = y.
+  int tsplit;
 };
+
+// Sub-transforms per column in the batched column pass: N <= 1024 is one
+// length-N transform; larger N are split R = N / 1024 ways along v (one
+// radix-R decimation-in-frequency step folded into the gather of the
+// column's cells), leaving R transforms of length 1024.
+constexpr int col_split(int n) { return n >= 2048 ? n / 1024 : 1; }
 
 // ---------------------------------------------------------------- launchers
 // All launchers return cudaSuccess or the launch error.
@@ -181,6 +211,20 @@ cudaError_t launch_grid_cells(const SegmentGeom& g, const DevTables& tb, const G
 cudaError_t launch_colfft(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin,
                           int ngroups, int img_base, const float2* cellbuf, float2* Tbuf, float* colsq,
                           float* mean0, cudaStream_t st);
+
+// Fused column + row pass (npix 1024 .. 4096) of the chunks [0, nchunks)
+// of one wave (chunks[] on the device, groups indexed absolutely, cellbuf
+// holding groups from g_begin): column FFTs into the ring Tring (ring slots
+// of fused_chunk_images(N) images, tensor map tm), row FFTs and statistics
+// into partials, Parseval sums into colsq/mean0 (slots relative to
+// img_base).  counters: 1 + 2 nchunks ints (zeroed here).  err: set when a
+// bounded wait gave up.
+cudaError_t launch_image_fused(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin,
+                               const FusedChunk* chunks, int nchunks, int img_base, const float2* cellbuf,
+                               float2* Tring, int ring, const TileMap& tm, float* colsq, float* mean0,
+                               StatPartial* partials, int* counters, int* err, cudaStream_t st);
+// Images per chunk of the fused pass (0: no fused pass at this size).
+int fused_chunk_images(int npix);
 
 // Clipping window of each of `nimg` slots for the clipped noise, in raw
 // pixel units (the image times 2W): clip[i] = {mean0[i], kClipSigmas *

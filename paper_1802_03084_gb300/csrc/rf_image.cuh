@@ -67,33 +67,149 @@ struct ImgCfg {
   static_assert(FftShape<N>::P2 == fft_pass2_radix(N), "twiddle table layout and FFT passes disagree");
 };
 
+// Launch shape of the batched column pass (k_colfft) per image side N: each
+// column is R = col_split(N) transforms of length L = N / R (TL threads of EL
+// values each); a round runs XA columns' transforms (one image each) at once.
+template <int N>
+struct ColCfg {
+  static constexpr int R = col_split(N);
+  static constexpr int L = N / R;
+  static constexpr int LOG2L = FftShape<L>::LOG2N;
+  static constexpr int TL = FftShape<L>::T;
+  static constexpr int EL = FftShape<L>::E;
+  static constexpr int THREADS = 256;
+  static constexpr int XA = cmin(THREADS / (R * TL), 32);       // images per round
+  static constexpr int PI = N >= 2048 ? 16 : 32;                // images whose cells are staged at once
+  static constexpr int STRIDE = fft_stride<L>();
+  // FFT buffers [XA][R][STRIDE]; per cell of the busiest column: the staged
+  // values (PI images), its row and (at most) one run
+  static constexpr int SMEM_FIXED = XA * R * STRIDE * 8;
+  static constexpr int SMEM_PER_CELL = PI * 8 + 4 + 4;
+  static_assert(TL <= 32, "column sub-transforms fit one warp");
+  static_assert(R <= 8, "at most eight sub-transforms per column");
+  static_assert((XA * R * STRIDE * 8) % 16 == 0, "staged cells start 16-byte aligned");
+};
+
+// Image row of index i of the column-FFT output (see SegmentGeom::tsplit).
+__device__ __forceinline__ int t_row(int i, int tsplit, int log2l) {
+  return tsplit > 1 ? ((i & ((1 << log2l) - 1)) * tsplit + (i >> log2l)) : i;
+}
+
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 
+// Column pass: the first-pass inputs of sub-transform p (of R) of staged
+// image kl, through the sub-transform's own buffer.  Its lanes zero the
+// buffer and scatter the column's runs into it: run j (cells at rows
+// v1 + L v2 for one v1) puts, for R > 1 with the decimation-in-frequency
+// step folded in,
+//   Y_p[v1] = w_N^(v1 p) sum_{v2 < R} H[v1 + L v2] w_R^(v2 p)
+// at row v1 (the run's cells in ascending v2, a fixed order; R = 1: the one
+// cell's value).  Only the sub-transform's lanes synchronise.  runs[j] =
+// (first cell << 4) | cells; cellv holds PI images per staged cell, 16-byte
+// chunks swizzled by the cell.  Not live: the buffer stays zero.
+template <int N, int PI>
+__device__ __forceinline__ void col_scatter(float2* buf, const int* __restrict__ runs, int nruns,
+                                            const float2* __restrict__ cellv, const int* __restrict__ crow, int kl,
+                                            bool live, const float2* __restrict__ twN, int t, int p, int xsub) {
+  using C = ColCfg<N>;
+  constexpr int CPC = PI > 1 ? PI / 2 : 1;
+  constexpr int L = C::L, R = C::R, TL = C::TL, STRIDE = C::STRIDE;
+  if constexpr (STRIDE % 2 == 0) {  // 16 bytes at a time (every buffer then starts 16-byte aligned)
+    float4* buf4 = reinterpret_cast<float4*>(buf);
+    for (int i = t; i < STRIDE / 2; i += TL) buf4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  } else {
+    for (int i = t; i < STRIDE; i += TL) buf[i] = make_float2(0.f, 0.f);
+  }
+  fft_sync<TL>(xsub);
+  if (live) {
+    const int kc = kl >> 1, ko = kl & 1;
+    for (int j = t; j < nruns; j += TL) {
+      const int m = runs[j];
+      const int c0 = m >> 4;
+      const int v1 = crow[c0] & (L - 1);
+      float2 a = cellv[c0 * PI + 2 * (kc ^ (c0 & (CPC - 1))) + ko];
+      if constexpr (R > 1) {
+        const int n = m & 15;
+        if (p > 0) {
+          int k = ((crow[c0] >> C::LOG2L) * p) & (R - 1);
+          if (k != 0) a = cmul(a, __ldg(twN + k * L));  // w_R^k = w_N^(k L)
+        }
+        for (int q = 1; q < n; ++q) {
+          const int c = c0 + q;
+          const float2 h = cellv[c * PI + 2 * (kc ^ (c & (CPC - 1))) + ko];
+          const int k = ((crow[c] >> C::LOG2L) * p) & (R - 1);
+          if (k == 0) {
+            a = cadd(a, h);
+          } else {
+            const float2 w = __ldg(twN + k * L);
+            a.x = fmaf(h.x, w.x, fmaf(-h.y, w.y, a.x));
+            a.y = fmaf(h.x, w.y, fmaf(h.y, w.x, a.y));
+          }
+        }
+        if (p > 0) a = cmul(a, __ldg(twN + ((v1 * p) & (N - 1))));  // w_N^(v1 p)
+      }
+      buf[padx(v1)] = a;
+    }
+  }
+  fft_sync<TL>(xsub);
+}
+
+// The length-L inverse FFT of the inputs col_scatter put in `buf`
+// (sub-transform xsub of the block), written to dst[0 .. L) if dst.
+template <int N>
+__device__ __forceinline__ void col_fft_store(float2* buf, const float2* __restrict__ twc, int t, int xsub,
+                                              float2* __restrict__ dst) {
+  using C = ColCfg<N>;
+  constexpr int L = C::L, TL = C::TL, EL = C::EL;
+  float2 v[EL];
+  fft_inverse_to_regs<L, true>(v, buf, twc, t, xsub);  // packed style (see rf_fft.cuh)
+  if (dst != nullptr) {
+    constexpr int LP = FftShape<L>::LAST_P;
+#pragma unroll
+    for (int m = 0; m < EL / LP; ++m)
+#pragma unroll
+      for (int q = 0; q < LP; ++q) dst[fft_out_index<L>(t, m, q)] = v[m * LP + dft_perm<LP>(q)];
+  }
+  fft_sync<TL>(xsub);  // the buffer is reused by the next transform
+}
+
 // Pass A2: the column FFTs of one group (up to 32 consecutive t' of a
 // trial) and one half-plane column u.  The column's cell sums for the
 // group's images (cellbuf row per cell, 32 images) are copied to shared
-// memory with cp.async (16-byte chunks XOR-swizzled by cell); then, XA
-// images at a time, each transform zeroes its buffer, scatters its image's
-// cells to rows iv mod N and inverse-FFTs the column along v.  Transforms
-// synchronise only among their own threads.
+// memory with cp.async (16-byte chunks XOR-swizzled by cell), PI images at a
+// time.  Each column is R = col_split(N) sub-transforms of length L = N/R.
+// In rounds of XA images, each sub-transform zeroes its own buffer and
+// scatters the column's runs into it (col_scatter), which for R > 1 folds in
+// one decimation-in-frequency step: sub-transform p takes
+//   Y_p[v1] = w_N^(v1 p) sum_{v2 < R} H[v1 + L v2] w_R^(v2 p),
+// and its length-L inverse FFT is column output y = R k + p at k, stored at
+// T[slot][u][p L + k] (see SegmentGeom::tsplit).  A sub-transform
+// synchronises only its own lanes (one warp or part of one), so there is no
+// third FFT pass and no barrier across warps for N >= 2048.
 template <int N>
-__global__ void __launch_bounds__(ImgCfg<N>::THREADS_A, 2)
+__global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
     k_colfft(SegmentGeom g, DevTables tb, const Group* __restrict__ groups, int g_begin, int img_base,
              const float2* __restrict__ cellbuf, float2* __restrict__ Tbuf, float* __restrict__ colsq,
              float* __restrict__ mean0) {
-  using K = ImgCfg<N>;
-  constexpr int PI = K::PART_IMAGES;  // images staged at a time
-  constexpr int CPC = PI / 2;         // 16-byte chunks per cell row
+  using C = ColCfg<N>;
+  constexpr int PI = C::PI;          // images staged at a time
+  constexpr int CPC = PI / 2;        // 16-byte chunks per cell row
+  constexpr int L = C::L, R = C::R, TL = C::TL;
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* fbuf = reinterpret_cast<float2*>(smraw);                     // [XA][STRIDE]
-  float2* cellv = fbuf + K::XA * K::STRIDE;                             // [max_cells][PI], swizzled
-  int* crow = reinterpret_cast<int*>(cellv + (size_t)g.max_cells * PI);  // [max_cells]
+  float2* fbuf = reinterpret_cast<float2*>(smraw);                       // [XA][R][STRIDE]
+  float2* cellv = reinterpret_cast<float2*>(fbuf + C::XA * R * C::STRIDE);  // [max_cells][PI], swizzled
+  int* crow = reinterpret_cast<int*>(cellv + (size_t)g.max_cells * PI);    // [max_cells]
+  int* runs = crow + g.max_cells;                                           // [max_cells]
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const Group gr = groups[g_begin + blockIdx.x];
@@ -101,20 +217,26 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_A, 2)
   const int cell0 = tb.col_cell_ptr[col];
   const int ncells = tb.col_cell_ptr[col + 1] - cell0;
   const float2* __restrict__ src = cellbuf + ((size_t)blockIdx.x * g.ncells + cell0) * 32;
-  for (int c = tid; c < ncells; c += K::THREADS_A) crow[c] = tb.cell_row[cell0 + c];
-  const int xf = tid / K::T;
-  const int t = tid - xf * K::T;
-  float2* buf = fbuf + xf * K::STRIDE;
+  // the column's cell rows and runs; visible after the first staging wait
+  // and barrier below
+  const int run0 = tb.col_run_ptr[col];
+  const int nruns = tb.col_run_ptr[col + 1] - run0;
+  for (int c = tid; c < ncells; c += C::THREADS) crow[c] = tb.cell_row[cell0 + c];
+  for (int j = tid; j < nruns; j += C::THREADS) runs[j] = tb.col_runs[run0 + j];
+  const int xf = tid / (R * TL);          // image of the round
+  const int p = (tid / TL) % R;           // sub-transform: output rows y = p mod R
+  const int t = tid % TL;
+  float2* buf = fbuf + (xf * R + p) * C::STRIDE;
   for (int kbase = 0; kbase < gr.nimg; kbase += PI) {
     if (kbase > 0) __syncthreads();  // the previous part's cells are consumed
-    for (int i = tid; i < ncells * CPC; i += K::THREADS_A) {
+    for (int i = tid; i < ncells * CPC; i += C::THREADS) {
       const int c = i / CPC;
       const int j = i - c * CPC;
       cp_async16(cellv + c * PI + 2 * (j ^ (c & (CPC - 1))), src + c * 32 + kbase + 2 * j);
     }
     cp_async_commit();
     cp_async_wait_all();
-    __syncthreads();
+    __syncthreads();  // also orders the row map before its first use
     const int nk = min(PI, gr.nimg - kbase);
 
     // Parseval: the image's sum of squares is N^2 / (4 W^2) times the sum
@@ -123,7 +245,7 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_A, 2)
     // |H|^2 of the column's cells for some of the images (FP32, fixed order).
     {
       const float wcol = col == 0 ? 1.f : 2.f;
-      for (int kl = tid >> 5; kl < nk; kl += K::THREADS_A / 32) {
+      for (int kl = tid >> 5; kl < nk; kl += C::THREADS / 32) {
         float acc = 0.f;
         for (int c = lane; c < ncells; c += 32) {
           const float2 h = cellv[c * PI + 2 * ((kl >> 1) ^ (c & (CPC - 1))) + (kl & 1)];
@@ -134,41 +256,20 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_A, 2)
         if (lane == 0) {
           const size_t slot = (size_t)(gr.img0 + kbase + kl - img_base);
           colsq[slot * g.ncol + col] = wcol * acc;
-          if (col == 0) mean0[slot] = (ncells > 0 && crow[0] == 0) ? cellv[kl].x : 0.f;  // cell 0 unswizzled
+          // row 0 sorts first in column 0; cell 0's first chunk is unswizzled
+          if (col == 0) mean0[slot] = (ncells > 0 && crow[0] == 0) ? cellv[kl].x : 0.f;
         }
       }
     }
 
-    if (xf < K::XA) {
-      const int nrounds = (nk + K::XA - 1) / K::XA;
+    if (xf < C::XA) {
+      const int nrounds = (nk + C::XA - 1) / C::XA;
       for (int rd = 0; rd < nrounds; ++rd) {
-        const int kl = rd * K::XA + xf;
-        const int kc = kl >> 1;
-        const int ko = kl & 1;
-        // zero the transform's buffer, 16 bytes at a time where STRIDE is
-        // even (then every transform's buffer starts 16-byte aligned)
-        if constexpr (K::STRIDE % 2 == 0) {
-          float4* buf4 = reinterpret_cast<float4*>(buf);
-          for (int i = t; i < K::STRIDE / 2; i += K::T) buf4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        } else {
-          for (int i = t; i < K::STRIDE; i += K::T) buf[i] = make_float2(0.f, 0.f);
-        }
-        fft_sync<K::T>(xf);
-        if (kl < nk)
-          for (int c = t; c < ncells; c += K::T) buf[padx(crow[c])] = cellv[c * PI + 2 * (kc ^ (c & (CPC - 1))) + ko];
-        fft_sync<K::T>(xf);
-        float2 v[K::E];
-        fft_inverse_to_regs<N, true>(v, buf, tb.twiddle, t, xf);  // packed style (see rf_fft.cuh)
-        if (kl < nk) {
-          const size_t slot = (size_t)(gr.img0 + kbase + kl - img_base);
-          float2* dst = Tbuf + (slot * g.ncol + col) * N;
-          constexpr int LP = FftShape<N>::LAST_P;
-#pragma unroll
-          for (int m = 0; m < K::E / LP; ++m)
-#pragma unroll
-            for (int q = 0; q < LP; ++q) dst[fft_out_index<N>(t, m, q)] = v[m * LP + dft_perm<LP>(q)];
-        }
-        fft_sync<K::T>(xf);
+        const int kl = rd * C::XA + xf;
+        const bool live = kl < nk;
+        float2* dst = live ? Tbuf + ((size_t)(gr.img0 + kbase + kl - img_base) * g.ncol + col) * N + p * L : nullptr;
+        col_scatter<N, PI>(buf, runs, nruns, cellv, crow, kl, live, tb.twiddle, t, p, xf * R + p);
+        col_fft_store<N>(buf, tb.twiddle_col, t, xf * R + p, dst);
       }
     }
   }
@@ -178,6 +279,184 @@ __device__ __forceinline__ void max_merge(float& m, int& i, float m2, int i2) {
   if (m2 > m || (m2 == m && i2 < i)) {
     m = m2;
     i = i2;
+  }
+}
+
+// Row pass: the first-pass inputs of row pair xf of the item whose tile
+// (T rows y0 .. y0 + RB of every imaged column u, swizzled 16-byte chunks)
+// is in shared memory.
+template <int N>
+__device__ __forceinline__ void row_zbuild(float2 (&v)[ImgCfg<N>::E], const float4* __restrict__ tile, int t,
+                                           int xf, int ncol) {
+  using K = ImgCfg<N>;
+  // first-pass inputs Z[u], u = t + r T: a + i b for 0 < u < ncol, the
+  // Hermitian mirror conj(a) + i conj(b) for N - u < ncol, real parts at
+  // u = 0, zero elsewhere (columns beyond iu_max are empty).  N/2 = 16 T,
+  // so r < 16 can only be a direct column and r >= 16 only a mirror.
+  if constexpr (K::E == 32 && K::T % (K::CH << K::SWZ_SH) == 0) {
+    // the swizzle term of u = t + r T (or N - t - r T) is that of t (N - t)
+    const int rd_end = ncol > t ? (ncol - t + K::T - 1) / K::T : 0;
+    const int rm_beg = (N - ncol - t) / K::T + 1;
+    const float4* pd = tile + t * K::CH + K::swz(t, xf);
+    const float4* pm = tile + (size_t)(N - t) * K::CH + K::swz(N - t, xf);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < rd_end) ab = pd[r * K::T * K::CH];
+      v[r] = (r == 0 && t == 0) ? make_float2(ab.x, ab.z) : make_float2(ab.x - ab.w, ab.y + ab.z);
+    }
+#pragma unroll
+    for (int r = 16; r < 32; ++r) {
+      float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r >= rm_beg) ab = pm[-r * K::T * K::CH];
+      v[r] = make_float2(ab.x + ab.w, ab.z - ab.y);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < K::E; ++r) {
+      const int u = t + r * K::T;
+      float2 z = make_float2(0.f, 0.f);
+      if (u < ncol) {
+        const float4 ab = tile[u * K::CH + K::swz(u, xf)];
+        z = (u == 0) ? make_float2(ab.x, ab.z) : make_float2(ab.x - ab.w, ab.y + ab.z);
+      } else if (N - u < ncol) {
+        const int uu = N - u;
+        const float4 ab = tile[uu * K::CH + K::swz(uu, xf)];
+        z = make_float2(ab.x + ab.w, ab.z - ab.y);
+      }
+      v[r] = z;
+    }
+  }
+}
+
+// Row pass, after row_zbuild: the inverse FFT of the row pair (T rows
+// i = y0 + 2 xf and i + 1, image rows t_row of them) in `buf`, the pair's
+// max pixel with its lowest index (and under CLIP the kept-pixel sums), one
+// StatPartial per warp of the transform, and the two image rows if `images`.
+template <int N, bool CLIP>
+__device__ __forceinline__ void row_finish(float2 (&v)[ImgCfg<N>::E], float2* buf, const float2* __restrict__ tw,
+                                           int t, int xf, int slot, int y0, int tsplit, int log2l,
+                                           const double* __restrict__ weight, int img_base,
+                                           float* __restrict__ images, StatPartial* __restrict__ partials,
+                                           const float2* __restrict__ clip) {
+  using K = ImgCfg<N>;
+  fft_inverse_from_regs<N>(v, buf, tw, t, xf);
+
+  // per-row-pair statistics: the max pixel and its lowest index (the
+  // noise comes from the grid by Parseval's identity, see k_colfft).  The
+  // pair is T rows i, i + 1, image rows ya < yb (adjacent unless the
+  // column pass split its transforms: then R apart)
+  const int i = y0 + 2 * xf;
+  const int ya = t_row(i, tsplit, log2l);
+  const int yb = t_row(i + 1, tsplit, log2l);
+  constexpr int LP = FftShape<N>::LAST_P;
+  constexpr int EM = K::E / LP;
+  if (images != nullptr) {
+    const double W = weight[img_base + slot];
+    const float scale = W > 0.0 ? (float)(0.5 / W) : 0.f;
+    float* ima = images + ((size_t)slot * N + ya) * N;
+    float* imb = images + ((size_t)slot * N + yb) * N;
+#pragma unroll
+    for (int m = 0; m < EM; ++m)
+#pragma unroll
+      for (int q = 0; q < LP; ++q) {
+        const float2 z = v[m * LP + dft_perm<LP>(q)];
+        const int o = fft_out_index<N>(t, m, q);
+        ima[o] = z.x * scale;
+        imb[o] = z.y * scale;
+      }
+  }
+  // max of row y (real parts) and of row y + 1 (imaginary parts), four
+  // independent chains each
+  float mxa[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
+  float mya[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
+#pragma unroll
+  for (int e = 0; e < K::E; e += 2) {
+    mxa[(e >> 1) & 3] = fmax3f(mxa[(e >> 1) & 3], v[e].x, v[e + 1].x);
+    mya[(e >> 1) & 3] = fmax3f(mya[(e >> 1) & 3], v[e].y, v[e + 1].y);
+  }
+  const float mx = fmaxf(fmaxf(mxa[0], mxa[1]), fmaxf(mxa[2], mxa[3]));
+  const float my = fmaxf(fmaxf(mya[0], mya[1]), fmaxf(mya[2], mya[3]));
+  const float lmax = fmaxf(mx, my);
+  // reduce over the transform's T threads (a warp, a part of one, or
+  // several warps joined through shared memory)
+  constexpr int WL = K::T < 32 ? K::T : 32;
+  constexpr unsigned MASK = 0xffffffffu;
+  float wmax = lmax;
+#pragma unroll
+  for (int off = WL / 2; off > 0; off >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(MASK, wmax, off));
+  // a lane holding the maximum finds its lowest index: row ya comes before
+  // row yb, and within a row the lane's outputs ascend with (q, m)
+  int best = INT_MAX;
+  if (lmax == wmax) {
+    if (mx == wmax) {
+#pragma unroll
+      for (int q = 0; q < LP; ++q)
+#pragma unroll
+        for (int m = 0; m < EM; ++m)
+          if (v[m * LP + dft_perm<LP>(q)].x == wmax) {
+            best = ya * N + fft_out_index<N>(t, m, q);
+            goto found;
+          }
+    } else {
+#pragma unroll
+      for (int q = 0; q < LP; ++q)
+#pragma unroll
+        for (int m = 0; m < EM; ++m)
+          if (v[m * LP + dft_perm<LP>(q)].y == wmax) {
+            best = yb * N + fft_out_index<N>(t, m, q);
+            goto found;
+          }
+    }
+  found:;
+  }
+#pragma unroll
+  for (int off = WL / 2; off > 0; off >>= 1) best = min(best, __shfl_xor_sync(MASK, best, off));
+  // clipped noise: sums of the kept pixels' deviations from mean0, rows y
+  // and y + 1 in separate chains
+  float s1 = 0.f, s2 = 0.f;
+  int cn = 0;
+  if constexpr (CLIP) {
+    const float2 cw = clip[slot];
+    float ax = 0.f, qx = 0.f, ay = 0.f, qy = 0.f;
+    int nx = 0, ny = 0;
+#pragma unroll
+    for (int e = 0; e < K::E; ++e) {
+      const float dx = v[e].x - cw.x;
+      const float dy = v[e].y - cw.x;
+      if (fabsf(dx) <= cw.y) {
+        ax += dx;
+        qx = fmaf(dx, dx, qx);
+        ++nx;
+      }
+      if (fabsf(dy) <= cw.y) {
+        ay += dy;
+        qy = fmaf(dy, dy, qy);
+        ++ny;
+      }
+    }
+    s1 = ax + ay;
+    s2 = qx + qy;
+    cn = nx + ny;
+#pragma unroll
+    for (int off = WL / 2; off > 0; off >>= 1) {
+      s1 += __shfl_xor_sync(MASK, s1, off);
+      s2 += __shfl_xor_sync(MASK, s2, off);
+      cn += __shfl_xor_sync(MASK, cn, off);
+    }
+  }
+  // one partial per warp of the transform (WPT of them when a transform
+  // spans several warps; the finalisation combines them): no barrier
+  if ((t & 31) == 0) {
+    constexpr int WPT = K::T > 32 ? K::T / 32 : 1;
+    StatPartial sp;
+    sp.sum = s1;
+    sp.sumsq = s2;
+    sp.kept = cn;
+    sp.max = wmax;
+    sp.idx = best;
+    sp.pad = 0;
+    partials[(size_t)slot * K::PARTIALS + ((y0 >> 1) + xf) * WPT + (t >> 5)] = sp;  // by T row pair
   }
 }
 
@@ -219,6 +498,7 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
   const int nitems = nimg * nrb;
   const int xf = tid / K::T;
   const int t = tid - xf * K::T;
+  const int log2l = FftShape<N>::LOG2N - (g.tsplit > 1 ? __ffs(g.tsplit) - 1 : 0);
   const bool use_tma = K::TILE_TMA && tma_boxes > 0;
   unsigned phase = 0;
   if (use_tma) {
@@ -268,161 +548,285 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     }
     const int slot = item / nrb;
     const int y0 = (item - slot * nrb) * K::RB;
-    // first-pass inputs Z[u], u = t + r T: a + i b for 0 < u < ncol, the
-    // Hermitian mirror conj(a) + i conj(b) for N - u < ncol, real parts at
-    // u = 0, zero elsewhere (columns beyond iu_max are empty).  N/2 = 16 T,
-    // so r < 16 can only be a direct column and r >= 16 only a mirror.
     float2 v[K::E];
-    if constexpr (K::E == 32 && K::T % (K::CH << K::SWZ_SH) == 0) {
-      // the swizzle term of u = t + r T (or N - t - r T) is that of t (N - t)
-      const int rd_end = ncol > t ? (ncol - t + K::T - 1) / K::T : 0;
-      const int rm_beg = (N - ncol - t) / K::T + 1;
-      const float4* pd = tile + t * K::CH + K::swz(t, xf);
-      const float4* pm = tile + (size_t)(N - t) * K::CH + K::swz(N - t, xf);
-#pragma unroll
-      for (int r = 0; r < 16; ++r) {
-        float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (r < rd_end) ab = pd[r * K::T * K::CH];
-        v[r] = (r == 0 && t == 0) ? make_float2(ab.x, ab.z) : make_float2(ab.x - ab.w, ab.y + ab.z);
-      }
-#pragma unroll
-      for (int r = 16; r < 32; ++r) {
-        float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (r >= rm_beg) ab = pm[-r * K::T * K::CH];
-        v[r] = make_float2(ab.x + ab.w, ab.z - ab.y);
-      }
-    } else {
-#pragma unroll
-      for (int r = 0; r < K::E; ++r) {
-        const int u = t + r * K::T;
-        float2 z = make_float2(0.f, 0.f);
-        if (u < ncol) {
-          const float4 ab = tile[u * K::CH + K::swz(u, xf)];
-          z = (u == 0) ? make_float2(ab.x, ab.z) : make_float2(ab.x - ab.w, ab.y + ab.z);
-        } else if (N - u < ncol) {
-          const int uu = N - u;
-          const float4 ab = tile[uu * K::CH + K::swz(uu, xf)];
-          z = make_float2(ab.x + ab.w, ab.z - ab.y);
-        }
-        v[r] = z;
-      }
-    }
+    row_zbuild<N>(v, tile, t, xf, ncol);
     __syncthreads();  // tile consumed: prefetch the next item
     if (item + (int)gridDim.x < nitems) fetch(item + gridDim.x);
-    fft_inverse_from_regs<N>(v, fbuf + xf * K::STRIDE, tb.twiddle, t, xf);
+    row_finish<N, CLIP>(v, fbuf + xf * K::STRIDE, tb.twiddle, t, xf, slot, y0, g.tsplit, log2l,
+                        images != nullptr ? weight : nullptr, img_base, images, partials, clip);
+  }
+}
 
-    // per-row-pair statistics: the max pixel and its lowest index (the
-    // noise comes from the grid by Parseval's identity, see k_colfft)
-    const int y = y0 + 2 * xf;
-    constexpr int LP = FftShape<N>::LAST_P;
-    constexpr int EM = K::E / LP;
-    if (images != nullptr) {
-      const double W = weight[img_base + slot];
-      const float scale = W > 0.0 ? (float)(0.5 / W) : 0.f;
-      float* im = images + ((size_t)slot * N + y) * N;
-#pragma unroll
-      for (int m = 0; m < EM; ++m)
-#pragma unroll
-        for (int q = 0; q < LP; ++q) {
-          const float2 z = v[m * LP + dft_perm<LP>(q)];
-          const int o = fft_out_index<N>(t, m, q);
-          im[o] = z.x * scale;
-          im[N + o] = z.y * scale;
-        }
+// ------------------------------------------------------- fused imaging pass
+// Launch shape of the fused column + row pass (N = 1024 .. 4096): one block
+// shape serves both roles; a chunk is CI = ColCfg<N>::XA images, one column
+// round.
+template <int N>
+struct FusedCfg {
+  using K = ImgCfg<N>;
+  using C = ColCfg<N>;
+  static constexpr int CI = C::XA;                    // images per chunk
+  static constexpr int NRB = N / K::RB;               // row items per image
+  static constexpr int FB = cmax(K::XB * K::STRIDE, C::XA * C::R * C::STRIDE);  // float2 of FFT buffers
+  static constexpr int THREADS = K::THREADS_B;
+  static_assert(K::THREADS_B == C::THREADS, "one block shape for both roles");
+  static_assert(K::TILE_TMA && CI >= 2, "fused pass: N = 1024 .. 4096");
+};
+
+// The fused imaging pass of one wave: the column FFTs and the row FFTs with
+// statistics in one persistent launch, the column-FFT output staying in an
+// L2-resident ring of `ring` chunk slots instead of a wave-sized buffer in
+// HBM.  Blocks take work items in order from one counter (two ahead of the
+// item in hand, so the counter's latency is hidden).  Step s holds the ncol
+// column items of chunk s (u = 0 .. ncol-1: stage the column's row map,
+// rows and cells for the chunk's images, Parseval sums, one round of column
+// transforms, store into ring slot s mod ring), then the row items of chunk
+// s - 1 (image, block of RB rows: tensor-copy tile, row FFTs, statistics,
+// as in k_rowfft_stats).  A row item waits until every warp of its chunk's
+// ncol column items has stored; a warp of a column item of chunk s >= ring
+// waits, before it stores, until the row items of chunk s - ring have read
+// the slot.  Every wait is on items taken from the counter earlier, and a
+// block finishes its item before it starts the next one it took, so the
+// smallest unfinished item always has its inputs: the order cannot
+// deadlock.  Each wait is bounded; one that gives up sets *err (the other
+// blocks then stop at their next wait or item) and the block leaves after
+// its copies in flight have landed.  The staging area (a row item's tile, or
+// a column item's map, rows and cells) is filled for the next item as soon
+// as the current one has read it.
+// counters: [0] work counter, [1 + c] warps of chunk c's column items that
+// stored, [1 + nchunks + c] row items that read chunk c's slot; zero at launch.
+template <int N>
+__global__ void __launch_bounds__(FusedCfg<N>::THREADS, 2)
+    k_image_fused(SegmentGeom g, DevTables tb, const Group* __restrict__ groups, int g_begin,
+                  const FusedChunk* __restrict__ chunks, int nchunks, int img_base,
+                  const float2* __restrict__ cellbuf, float2* __restrict__ Tring, int ring,
+                  float* __restrict__ colsq, float* __restrict__ mean0, StatPartial* __restrict__ partials,
+                  const __grid_constant__ CUtensorMap tmap, int tma_boxes, int tma_rows, int* __restrict__ counters,
+                  int* __restrict__ err) {
+  using K = ImgCfg<N>;
+  using C = ColCfg<N>;
+  using F = FusedCfg<N>;
+  constexpr int CI = F::CI;
+  constexpr int CPC = CI / 2;       // 16-byte chunks per staged cell row
+  constexpr int NRB = F::NRB;
+  constexpr int WPB = F::THREADS / 32;
+  constexpr int L = C::L, R = C::R, TL = C::TL;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* fbuf = reinterpret_cast<float2*>(smraw);
+  unsigned char* st0 = smraw + F::FB * 8;
+  st0 += (1024u - (smem_u32(st0) & 1023u)) & 1023u;  // swizzle atom alignment of the tile
+  float4* tile = reinterpret_cast<float4*>(st0);                           // row role: [rows][CH]
+  float2* cellv = reinterpret_cast<float2*>(st0);                          // column role: [max_cells][CI]
+  int* crow = reinterpret_cast<int*>(cellv + (size_t)g.max_cells * CI);    // [max_cells]
+  int* runs = crow + g.max_cells;                                           // [max_cells]
+  __shared__ __align__(8) unsigned long long tbar;
+  __shared__ int s_q;     // the item after next
+  __shared__ int s_fail;  // a wait gave up, or another block reported one
+  __shared__ int s_pf;    // the next item's tile copy was issued
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int ncol = g.ncol;
+  const int ips = ncol + CI * NRB;  // items per step
+  const long total = (long)(nchunks + 1) * ips;
+  int* const work = counters;
+  int* const colcnt = counters + 1;
+  int* const rowcnt = counters + 1 + nchunks;
+  const int log2l = FftShape<N>::LOG2N - (g.tsplit > 1 ? __ffs(g.tsplit) - 1 : 0);
+  const unsigned tile_bytes = (unsigned)(tma_boxes * tma_rows * K::CH * 16);
+  // roles' thread layouts
+  const int xfb = tid / K::T, tb_ = tid - xfb * K::T;                  // row role
+  const int xfa = tid / (R * TL), pa = (tid / TL) % R, ta = tid % TL;  // column role
+
+  // item q's kind: 0 none, 1 column (chunk c, column a), 2 row (chunk c, image a, block b)
+  auto decode = [&](long qq, int& c, int& a, int& b) -> int {
+    if (qq >= total) return 0;
+    const int st = (int)(qq / ips), o = (int)(qq - (long)st * ips);
+    if (o < ncol) {
+      c = st;
+      a = o;
+      return st < nchunks ? 1 : 0;
     }
-    // max of row y (real parts) and of row y + 1 (imaginary parts), four
-    // independent chains each
-    float mxa[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
-    float mya[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
-#pragma unroll
-    for (int e = 0; e < K::E; e += 2) {
-      mxa[(e >> 1) & 3] = fmax3f(mxa[(e >> 1) & 3], v[e].x, v[e + 1].x);
-      mya[(e >> 1) & 3] = fmax3f(mya[(e >> 1) & 3], v[e].y, v[e + 1].y);
+    c = st - 1;
+    const int j = o - ncol;
+    a = j / NRB;
+    b = j - a * NRB;
+    return (c >= 0 && c < nchunks && a < chunks[c].nk) ? 2 : 0;
+  };
+  auto ring_slot = [&](int c, int jj) { return (c % ring) * CI + jj; };
+  auto issue_tile = [&](int c, int jj, int rb) {  // thread 0
+    fence_proxy_async_global();
+    mbar_expect_tx(&tbar, tile_bytes);
+    for (int bx = 0; bx < tma_boxes; ++bx)
+      tma_load_3d(tile + (size_t)bx * tma_rows * K::CH, &tmap, 2 * rb * K::RB, bx * tma_rows, ring_slot(c, jj),
+                  &tbar);
+  };
+  auto issue_stage = [&](int c, int u) {  // all threads: the column's rows, runs and cells
+    const FusedChunk ch = chunks[c];
+    const int cell0 = tb.col_cell_ptr[u];
+    const int nc = tb.col_cell_ptr[u + 1] - cell0;
+    const int run0 = tb.col_run_ptr[u];
+    const int nr = tb.col_run_ptr[u + 1] - run0;
+    for (int cc = tid; cc < nc; cc += F::THREADS) cp_async4(crow + cc, tb.cell_row + cell0 + cc);
+    for (int j = tid; j < nr; j += F::THREADS) cp_async4(runs + j, tb.col_runs + run0 + j);
+    const float2* src = cellbuf + ((size_t)(ch.g - g_begin) * g.ncells + cell0) * 32 + ch.kbase;
+    for (int i = tid; i < nc * CPC; i += F::THREADS) {
+      const int cc = i / CPC;
+      const int j = i - cc * CPC;
+      cp_async16(cellv + cc * CI + 2 * (j ^ (cc & (CPC - 1))), src + cc * 32 + 2 * j);
     }
-    const float mx = fmaxf(fmaxf(mxa[0], mxa[1]), fmaxf(mxa[2], mxa[3]));
-    const float my = fmaxf(fmaxf(mya[0], mya[1]), fmaxf(mya[2], mya[3]));
-    const float lmax = fmaxf(mx, my);
-    // reduce over the transform's T threads (a warp, a part of one, or
-    // several warps joined through shared memory)
-    constexpr int WL = K::T < 32 ? K::T : 32;
-    constexpr unsigned MASK = 0xffffffffu;
-    float wmax = lmax;
-#pragma unroll
-    for (int off = WL / 2; off > 0; off >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(MASK, wmax, off));
-    // a lane holding the maximum finds its lowest index: row y comes before
-    // row y + 1, and within a row the lane's outputs ascend with (q, m)
-    int best = INT_MAX;
-    if (lmax == wmax) {
-      if (mx == wmax) {
-#pragma unroll
-        for (int q = 0; q < LP; ++q)
-#pragma unroll
-          for (int m = 0; m < EM; ++m)
-            if (v[m * LP + dft_perm<LP>(q)].x == wmax) {
-              best = y * N + fft_out_index<N>(t, m, q);
-              goto found;
-            }
-      } else {
-#pragma unroll
-        for (int q = 0; q < LP; ++q)
-#pragma unroll
-          for (int m = 0; m < EM; ++m)
-            if (v[m * LP + dft_perm<LP>(q)].y == wmax) {
-              best = (y + 1) * N + fft_out_index<N>(t, m, q);
-              goto found;
-            }
+    cp_async_commit();
+  };
+  // fill the staging area for item qn after the current item has read it:
+  // a column item's stage (all threads), or a row item's tile if its chunk is
+  // complete (thread 0; *pf tells)
+  auto prefetch = [&](long qn, bool& stage_ready, int& pf) {
+    int c2 = 0, a2 = 0, b2 = 0;
+    const int k2 = decode(qn, c2, a2, b2);
+    stage_ready = false;
+    if (k2 == 2) {
+      if (tid == 0 && ld_acquire_gpu(colcnt + c2) >= ncol * WPB) {
+        issue_tile(c2, a2, b2);
+        pf = 1;
       }
-    found:;
+    } else if (k2 == 1) {
+      issue_stage(c2, a2);
+      stage_ready = true;
     }
-#pragma unroll
-    for (int off = WL / 2; off > 0; off >>= 1) best = min(best, __shfl_xor_sync(MASK, best, off));
-    // clipped noise: sums of the kept pixels' deviations from mean0, rows y
-    // and y + 1 in separate chains
-    float s1 = 0.f, s2 = 0.f;
-    int cn = 0;
-    if constexpr (CLIP) {
-      const float2 cw = clip[slot];
-      float ax = 0.f, qx = 0.f, ay = 0.f, qy = 0.f;
-      int nx = 0, ny = 0;
-#pragma unroll
-      for (int e = 0; e < K::E; ++e) {
-        const float dx = v[e].x - cw.x;
-        const float dy = v[e].y - cw.x;
-        if (fabsf(dx) <= cw.y) {
-          ax += dx;
-          qx = fmaf(dx, dx, qx);
-          ++nx;
+  };
+
+  if (tid == 0) {
+    mbar_init(&tbar, 1);
+    s_fail = 0;
+    s_pf = 0;
+    s_q = atomicAdd(work, 1);
+  }
+  __syncthreads();
+  long q = s_q;
+  __syncthreads();
+  if (tid == 0) s_q = atomicAdd(work, 1);
+  __syncthreads();
+  long qn = s_q;
+  unsigned phase = 0;
+  bool tile_ready = false;   // a tile copy for item q is in flight
+  bool stage_ready = false;  // item q's column stage is in flight (cp.async)
+
+  while (q < total) {
+    int qf = 0;
+    if (tid == 0) qf = atomicAdd(work, 1);  // the item after next, used at the item's end
+    int pf = 0;                              // thread 0: a tile copy for item qn was issued
+    bool next_stage = false;
+    int c = 0, a = 0, b = 0;
+    const int kind = decode(q, c, a, b);
+    if (kind == 2) {
+      // ------------------------------------------------------------ row item
+      if (!tile_ready) {
+        bool bad = false;
+        if (tid == 0) {
+          if (wait_count(colcnt + c, ncol * WPB, err)) issue_tile(c, a, b);
+          else bad = true;
         }
-        if (fabsf(dy) <= cw.y) {
-          ay += dy;
-          qy = fmaf(dy, dy, qy);
-          ++ny;
+        if (__syncthreads_or(bad)) {
+          if (tid == 0) atomicExch(err, 1);
+          cp_async_wait_all();
+          __syncthreads();
+          return;
         }
       }
-      s1 = ax + ay;
-      s2 = qx + qy;
-      cn = nx + ny;
-#pragma unroll
-      for (int off = WL / 2; off > 0; off >>= 1) {
-        s1 += __shfl_xor_sync(MASK, s1, off);
-        s2 += __shfl_xor_sync(MASK, s2, off);
-        cn += __shfl_xor_sync(MASK, cn, off);
+      const bool ok = mbar_wait(&tbar, phase);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+          atomicExch(err, 1);
+          mbar_wait(&tbar, phase);  // once more, so the copy does not land after the block has left
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        return;
       }
+      phase ^= 1u;
+      if (tid == 0) {  // the tile's reads of the ring slot are complete
+        fence_proxy_async_global();
+        __threadfence();
+        atomicAdd(rowcnt + c, 1);
+      }
+      float2 v[K::E];
+      row_zbuild<N>(v, tile, tb_, xfb, ncol);
+      __syncthreads();  // the staging area is read
+      prefetch(qn, next_stage, pf);
+      const FusedChunk ch = chunks[c];
+      const int slot = groups[ch.g].img0 + ch.kbase + a - img_base;
+      row_finish<N, false>(v, fbuf + xfb * K::STRIDE, tb.twiddle, tb_, xfb, slot, b * K::RB, g.tsplit, log2l,
+                           nullptr, img_base, nullptr, partials, nullptr);
+    } else if (kind == 1) {
+      // --------------------------------------------------------- column item
+      const FusedChunk ch = chunks[c];
+      const int u = a;
+      const int ncells = tb.col_cell_ptr[u + 1] - tb.col_cell_ptr[u];
+      const int nruns = tb.col_run_ptr[u + 1] - tb.col_run_ptr[u];
+      if (!stage_ready) issue_stage(c, u);
+      cp_async_wait_all();
+      __syncthreads();
+      const int wslot0 = groups[ch.g].img0 + ch.kbase - img_base;
+      // Parseval sums of the column, one warp per image
+      if (warp < ch.nk) {
+        const int kl = warp;
+        float acc = 0.f;
+        for (int cc = lane; cc < ncells; cc += 32) {
+          const float2 h = cellv[cc * CI + 2 * ((kl >> 1) ^ (cc & (CPC - 1))) + (kl & 1)];
+          acc = fmaf(h.x, h.x, fmaf(h.y, h.y, acc));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) {
+          colsq[(size_t)(wslot0 + kl) * ncol + u] = (u == 0 ? 1.f : 2.f) * acc;
+          if (u == 0) mean0[wslot0 + kl] = (ncells > 0 && crow[0] == 0) ? cellv[kl].x : 0.f;
+        }
+      }
+      float2* buf = fbuf + (xfa * R + pa) * C::STRIDE;
+      col_scatter<N, CI>(buf, runs, nruns, cellv, crow, xfa, xfa < ch.nk, tb.twiddle, ta, pa, xfa * R + pa);
+      __syncthreads();  // the staging area is read
+      prefetch(qn, next_stage, pf);
+      // this warp's slot rows are free once the row items of chunk c - ring have read them
+      bool ok = true;
+      if (c >= ring) {
+        if (lane == 0) ok = wait_count(rowcnt + (c - ring), chunks[c - ring].nk * NRB, err);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok && lane == 0) atomicExch(err, 1);
+      }
+      float2* dst = (ok && xfa < ch.nk) ? Tring + ((size_t)ring_slot(c, xfa) * ncol + u) * N + pa * L : nullptr;
+      col_fft_store<N>(buf, tb.twiddle_col, ta, xfa * R + pa, dst);
+      if (ok) {
+        __threadfence();
+        fence_proxy_async_global();
+        __syncwarp();
+        if (lane == 0) atomicAdd(colcnt + c, 1);
+      }
+    } else {
+      // an empty place of the order (a missing image of a short chunk, the
+      // first and last steps): nothing was staged for it
+      __syncthreads();
+      prefetch(qn, next_stage, pf);
     }
-    // one partial per warp of the transform (WPT of them when a transform
-    // spans several warps; the finalisation combines them): no barrier
-    if ((t & 31) == 0) {
-      constexpr int WPT = K::T > 32 ? K::T / 32 : 1;
-      StatPartial sp;
-      sp.sum = s1;
-      sp.sumsq = s2;
-      sp.kept = cn;
-      sp.max = wmax;
-      sp.idx = best;
-      sp.pad = 0;
-      partials[(size_t)slot * K::PARTIALS + ((y0 >> 1) + xf) * WPT + (t >> 5)] = sp;
+    // end of the item: publish the item after next and the prefetch; stop
+    // if any block has given up
+    if (tid == 0) {
+      s_q = qf;
+      s_pf = pf;
+      s_fail = ld_acquire_gpu(err) != 0;
+    }
+    __syncthreads();
+    tile_ready = s_pf != 0;
+    stage_ready = next_stage;
+    q = qn;
+    qn = s_q;
+    if (s_fail) {
+      if (tid == 0 && tile_ready) mbar_wait(&tbar, phase);
+      cp_async_wait_all();
+      __syncthreads();
+      return;
     }
   }
+  cp_async_wait_all();
 }
 
 // The most dynamic shared memory a block of `kern` can have: the device's
@@ -474,6 +878,7 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
   const int nitems = npairs * nrb;
   const int xf = tid / K::T;
   const int t = tid - xf * K::T;
+  const int log2l = FftShape<N>::LOG2N - (g.tsplit > 1 ? __ffs(g.tsplit) - 1 : 0);
 
   auto prefetch = [&](int it) {
     const int pj = it / nrb;
@@ -497,7 +902,8 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     cp_async_wait_all();
     __syncthreads();
     const int pj = item / nrb;
-    const int y = (item - pj * nrb) * K::XB + xf;
+    const int iy = (item - pj * nrb) * K::XB + xf;   // T row; image row y below
+    const int y = t_row(iy, g.tsplit, log2l);
     float2 v[K::E];
     if constexpr (K::E == 32 && K::T % K::CH == 0) {
       // as in the search's row pass: u = t + r T (or N - t - r T) has the
@@ -591,7 +997,7 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
       sp.idx = mi;
       sp.kept = 0;
       sp.pad = 0;
-      partials[(size_t)pj * N + y] = sp;
+      partials[(size_t)pj * N + iy] = sp;
     }
   }
 }
@@ -623,8 +1029,8 @@ template <int N>
 cudaError_t run_colfft(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin, int ngroups,
                        int img_base, const float2* cellbuf, float2* Tbuf, float* colsq, float* mean0,
                        cudaStream_t st) {
-  using K = ImgCfg<N>;
-  const int smem = K::SMEM_A_FIXED + g.max_cells * (K::PART_IMAGES * 8 + 4);
+  using C = ColCfg<N>;
+  const int smem = C::SMEM_FIXED + g.max_cells * C::SMEM_PER_CELL;
   const int smem_max = max_dynamic_smem(k_colfft<N>);
   if (smem > smem_max) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_colfft<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
@@ -634,7 +1040,7 @@ cudaError_t run_colfft(const SegmentGeom& g, const DevTables& tb, const Group* g
   if (e != cudaSuccess) return e;
   if (ngroups <= 0) return cudaSuccess;
   dim3 grid(ngroups, g.ncol);
-  k_colfft<N><<<grid, K::THREADS_A, smem, st>>>(g, tb, groups, g_begin, img_base, cellbuf, Tbuf, colsq, mean0);
+  k_colfft<N><<<grid, C::THREADS, smem, st>>>(g, tb, groups, g_begin, img_base, cellbuf, Tbuf, colsq, mean0);
   return cudaGetLastError();
 }
 
@@ -685,18 +1091,50 @@ cudaError_t run_rowfft_stats(const SegmentGeom& g, const DevTables& tb, const fl
 }
 
 template <int N>
+cudaError_t run_image_fused(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin,
+                            const FusedChunk* chunks, int nchunks, int img_base, const float2* cellbuf,
+                            float2* Tring, int ring, const TileMap& tm, float* colsq, float* mean0,
+                            StatPartial* partials, int* counters, int* err, cudaStream_t st) {
+  using K = ImgCfg<N>;
+  using C = ColCfg<N>;
+  using F = FusedCfg<N>;
+  if (nchunks <= 0) return cudaSuccess;
+  if (tm.nbox <= 0 || ring < 2) return cudaErrorInvalidValue;
+  const int tile = rowfft_tile_rows<N>(g.ncol) * K::CH * 16;
+  const int cols = g.max_cells * (F::CI * 8 + 8);
+  const int smem = F::FB * 8 + 1024 + std::max(tile, cols);
+  auto kern = k_image_fused<N>;
+  const int smem_max = max_dynamic_smem(kern);
+  if (smem > smem_max) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(counters, 0, (size_t)(1 + 2 * nchunks) * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, F::THREADS, smem);
+  if (e != cudaSuccess) return e;
+  const long items = (long)(nchunks + 1) * (g.ncol + F::CI * F::NRB);
+  const long grid = std::min<long>(items, (long)std::max(per_sm, 1) * sm_count());
+  kern<<<(int)grid, F::THREADS, smem, st>>>(g, tb, groups, g_begin, chunks, nchunks, img_base, cellbuf, Tring, ring,
+                                           colsq, mean0, partials, tm.map, tm.nbox, tm.rows, counters, err);
+  return cudaGetLastError();
+}
+
+template <int N>
 void fill_shape(ImageKernelShape* o) {
   using K = ImgCfg<N>;
   o->images_per_group = K::B;
   o->cols_per_cta = 1;
-  o->threads_a = K::THREADS_A;
-  o->smem_a = K::SMEM_A_FIXED;
+  o->threads_a = ColCfg<N>::THREADS;
+  o->smem_a = ColCfg<N>::SMEM_FIXED;
   o->warps_per_col = 0;
   o->rows_per_cta = K::RB;
   o->partials_per_image = K::PARTIALS;
   o->threads_b = K::THREADS_B;
   o->smem_b = K::SMEM_B_FIXED;
-  o->smem_a_per_cell = K::PART_IMAGES * 8 + 4;
+  o->smem_a_per_cell = ColCfg<N>::SMEM_PER_CELL;
   o->smem_b_per_row = K::CH * 16;
   o->tile_tma = K::TILE_TMA;
 }
@@ -710,5 +1148,10 @@ void fill_shape(ImageKernelShape* o) {
   template void fill_shape<N>(ImageKernelShape*);                                                           \
   template cudaError_t run_rowfft_power<N>(const SegmentGeom&, const DevTables&, const float2*, const int4*, \
                                            int, StatPartial*, cudaStream_t);
+
+#define RF_INSTANTIATE_FUSED(N)                                                                              \
+  template cudaError_t run_image_fused<N>(const SegmentGeom&, const DevTables&, const Group*, int,            \
+                                          const FusedChunk*, int, int, const float2*, float2*, int,         \
+                                          const TileMap&, float*, float*, StatPartial*, int*, int*, cudaStream_t);
 
 }  // namespace rf

@@ -580,7 +580,37 @@ template <int N>
 cudaError_t run_rowfft_power(const SegmentGeom&, const DevTables&, const float2*, const int4*, int, StatPartial*,
                              cudaStream_t);
 
+template <int N>
+cudaError_t run_image_fused(const SegmentGeom&, const DevTables&, const Group*, int, const FusedChunk*, int, int,
+                            const float2*, float2*, int, const TileMap&, float*, float*, StatPartial*, int*, int*,
+                            cudaStream_t);
+
 #define RF_FOR_EACH_N(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
+
+int fused_chunk_images(int npix) {
+  switch (npix) {
+    case 1024: return 8;
+    case 2048: return 4;
+    case 4096: return 2;
+    default: return 0;
+  }
+}
+
+cudaError_t launch_image_fused(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin,
+                               const FusedChunk* chunks, int nchunks, int img_base, const float2* cellbuf,
+                               float2* Tring, int ring, const TileMap& tm, float* colsq, float* mean0,
+                               StatPartial* partials, int* counters, int* err, cudaStream_t st) {
+  switch (g.npix) {
+#define RF_CASE(N)                                                                                               \
+  case N:                                                                                                        \
+    return run_image_fused<N>(g, tb, groups, g_begin, chunks, nchunks, img_base, cellbuf, Tring, ring, tm, colsq, \
+                              mean0, partials, counters, err, st);
+    RF_CASE(1024) RF_CASE(2048) RF_CASE(4096)
+#undef RF_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_colfft(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin,
                           int ngroups, int img_base, const float2* cellbuf, float2* Tbuf, float* colsq,

@@ -203,8 +203,10 @@ cudaError_t run_noalloc(const float2* grid, double weight, const DeviceSetup& d,
   SegmentGeom g{};
   g.npix = N;
   g.ncol = NC;
+  g.tsplit = 1;  // k_colfft_dense stores T in natural row order
   DevTables tb{};
   tb.twiddle = tw;
+  tb.twiddle_col = tw;
   e = launch_rowfft_stats(g, tb, T, 1, 0, nullptr, partials, nullptr, nullptr, nullptr, st);
   if (e != cudaSuccess) return e;
   k_noalloc_finalize<<<1, 32, 0, st>>>(partials, K::PARTIALS, colsq, mean0, N, weight, out);

@@ -296,6 +296,7 @@ cudaError_t launch_plain_chunk(const SegmentGeom& g, const DevTables& tb, const 
   if (e != cudaSuccess) return e;
   SegmentGeom gr = g;
   gr.ncol = g.npix / 2;
+  gr.tsplit = 1;  // k_plain_colfft stores T in natural row order
   e = launch_rowfft_stats(gr, tb, pb.T, nk, img0, weight, pb.partials, pb.images, nullptr, nullptr, st);
   if (e != cudaSuccess) return e;
   k_plain_stats<<<nk, 256, 0, st>>>(g.npix, pb.images, img_info, weight, img0, threshold, cands, ncand, cand_cap,

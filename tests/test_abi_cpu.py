@@ -215,6 +215,19 @@ def test_wide_index_tuning_key(L):
         assert e.value.status == rf.RF_ERR_INVALID_ARG
 
 
+def test_fused_and_ring_tuning_keys(L):
+    kw = _desc_kwargs(synth.config("tiny"))
+    with rf.Plan(**kw) as p:
+        assert rf.rf_plan_get_tuning(p.handle, rf.RF_TUNE_FUSED) == 0
+        assert rf.rf_plan_get_tuning(p.handle, rf.RF_TUNE_RING) == 2
+        p.set_fused(True)
+        assert rf.rf_plan_get_tuning(p.handle, rf.RF_TUNE_FUSED) == 1
+        for bad_key, bad in ((rf.RF_TUNE_FUSED, 2), (rf.RF_TUNE_RING, 1), (rf.RF_TUNE_RING, 9)):
+            with pytest.raises(rf.RfError) as e:
+                rf.rf_plan_set_tuning(p.handle, bad_key, bad)
+            assert e.value.status == rf.RF_ERR_INVALID_ARG
+
+
 def test_noalloc_rejects_host_memory(L):
     # a host (numpy) buffer is not device memory of a current device: the call
     # rejects it before any launch (on a machine without a GPU as on one with)
