@@ -178,6 +178,14 @@ struct SegmentGeom {
 // column's cells), leaving R transforms of length 1024.
 constexpr int col_split(int n) { return n >= 2048 ? n / 1024 : 1; }
 
+// Complex values per thread of the row pass at N = 2048: 32 (64 threads per
+// row pair, 256-thread blocks) or 16 (128 threads per row pair, 512-thread
+// blocks: twice the warps in the same shared memory, at 64 registers a
+// thread).  Both give the same images; 16 measured 36% slower on GB300
+// (48.0 against 35.2 ms per 8134-image launch), so 32 is built.  The fused
+// pass exists at 2048 only with 32.
+#define RF_ROW_VALUES_2048 32
+
 // ---------------------------------------------------------------- launchers
 // All launchers return cudaSuccess or the launch error.
 

@@ -3,7 +3,9 @@
 // 2D FFT is the most demanding stage of the search).
 //
 // A length-N transform (N a power of two, 16..8192) is done by T = N/E
-// threads that each hold E = 32 complex values (E = 16 for N = 16).  Each
+// threads that each hold E = 32 complex values (E = 16 for N = 16; a kernel
+// may ask for E = 16 at any N, whose passes then all take their twiddles by
+// products of table entries, see twiddle_mul).  Each
 // pass is a radix-P Stockham autosort step: thread t loads the P inputs
 // j + r (N/P) of each of its E/P butterflies j, multiplies them by
 // exp(+2 pi i k r / (Ns P)) with k = j mod Ns, does a radix-P inverse DFT in
@@ -231,11 +233,13 @@ __host__ __device__ constexpr int dft_perm(int q) {
                  : (P == 16 ? 4 * (q & 3) + (q >> 2) : (P == 8 ? 4 * (q & 1) + (q >> 1) : q));
 }
 
-// Compile-time pass layout of a length-N transform.
-template <int N>
+// Compile-time pass layout of a length-N transform with EV complex values
+// per thread (32 by default; 16 below N = 32).
+template <int N, int EV = (N >= 32 ? 32 : 16)>
 struct FftShape {
   static_assert(N >= 16 && N <= 8192 && (N & (N - 1)) == 0, "N must be a power of two in [16, 8192]");
-  static constexpr int E = N >= 32 ? 32 : 16;           // complex values per thread
+  static_assert(EV == 16 || EV == 32, "16 or 32 values per thread");
+  static constexpr int E = EV;                          // complex values per thread
   static constexpr int T = N / E;                       // threads per transform
   static constexpr int LOG2N = ilog2c(N);
   static constexpr int LOG2E = ilog2c(E);
@@ -281,10 +285,10 @@ __device__ __forceinline__ void twiddle_mul(float2* v, const float2* __restrict_
 // Load phase of one pass: v[m P + r] = s[j + r N/P], j = t + m T.  When
 // m T and r N/P are multiples of 32 (N >= 1024), padx(t + m T + r N/P) =
 // padx(t) + padx(m T) + padx(r N/P): one index per thread, the rest constant.
-template <int N, int P>
-__device__ __forceinline__ void pass_load(float2 (&v)[FftShape<N>::E], const float2* s, int t) {
-  constexpr int E = FftShape<N>::E;
-  constexpr int T = FftShape<N>::T;
+template <int N, int P, int EV = FftShape<N>::E>
+__device__ __forceinline__ void pass_load(float2 (&v)[EV], const float2* s, int t) {
+  constexpr int E = FftShape<N, EV>::E;
+  constexpr int T = FftShape<N, EV>::T;
   constexpr int J = N / P;
   if constexpr (T % 32 == 0 && J % 32 == 0) {
     const float2* st = s + padx(t);
@@ -303,11 +307,10 @@ __device__ __forceinline__ void pass_load(float2 (&v)[FftShape<N>::E], const flo
 }
 
 // Twiddle + radix-P DFT of each butterfly held by the thread.
-template <int N, int P, bool PK = false>
-__device__ __forceinline__ void pass_compute(float2 (&v)[FftShape<N>::E], const float2* __restrict__ tw, int t,
-                                             int Ns) {
-  constexpr int E = FftShape<N>::E;
-  constexpr int T = FftShape<N>::T;
+template <int N, int P, bool PK = false, int EV = FftShape<N>::E>
+__device__ __forceinline__ void pass_compute(float2 (&v)[EV], const float2* __restrict__ tw, int t, int Ns) {
+  constexpr int E = FftShape<N, EV>::E;
+  constexpr int T = FftShape<N, EV>::T;
 #pragma unroll
   for (int m = 0; m < E / P; ++m) {
     const int j = t + m * T;
@@ -345,10 +348,10 @@ __device__ __forceinline__ void pass2_compute(float2 (&v)[FftShape<N>::E], const
 // Store phase of a non-final pass.  Output q of butterfly j goes to
 // base + q Ns.  When q Ns is a multiple of 32, or Ns = 1 and base is (P = 32),
 // padx(base + q Ns) = padx(base) + padx(q Ns) with the second term constant.
-template <int N, int P>
-__device__ __forceinline__ void pass_store(const float2 (&v)[FftShape<N>::E], float2* s, int t, int Ns) {
-  constexpr int E = FftShape<N>::E;
-  constexpr int T = FftShape<N>::T;
+template <int N, int P, int EV = FftShape<N>::E>
+__device__ __forceinline__ void pass_store(const float2 (&v)[EV], float2* s, int t, int Ns) {
+  constexpr int E = FftShape<N, EV>::E;
+  constexpr int T = FftShape<N, EV>::T;
 #pragma unroll
   for (int m = 0; m < E / P; ++m) {
     const int j = t + m * T;
@@ -377,12 +380,30 @@ __device__ __forceinline__ float fmax3f(float a, float b, float c) {
 // (fft_twiddle_len(N) entries: the N powers of w, then the second pass's
 // table); on return the thread holds the outputs
 // X[o] for o = t + m T + q (N / LAST_P) in v[m LAST_P + dft_perm(q)].
-template <int N, bool PK = false>
-__device__ __forceinline__ void fft_inverse_from_regs(float2 (&v)[FftShape<N>::E], float2* s,
-                                                      const float2* __restrict__ tw, int t, int xf) {
-  using S = FftShape<N>;
+template <int N, bool PK = false, int EV = FftShape<N>::E>
+__device__ __forceinline__ void fft_inverse_from_regs(float2 (&v)[EV], float2* s, const float2* __restrict__ tw,
+                                                      int t, int xf) {
+  using S = FftShape<N, EV>;
   if constexpr (S::NPASS == 1) {
     pass_compute<N, S::LAST_P, PK>(v, tw, t, 1);
+  } else if constexpr (S::E != 32) {
+    // 16 values a thread: every pass's twiddles from the length-N table
+    // (products of w^(s 2^i), see twiddle_mul)
+    pass_compute<N, S::E, PK, EV>(v, tw, t, 1);
+    pass_store<N, S::E, EV>(v, s, t, 1);
+    fft_sync<S::T>(xf);
+    if constexpr (S::NPASS == 2) {
+      pass_load<N, S::LAST_P, EV>(v, s, t);
+      pass_compute<N, S::LAST_P, PK, EV>(v, tw, t, S::E);
+    } else {
+      pass_load<N, S::E, EV>(v, s, t);
+      fft_sync<S::T>(xf);
+      pass_compute<N, S::E, PK, EV>(v, tw, t, S::E);
+      pass_store<N, S::E, EV>(v, s, t, S::E);
+      fft_sync<S::T>(xf);
+      pass_load<N, S::LAST_P, EV>(v, s, t);
+      pass_compute<N, S::LAST_P, PK, EV>(v, tw, t, S::E * S::E);
+    }
   } else {
     pass_compute<N, S::E, PK>(v, tw, t, 1);
     pass_store<N, S::E>(v, s, t, 1);
@@ -403,20 +424,20 @@ __device__ __forceinline__ void fft_inverse_from_regs(float2 (&v)[FftShape<N>::E
 
 // The same with the first-pass inputs read from the padded buffer `s`
 // (filled and made visible to the transform's threads by the caller).
-template <int N, bool PK = false>
-__device__ __forceinline__ void fft_inverse_to_regs(float2 (&v)[FftShape<N>::E], float2* s,
-                                                    const float2* __restrict__ tw, int t, int xf) {
-  using S = FftShape<N>;
+template <int N, bool PK = false, int EV = FftShape<N>::E>
+__device__ __forceinline__ void fft_inverse_to_regs(float2 (&v)[EV], float2* s, const float2* __restrict__ tw,
+                                                    int t, int xf) {
+  using S = FftShape<N, EV>;
   constexpr int P0 = S::NPASS == 1 ? S::LAST_P : S::E;
-  pass_load<N, P0>(v, s, t);
+  pass_load<N, P0, EV>(v, s, t);
   if (S::NPASS > 1) fft_sync<S::T>(xf);  // in place: all loads before the first store
-  fft_inverse_from_regs<N, PK>(v, s, tw, t, xf);
+  fft_inverse_from_regs<N, PK, EV>(v, s, tw, t, xf);
 }
 
 // Output index of register (m, q) after the last pass.
-template <int N>
+template <int N, int EV = FftShape<N>::E>
 __device__ __forceinline__ int fft_out_index(int t, int m, int q) {
-  using S = FftShape<N>;
+  using S = FftShape<N, EV>;
   return t + m * S::T + q * (N / S::LAST_P);
 }
 

@@ -47,12 +47,15 @@ struct ImgCfg {
   static constexpr int CELL_PITCH = 33;                          // cell values per cell row (32 + pad)
   static constexpr int PART_IMAGES = N >= 2048 ? 16 : 32;        // images whose cells are staged at once
   static constexpr int SMEM_A_FIXED = XA * fft_stride<N>() * 8;
-  // pass B: XB row pairs (RB rows) per work item; the column-FFT tile of the
-  // next item is prefetched while the current one is transformed
-  static constexpr int XB = cmin(256 / T, N / 2);
-  static constexpr int THREADS_B = T * XB;
+  // pass B (row pass): EB values per thread, TB threads per transform, XB row
+  // pairs (RB rows) per work item; the column-FFT tile of the next item is
+  // prefetched while the current one is transformed
+  static constexpr int EB = N == 2048 ? RF_ROW_VALUES_2048 : E;
+  static constexpr int TB = N / EB;
+  static constexpr int XB = cmin((EB == 32 ? 256 : 512) / TB, N / 2);
+  static constexpr int THREADS_B = TB * XB;
   static constexpr int RB = 2 * XB;
-  static constexpr int PARTIALS = (N / 2) * (T > 32 ? T / 32 : 1);  // row-pass partials per image
+  static constexpr int PARTIALS = (N / 2) * (TB > 32 ? TB / 32 : 1);  // row-pass partials per image
   static constexpr int CH = XB;                                  // 16-byte chunks per tile row
   static constexpr int STRIDE = fft_stride<N>();
   static constexpr int SMEM_B_FIXED = XB * STRIDE * 8;
@@ -63,7 +66,7 @@ struct ImgCfg {
   static constexpr bool TILE_TMA = N >= 1024;
   static constexpr int SWZ_SH = CH == 4 ? 1 : (CH == 2 ? 2 : 0);
   __device__ static __forceinline__ int swz(int u, int c) { return c ^ ((u >> SWZ_SH) & (CH - 1)); }
-  static_assert(T <= 32 || (XA <= 15 && XB <= 15), "named barriers: at most 15 wide transforms per block");
+  static_assert((T <= 32 || XA <= 15) && (TB <= 32 || XB <= 15), "named barriers: at most 15 wide transforms per block");
   static_assert(FftShape<N>::P2 == fft_pass2_radix(N), "twiddle table layout and FFT passes disagree");
 };
 
@@ -286,35 +289,36 @@ __device__ __forceinline__ void max_merge(float& m, int& i, float m2, int i2) {
 // (T rows y0 .. y0 + RB of every imaged column u, swizzled 16-byte chunks)
 // is in shared memory.
 template <int N>
-__device__ __forceinline__ void row_zbuild(float2 (&v)[ImgCfg<N>::E], const float4* __restrict__ tile, int t,
+__device__ __forceinline__ void row_zbuild(float2 (&v)[ImgCfg<N>::EB], const float4* __restrict__ tile, int t,
                                            int xf, int ncol) {
   using K = ImgCfg<N>;
+  constexpr int EB = K::EB, TB = K::TB;
   // first-pass inputs Z[u], u = t + r T: a + i b for 0 < u < ncol, the
   // Hermitian mirror conj(a) + i conj(b) for N - u < ncol, real parts at
-  // u = 0, zero elsewhere (columns beyond iu_max are empty).  N/2 = 16 T,
-  // so r < 16 can only be a direct column and r >= 16 only a mirror.
-  if constexpr (K::E == 32 && K::T % (K::CH << K::SWZ_SH) == 0) {
+  // u = 0, zero elsewhere (columns beyond iu_max are empty).  N/2 = (EB/2) TB,
+  // so r < EB/2 can only be a direct column and r >= EB/2 only a mirror.
+  if constexpr (TB % (K::CH << K::SWZ_SH) == 0) {
     // the swizzle term of u = t + r T (or N - t - r T) is that of t (N - t)
-    const int rd_end = ncol > t ? (ncol - t + K::T - 1) / K::T : 0;
-    const int rm_beg = (N - ncol - t) / K::T + 1;
+    const int rd_end = ncol > t ? (ncol - t + TB - 1) / TB : 0;
+    const int rm_beg = (N - ncol - t) / TB + 1;
     const float4* pd = tile + t * K::CH + K::swz(t, xf);
     const float4* pm = tile + (size_t)(N - t) * K::CH + K::swz(N - t, xf);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
+    for (int r = 0; r < EB / 2; ++r) {
       float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (r < rd_end) ab = pd[r * K::T * K::CH];
+      if (r < rd_end) ab = pd[r * TB * K::CH];
       v[r] = (r == 0 && t == 0) ? make_float2(ab.x, ab.z) : make_float2(ab.x - ab.w, ab.y + ab.z);
     }
 #pragma unroll
-    for (int r = 16; r < 32; ++r) {
+    for (int r = EB / 2; r < EB; ++r) {
       float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (r >= rm_beg) ab = pm[-r * K::T * K::CH];
+      if (r >= rm_beg) ab = pm[-r * TB * K::CH];
       v[r] = make_float2(ab.x + ab.w, ab.z - ab.y);
     }
   } else {
 #pragma unroll
-    for (int r = 0; r < K::E; ++r) {
-      const int u = t + r * K::T;
+    for (int r = 0; r < EB; ++r) {
+      const int u = t + r * TB;
       float2 z = make_float2(0.f, 0.f);
       if (u < ncol) {
         const float4 ab = tile[u * K::CH + K::swz(u, xf)];
@@ -334,13 +338,14 @@ __device__ __forceinline__ void row_zbuild(float2 (&v)[ImgCfg<N>::E], const floa
 // max pixel with its lowest index (and under CLIP the kept-pixel sums), one
 // StatPartial per warp of the transform, and the two image rows if `images`.
 template <int N, bool CLIP>
-__device__ __forceinline__ void row_finish(float2 (&v)[ImgCfg<N>::E], float2* buf, const float2* __restrict__ tw,
+__device__ __forceinline__ void row_finish(float2 (&v)[ImgCfg<N>::EB], float2* buf, const float2* __restrict__ tw,
                                            int t, int xf, int slot, int y0, int tsplit, int log2l,
                                            const double* __restrict__ weight, int img_base,
                                            float* __restrict__ images, StatPartial* __restrict__ partials,
                                            const float2* __restrict__ clip) {
   using K = ImgCfg<N>;
-  fft_inverse_from_regs<N>(v, buf, tw, t, xf);
+  constexpr int EB = K::EB, TB = K::TB;
+  fft_inverse_from_regs<N, false, EB>(v, buf, tw, t, xf);
 
   // per-row-pair statistics: the max pixel and its lowest index (the
   // noise comes from the grid by Parseval's identity, see k_colfft).  The
@@ -349,8 +354,8 @@ __device__ __forceinline__ void row_finish(float2 (&v)[ImgCfg<N>::E], float2* bu
   const int i = y0 + 2 * xf;
   const int ya = t_row(i, tsplit, log2l);
   const int yb = t_row(i + 1, tsplit, log2l);
-  constexpr int LP = FftShape<N>::LAST_P;
-  constexpr int EM = K::E / LP;
+  constexpr int LP = FftShape<N, EB>::LAST_P;
+  constexpr int EM = EB / LP;
   if (images != nullptr) {
     const double W = weight[img_base + slot];
     const float scale = W > 0.0 ? (float)(0.5 / W) : 0.f;
@@ -361,7 +366,7 @@ __device__ __forceinline__ void row_finish(float2 (&v)[ImgCfg<N>::E], float2* bu
 #pragma unroll
       for (int q = 0; q < LP; ++q) {
         const float2 z = v[m * LP + dft_perm<LP>(q)];
-        const int o = fft_out_index<N>(t, m, q);
+        const int o = fft_out_index<N, EB>(t, m, q);
         ima[o] = z.x * scale;
         imb[o] = z.y * scale;
       }
@@ -371,7 +376,7 @@ __device__ __forceinline__ void row_finish(float2 (&v)[ImgCfg<N>::E], float2* bu
   float mxa[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
   float mya[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
 #pragma unroll
-  for (int e = 0; e < K::E; e += 2) {
+  for (int e = 0; e < EB; e += 2) {
     mxa[(e >> 1) & 3] = fmax3f(mxa[(e >> 1) & 3], v[e].x, v[e + 1].x);
     mya[(e >> 1) & 3] = fmax3f(mya[(e >> 1) & 3], v[e].y, v[e + 1].y);
   }
@@ -380,7 +385,7 @@ __device__ __forceinline__ void row_finish(float2 (&v)[ImgCfg<N>::E], float2* bu
   const float lmax = fmaxf(mx, my);
   // reduce over the transform's T threads (a warp, a part of one, or
   // several warps joined through shared memory)
-  constexpr int WL = K::T < 32 ? K::T : 32;
+  constexpr int WL = TB < 32 ? TB : 32;
   constexpr unsigned MASK = 0xffffffffu;
   float wmax = lmax;
 #pragma unroll
@@ -395,7 +400,7 @@ __device__ __forceinline__ void row_finish(float2 (&v)[ImgCfg<N>::E], float2* bu
 #pragma unroll
         for (int m = 0; m < EM; ++m)
           if (v[m * LP + dft_perm<LP>(q)].x == wmax) {
-            best = ya * N + fft_out_index<N>(t, m, q);
+            best = ya * N + fft_out_index<N, EB>(t, m, q);
             goto found;
           }
     } else {
@@ -404,7 +409,7 @@ __device__ __forceinline__ void row_finish(float2 (&v)[ImgCfg<N>::E], float2* bu
 #pragma unroll
         for (int m = 0; m < EM; ++m)
           if (v[m * LP + dft_perm<LP>(q)].y == wmax) {
-            best = yb * N + fft_out_index<N>(t, m, q);
+            best = yb * N + fft_out_index<N, EB>(t, m, q);
             goto found;
           }
     }
@@ -421,7 +426,7 @@ __device__ __forceinline__ void row_finish(float2 (&v)[ImgCfg<N>::E], float2* bu
     float ax = 0.f, qx = 0.f, ay = 0.f, qy = 0.f;
     int nx = 0, ny = 0;
 #pragma unroll
-    for (int e = 0; e < K::E; ++e) {
+    for (int e = 0; e < EB; ++e) {
       const float dx = v[e].x - cw.x;
       const float dy = v[e].y - cw.x;
       if (fabsf(dx) <= cw.y) {
@@ -448,7 +453,7 @@ __device__ __forceinline__ void row_finish(float2 (&v)[ImgCfg<N>::E], float2* bu
   // one partial per warp of the transform (WPT of them when a transform
   // spans several warps; the finalisation combines them): no barrier
   if ((t & 31) == 0) {
-    constexpr int WPT = K::T > 32 ? K::T / 32 : 1;
+    constexpr int WPT = TB > 32 ? TB / 32 : 1;
     StatPartial sp;
     sp.sum = s1;
     sp.sumsq = s2;
@@ -496,8 +501,8 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
   const int ncol = g.ncol;
   constexpr int nrb = N / K::RB;
   const int nitems = nimg * nrb;
-  const int xf = tid / K::T;
-  const int t = tid - xf * K::T;
+  const int xf = tid / K::TB;
+  const int t = tid - xf * K::TB;
   const int log2l = FftShape<N>::LOG2N - (g.tsplit > 1 ? __ffs(g.tsplit) - 1 : 0);
   const bool use_tma = K::TILE_TMA && tma_boxes > 0;
   unsigned phase = 0;
@@ -548,7 +553,7 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     }
     const int slot = item / nrb;
     const int y0 = (item - slot * nrb) * K::RB;
-    float2 v[K::E];
+    float2 v[K::EB];
     row_zbuild<N>(v, tile, t, xf, ncol);
     __syncthreads();  // tile consumed: prefetch the next item
     if (item + (int)gridDim.x < nitems) fetch(item + gridDim.x);
@@ -635,7 +640,7 @@ __global__ void __launch_bounds__(FusedCfg<N>::THREADS, 2)
   const int log2l = FftShape<N>::LOG2N - (g.tsplit > 1 ? __ffs(g.tsplit) - 1 : 0);
   const unsigned tile_bytes = (unsigned)(tma_boxes * tma_rows * K::CH * 16);
   // roles' thread layouts
-  const int xfb = tid / K::T, tb_ = tid - xfb * K::T;                  // row role
+  const int xfb = tid / K::TB, tb_ = tid - xfb * K::TB;                // row role
   const int xfa = tid / (R * TL), pa = (tid / TL) % R, ta = tid % TL;  // column role
 
   // item q's kind: 0 none, 1 column (chunk c, column a), 2 row (chunk c, image a, block b)
@@ -749,7 +754,7 @@ __global__ void __launch_bounds__(FusedCfg<N>::THREADS, 2)
         __threadfence();
         atomicAdd(rowcnt + c, 1);
       }
-      float2 v[K::E];
+      float2 v[K::EB];
       row_zbuild<N>(v, tile, tb_, xfb, ncol);
       __syncthreads();  // the staging area is read
       prefetch(qn, next_stage, pf);
@@ -865,6 +870,7 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     k_rowfft_power(SegmentGeom g, DevTables tb, const float2* __restrict__ Tbuf, const int4* __restrict__ pairs,
                    int npairs, StatPartial* __restrict__ partials) {
   using K = ImgCfg<N>;
+  constexpr int EB = K::EB, TB = K::TB;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* fbuf = reinterpret_cast<float2*>(smraw);                     // [XB][STRIDE]
   float4* tile = reinterpret_cast<float4*>(fbuf + K::XB * K::STRIDE);  // [ncol][CH]
@@ -876,8 +882,8 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
   const int ncol = g.ncol;
   constexpr int nrb = N / K::XB;  // row blocks per pair
   const int nitems = npairs * nrb;
-  const int xf = tid / K::T;
-  const int t = tid - xf * K::T;
+  const int xf = tid / TB;
+  const int t = tid - xf * TB;
   const int log2l = FftShape<N>::LOG2N - (g.tsplit > 1 ? __ffs(g.tsplit) - 1 : 0);
 
   auto prefetch = [&](int it) {
@@ -904,30 +910,30 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     const int pj = item / nrb;
     const int iy = (item - pj * nrb) * K::XB + xf;   // T row; image row y below
     const int y = t_row(iy, g.tsplit, log2l);
-    float2 v[K::E];
-    if constexpr (K::E == 32 && K::T % K::CH == 0) {
+    float2 v[EB];
+    if constexpr (TB % K::CH == 0) {
       // as in the search's row pass: u = t + r T (or N - t - r T) has the
       // swizzle term of t (N - t), and the loads are predicated, not branched
-      const int rd_end = ncol > t ? (ncol - t + K::T - 1) / K::T : 0;
-      const int rm_beg = (N - ncol - t) / K::T + 1;
+      const int rd_end = ncol > t ? (ncol - t + TB - 1) / TB : 0;
+      const int rm_beg = (N - ncol - t) / TB + 1;
       const float4* pd = tile + t * K::CH + (xf ^ (t & (K::CH - 1)));
       const float4* pm = tile + (size_t)(N - t) * K::CH + (xf ^ ((N - t) & (K::CH - 1)));
 #pragma unroll
-      for (int r = 0; r < 16; ++r) {
+      for (int r = 0; r < EB / 2; ++r) {
         float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (r < rd_end) ab = pd[r * K::T * K::CH];
+        if (r < rd_end) ab = pd[r * TB * K::CH];
         v[r] = (r == 0 && t == 0) ? make_float2(ab.x, ab.z) : make_float2(ab.x - ab.w, ab.y + ab.z);
       }
 #pragma unroll
-      for (int r = 16; r < 32; ++r) {
+      for (int r = EB / 2; r < EB; ++r) {
         float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (r >= rm_beg) ab = pm[-r * K::T * K::CH];
+        if (r >= rm_beg) ab = pm[-r * TB * K::CH];
         v[r] = make_float2(ab.x + ab.w, ab.z - ab.y);
       }
     } else {
 #pragma unroll
-      for (int r = 0; r < K::E; ++r) {
-        const int u = t + r * K::T;
+      for (int r = 0; r < EB; ++r) {
+        const int u = t + r * TB;
         float2 z = make_float2(0.f, 0.f);
         if (u < ncol) {
           const float4 ab = tile[u * K::CH + (xf ^ (u & (K::CH - 1)))];
@@ -942,15 +948,15 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     }
     __syncthreads();  // tile consumed: prefetch the next item
     if (item + (int)gridDim.x < nitems) prefetch(item + gridDim.x);
-    fft_inverse_from_regs<N>(v, fbuf + xf * K::STRIDE, tb.twiddle, t, xf);
+    fft_inverse_from_regs<N, false, EB>(v, fbuf + xf * K::STRIDE, tb.twiddle, t, xf);
 
-    constexpr int LP = FftShape<N>::LAST_P;
-    constexpr int EM = K::E / LP;
+    constexpr int LP = FftShape<N, EB>::LAST_P;
+    constexpr int EM = EB / LP;
     float pa[4] = {-1.f, -1.f, -1.f, -1.f};
 #pragma unroll
-    for (int e = 0; e < K::E; ++e) pa[e & 3] = fmaxf(pa[e & 3], fmaf(v[e].x, v[e].x, v[e].y * v[e].y));
+    for (int e = 0; e < EB; ++e) pa[e & 3] = fmaxf(pa[e & 3], fmaf(v[e].x, v[e].x, v[e].y * v[e].y));
     const float lmax = fmaxf(fmaxf(pa[0], pa[1]), fmaxf(pa[2], pa[3]));
-    constexpr int WL = K::T < 32 ? K::T : 32;
+    constexpr int WL = TB < 32 ? TB : 32;
     constexpr unsigned MASK = 0xffffffffu;
     float wmax = lmax;
 #pragma unroll
@@ -963,7 +969,7 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
         for (int m = 0; m < EM; ++m) {
           const float2 z = v[m * LP + dft_perm<LP>(q)];
           if (fmaf(z.x, z.x, z.y * z.y) == wmax) {
-            best = y * N + fft_out_index<N>(t, m, q);
+            best = y * N + fft_out_index<N, EB>(t, m, q);
             goto found;
           }
         }
@@ -973,21 +979,21 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     for (int off = WL / 2; off > 0; off >>= 1) best = min(best, __shfl_xor_sync(MASK, best, off));
     float mx = wmax;
     int mi = best;
-    if (K::T > 32) {
-      constexpr int WPT = K::T / 32;
+    if (TB > 32) {
+      constexpr int WPT = TB / 32;
       const int wi = t >> 5;
       if (lane == 0) {
         w_max[wid] = wmax;
         w_idx[wid] = best;
       }
-      fft_sync<K::T>(xf);
+      fft_sync<TB>(xf);
       if (t == 0) {
         const int w0 = wid - wi;
         mx = -1.f;
         mi = INT_MAX;
         for (int w = 0; w < WPT; ++w) max_merge(mx, mi, w_max[w0 + w], w_idx[w0 + w]);
       }
-      fft_sync<K::T>(xf);
+      fft_sync<TB>(xf);
     }
     if (t == 0) {
       StatPartial sp;

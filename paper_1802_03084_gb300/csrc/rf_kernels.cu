@@ -590,7 +590,7 @@ cudaError_t run_image_fused(const SegmentGeom&, const DevTables&, const Group*, 
 int fused_chunk_images(int npix) {
   switch (npix) {
     case 1024: return 8;
-    case 2048: return 4;
+    case 2048: return RF_ROW_VALUES_2048 == 32 ? 4 : 0;
     case 4096: return 2;
     default: return 0;
   }
@@ -605,7 +605,10 @@ cudaError_t launch_image_fused(const SegmentGeom& g, const DevTables& tb, const 
   case N:                                                                                                        \
     return run_image_fused<N>(g, tb, groups, g_begin, chunks, nchunks, img_base, cellbuf, Tring, ring, tm, colsq, \
                               mean0, partials, counters, err, st);
-    RF_CASE(1024) RF_CASE(2048) RF_CASE(4096)
+    RF_CASE(1024) RF_CASE(4096)
+#if RF_ROW_VALUES_2048 == 32
+    RF_CASE(2048)
+#endif
 #undef RF_CASE
     default:
       return cudaErrorInvalidValue;
