@@ -595,12 +595,13 @@ rf_status rf_stream_get_info(const struct rf_stream* s, rf_stream_info* out);
 /* Free the windows and queues (NULL-safe).  The plan is not destroyed. */
 rf_status rf_stream_destroy(struct rf_stream* s);
 
-/* Check of the bounded device-side wait (no counterpart in the paper): one
- * block waits, at most `polls` polls (1 .. 2^20), on an mbarrier that
- * nothing arrives at, as the row pass waits for its tile copies.  The wait
- * must give up and report it instead of hanging: *gave_up = 1.  The device
- * stays usable afterwards.  Errors: RF_ERR_INVALID_ARG, RF_ERR_NO_DEVICE,
- * RF_ERR_CUDA. */
+/* Check of the bounded device-side waits (no counterpart in the paper): one
+ * block waits, at most `polls` polls (1 .. 2^20) each, on an mbarrier that
+ * nothing arrives at, as the row pass waits for its tile copies, and on a
+ * global count that nothing raises, as the fused imaging pass waits for
+ * work items of other blocks.  Both waits must give up and report it
+ * instead of hanging: *gave_up = 1.  The device stays usable afterwards.
+ * Errors: RF_ERR_INVALID_ARG, RF_ERR_NO_DEVICE, RF_ERR_CUDA. */
 rf_status rf_selftest_bounded_wait(int32_t device, int32_t polls, int32_t* gave_up);
 
 /* Library version string. */

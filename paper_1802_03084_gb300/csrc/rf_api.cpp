@@ -1800,14 +1800,14 @@ rf_status rf_selftest_bounded_wait(int32_t device, int32_t polls, int32_t* gave_
   DeviceGuard dg(device);
   if (!dg.ok) return fail(RF_ERR_CUDA, "cannot select device %d", device);
   int* d = nullptr;
-  RF_CUDA(cudaMalloc(&d, sizeof(int)));
+  RF_CUDA(cudaMalloc(&d, 2 * sizeof(int)));
   int h = 0;
-  cudaError_t e = cudaMemset(d, 0, sizeof(int));
+  cudaError_t e = cudaMemset(d, 0, 2 * sizeof(int));
   if (e == cudaSuccess) e = rf::launch_wait_selftest(polls, d, nullptr);
   if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
   cudaFree(d);
   if (e != cudaSuccess) return fail(RF_ERR_CUDA, "bounded-wait check: %s", cudaGetErrorString(e));
-  *gave_up = h;
+  *gave_up = h == 3 ? 1 : 0;  // both waits gave up
   return RF_OK;
 }
 

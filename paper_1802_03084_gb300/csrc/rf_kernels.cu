@@ -674,14 +674,21 @@ bool image_kernel_shape(int npix, ImageKernelShape* out) {
 // ------------------------------------------------------ bounded-wait check --
 namespace rf {
 namespace {
-// The row pass's bounded mbarrier wait on a barrier that nothing arrives at:
-// it must give up and report it (status 1) instead of hanging.
+// The two kinds of bounded device-side wait, each on something that never
+// comes: the row pass's mbarrier wait for a tile copy (on a barrier that
+// nothing arrives at) and the fused pass's wait for a global count (on
+// status[1], which stays 0).  Each must give up and report it instead of
+// hanging: status[0] gets bit 0 for the first, bit 1 for the second.
 __global__ void k_wait_selftest(int polls, int* status) {
   __shared__ __align__(8) unsigned long long bar;
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
   const bool ok = mbar_wait(&bar, 0, polls);
-  if (__syncthreads_or(!ok) && threadIdx.x == 0) *status = 1;
+  const bool gave_up_bar = __syncthreads_or(!ok);
+  if (threadIdx.x == 0) {
+    const bool gave_up_count = !wait_count(status + 1, 1, status + 1, polls);
+    *status = (gave_up_bar ? 1 : 0) | (gave_up_count ? 2 : 0);
+  }
 }
 }  // namespace
 

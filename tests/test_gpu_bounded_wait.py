@@ -1,5 +1,6 @@
-"""The device-side wait of the row pass is bounded: on an mbarrier that nothing
-arrives at it gives up, reports it, and the device stays usable."""
+"""The device-side waits are bounded: the row pass's wait on an mbarrier that
+nothing arrives at and the fused pass's wait on a count that nothing raises
+each give up and report it, and the device stays usable."""
 
 import numpy as np
 import pytest
