@@ -284,7 +284,7 @@ rf_status rf_plan_set_form(struct rf_plan* plan, int32_t form);
  *                      autotuner times both. */
 #define RF_TUNE_FUSED 4
 /* RF_TUNE_RING         chunk slots of the fused pass's ring, 2 .. 8
- *                      (default 2). */
+ *                      (default 3). */
 #define RF_TUNE_RING 5
 rf_status rf_plan_set_tuning(struct rf_plan* plan, int32_t key, int64_t value);
 rf_status rf_plan_get_tuning(const struct rf_plan* plan, int32_t key, int64_t* value);

@@ -55,7 +55,7 @@ constexpr size_t kTBudgetBytes = 4096ull << 20;  // column-FFT scratch per wave
 constexpr int kRangeEntries = 64;                // target entries per gridding warp
 constexpr size_t kPeriodicBudgetBytes = 1ull << 30;  // transformed series per DM batch
 constexpr size_t kPlainBudgetBytes = 4096ull << 20;  // plain form: intermediates of one chunk
-constexpr int kDefaultRing = 2;                      // fused pass: chunk slots of the ring
+constexpr int kDefaultRing = 3;                      // fused pass: chunk slots of the ring
 
 // Round half away from zero: sign(x) floor(|x| + 1/2).
 inline double round_half_away(double x) { return x >= 0.0 ? std::floor(x + 0.5) : -std::floor(-x + 0.5); }
@@ -207,6 +207,7 @@ struct rf_plan {
   std::vector<uint8_t> ongrid;     // [nbl][nchan]
   std::vector<int32_t> col_ent_ptr, col_cell_ptr, cell_row;
   std::vector<int32_t> col_run_ptr, col_runs;  // runs of each column (see DevTables::col_runs)
+  std::vector<float2> col_run_tw;              // their twiddles (see DevTables::col_run_tw)
   std::vector<int2> ranges;
   std::vector<int4> plain_ent;  // {bc, col, row, flags} for the plain form
   std::vector<GridEntry> ent;
@@ -258,7 +259,7 @@ struct rf_plan {
   // fused column + row pass (npix 1024 .. 4096): chunks of the image list,
   // the chunks of each wave, and the L2-resident ring of column-FFT output
   bool fused = false;           // RF_TUNE_FUSED (the autotuner turns it on where it wins)
-  int ring = 2;                 // RF_TUNE_RING
+  int ring = kDefaultRing;      // RF_TUNE_RING
   int chunk_images = 0;         // images per chunk (0: no fused pass at this size)
   std::vector<rf::FusedChunk> chunks;
   std::vector<int2> wave_chunks;  // per wave: [first, last) chunk
@@ -541,6 +542,21 @@ rf_status build_tables(rf_plan* p) {
     }
   }
   p->col_run_ptr[p->ncol] = (int)p->col_runs.size();
+  {
+    // w_N^(v1 p) of every run for p = 1 .. R-1, FP64 and rounded once (the
+    // same values as the length-N twiddle table)
+    const int R = rf::col_split(N);
+    p->col_run_tw.assign(p->col_runs.size() * (size_t)std::max(R - 1, 1), make_float2(0.f, 0.f));
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int col = 0; col < p->ncol; ++col)
+      for (int j = p->col_run_ptr[col]; j < p->col_run_ptr[col + 1]; ++j) {
+        const int v1 = p->cell_row[p->col_cell_ptr[col] + (p->col_runs[j] >> 4)] % Lc;
+        for (int q = 1; q < R; ++q) {
+          const double a = two_pi * (double)((v1 * q) % N) / (double)N;
+          p->col_run_tw[(size_t)j * (R - 1) + q - 1] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+      }
+  }
   cell_start.push_back((int)p->ent.size());
   // Cell-aligned entry ranges of about kRangeEntries entries (a range holds
   // whole cells; a cell with more entries is a range of its own).
@@ -767,7 +783,7 @@ uint64_t estimate_device_bytes(const rf_plan* p, int slots) {
   auto r = [](size_t n, size_t sz) { return (uint64_t)std::max<size_t>(n, 1) * sz; };
   uint64_t b = 0;
   b += r(p->delays.size(), 4) + r(p->dt.size(), 4) + r(p->ranges.size(), 8) + r(p->col_cell_ptr.size(), 4) +
-       r(p->cell_row.size(), 4) + r(p->col_run_ptr.size(), 4) + r(p->col_runs.size(), 4) + r(p->ent.size(), sizeof(GridEntry)) + r(p->ongrid_chan.size(), 4) + r(rf::fft_twiddle_len((int)N), 8);
+       r(p->cell_row.size(), 4) + r(p->col_run_ptr.size(), 4) + r(p->col_runs.size(), 4) + r(p->col_run_tw.size(), 8) + r(p->ent.size(), sizeof(GridEntry)) + r(p->ongrid_chan.size(), 4) + r(rf::fft_twiddle_len((int)N), 8);
   if (rf::col_split((int)N) > 1) b += r(rf::fft_twiddle_len((int)N / rf::col_split((int)N)), 8);
   const size_t nint_pad = (p->max_nint + 31) / 32 * 32;
   const size_t esz = (p->flags & RF_STORE_FP16) ? 4 : 8;
@@ -815,6 +831,7 @@ rf_status alloc_device(rf_plan* p) {
   };
   int32_t *d_delays = nullptr, *d_dt = nullptr, *d_ogc = nullptr, *d_ccp = nullptr, *d_crow = nullptr,
           *d_rptr = nullptr, *d_runs = nullptr;
+  float2* d_rtw = nullptr;
   int2* d_ranges = nullptr;
   GridEntry* d_ent = nullptr;
   rf_status s;
@@ -826,6 +843,7 @@ rf_status alloc_device(rf_plan* p) {
   if ((s = up(&d_crow, p->cell_row)) != RF_OK) return s;
   if ((s = up(&d_rptr, p->col_run_ptr)) != RF_OK) return s;
   if ((s = up(&d_runs, p->col_runs)) != RF_OK) return s;
+  if ((s = up(&d_rtw, p->col_run_tw)) != RF_OK) return s;
   if ((s = up(&d_ent, p->ent)) != RF_OK) return s;
   if ((s = up(&d_ogc, p->ongrid_chan)) != RF_OK) return s;
   std::vector<float2> tw(rf::fft_twiddle_len(N));
@@ -846,6 +864,7 @@ rf_status alloc_device(rf_plan* p) {
   p->tb.cell_row = d_crow;
   p->tb.col_run_ptr = d_rptr;
   p->tb.col_runs = d_runs;
+  p->tb.col_run_tw = d_rtw;
   p->tb.ent = d_ent;
   p->tb.ongrid_chan = d_ogc;
   p->tb.twiddle = d_tw;

@@ -46,6 +46,10 @@ struct DevTables {
   // the first cell counted within the column
   const int32_t* col_run_ptr;   // [ncol + 1]
   const int32_t* col_runs;
+  // per run j and sub-transform p = 1 .. R-1 (R = col_split(N) > 1): the
+  // decimation-in-frequency twiddle w_N^(v1 p) of the run's row v1, at
+  // col_run_tw[j (R - 1) + p - 1] (computed in FP64, rounded once)
+  const float2* col_run_tw;
   // boxcar-resampled Stokes I per dt index s, phase-split: element (row, p, i)
   // at sdt_ptr[s] + row * dt * sdt_lp[s] + p * sdt_lp[s] + i holds
   // sum_{j < dt, i dt + p + j < nint} S[row][i dt + p + j]

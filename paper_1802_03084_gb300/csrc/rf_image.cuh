@@ -85,9 +85,9 @@ struct ColCfg {
   static constexpr int PI = N >= 2048 ? 16 : 32;                // images whose cells are staged at once
   static constexpr int STRIDE = fft_stride<L>();
   // FFT buffers [XA][R][STRIDE]; per cell of the busiest column: the staged
-  // values (PI images), its row and (at most) one run
+  // values (PI images), its row and (at most) one run with its R - 1 twiddles
   static constexpr int SMEM_FIXED = XA * R * STRIDE * 8;
-  static constexpr int SMEM_PER_CELL = PI * 8 + 4 + 4;
+  static constexpr int SMEM_PER_CELL = PI * 8 + 4 + 4 + (R - 1) * 8;
   static_assert(TL <= 32, "column sub-transforms fit one warp");
   static_assert(R <= 8, "at most eight sub-transforms per column");
   static_assert((XA * R * STRIDE * 8) % 16 == 0, "staged cells start 16-byte aligned");
@@ -101,6 +101,10 @@ __device__ __forceinline__ int t_row(int i, int tsplit, int log2l) {
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -120,10 +124,25 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // cell's value).  Only the sub-transform's lanes synchronise.  runs[j] =
 // (first cell << 4) | cells; cellv holds PI images per staged cell, 16-byte
 // chunks swizzled by the cell.  Not live: the buffer stays zero.
+// a times w_R^k, k < R <= 8: exact for the powers of i, the sqrt(1/2)
+// constant for the odd eighths.
+template <int R>
+__device__ __forceinline__ float2 mul_wR(float2 a, int k) {
+  const int e = k * (8 / R);  // eighths of a turn
+  float2 b = a;
+  if (e & 1) b = cmul(a, make_float2(RF_R2_2, RF_R2_2));  // w_8
+  switch (e >> 1) {  // quarter turns
+    case 1: return make_float2(-b.y, b.x);
+    case 2: return make_float2(-b.x, -b.y);
+    case 3: return make_float2(b.y, -b.x);
+    default: return b;
+  }
+}
+
 template <int N, int PI>
 __device__ __forceinline__ void col_scatter(float2* buf, const int* __restrict__ runs, int nruns,
                                             const float2* __restrict__ cellv, const int* __restrict__ crow, int kl,
-                                            bool live, const float2* __restrict__ twN, int t, int p, int xsub) {
+                                            bool live, const float2* __restrict__ rtw, int t, int p, int xsub) {
   using C = ColCfg<N>;
   constexpr int CPC = PI > 1 ? PI / 2 : 1;
   constexpr int L = C::L, R = C::R, TL = C::TL, STRIDE = C::STRIDE;
@@ -143,23 +162,14 @@ __device__ __forceinline__ void col_scatter(float2* buf, const int* __restrict__
       float2 a = cellv[c0 * PI + 2 * (kc ^ (c0 & (CPC - 1))) + ko];
       if constexpr (R > 1) {
         const int n = m & 15;
-        if (p > 0) {
-          int k = ((crow[c0] >> C::LOG2L) * p) & (R - 1);
-          if (k != 0) a = cmul(a, __ldg(twN + k * L));  // w_R^k = w_N^(k L)
-        }
+        if (p > 0) a = mul_wR<R>(a, ((crow[c0] >> C::LOG2L) * p) & (R - 1));
         for (int q = 1; q < n; ++q) {
           const int c = c0 + q;
-          const float2 h = cellv[c * PI + 2 * (kc ^ (c & (CPC - 1))) + ko];
-          const int k = ((crow[c] >> C::LOG2L) * p) & (R - 1);
-          if (k == 0) {
-            a = cadd(a, h);
-          } else {
-            const float2 w = __ldg(twN + k * L);
-            a.x = fmaf(h.x, w.x, fmaf(-h.y, w.y, a.x));
-            a.y = fmaf(h.x, w.y, fmaf(h.y, w.x, a.y));
-          }
+          float2 h = cellv[c * PI + 2 * (kc ^ (c & (CPC - 1))) + ko];
+          if (p > 0) h = mul_wR<R>(h, ((crow[c] >> C::LOG2L) * p) & (R - 1));
+          a = cadd(a, h);
         }
-        if (p > 0) a = cmul(a, __ldg(twN + ((v1 * p) & (N - 1))));  // w_N^(v1 p)
+        if (p > 0) a = cmul(a, rtw[j * (R - 1) + p - 1]);  // w_N^(v1 p), staged per run
       }
       buf[padx(v1)] = a;
     }
@@ -211,7 +221,8 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* fbuf = reinterpret_cast<float2*>(smraw);                       // [XA][R][STRIDE]
   float2* cellv = reinterpret_cast<float2*>(fbuf + C::XA * R * C::STRIDE);  // [max_cells][PI], swizzled
-  int* crow = reinterpret_cast<int*>(cellv + (size_t)g.max_cells * PI);    // [max_cells]
+  float2* rtw = cellv + (size_t)g.max_cells * PI;                           // [max_cells][R - 1]
+  int* crow = reinterpret_cast<int*>(rtw + (size_t)g.max_cells * (R - 1));  // [max_cells]
   int* runs = crow + g.max_cells;                                           // [max_cells]
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -226,6 +237,8 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
   const int nruns = tb.col_run_ptr[col + 1] - run0;
   for (int c = tid; c < ncells; c += C::THREADS) crow[c] = tb.cell_row[cell0 + c];
   for (int j = tid; j < nruns; j += C::THREADS) runs[j] = tb.col_runs[run0 + j];
+  if constexpr (R > 1)
+    for (int i = tid; i < nruns * (R - 1); i += C::THREADS) rtw[i] = tb.col_run_tw[(size_t)run0 * (R - 1) + i];
   const int xf = tid / (R * TL);          // image of the round
   const int p = (tid / TL) % R;           // sub-transform: output rows y = p mod R
   const int t = tid % TL;
@@ -271,7 +284,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
         const int kl = rd * C::XA + xf;
         const bool live = kl < nk;
         float2* dst = live ? Tbuf + ((size_t)(gr.img0 + kbase + kl - img_base) * g.ncol + col) * N + p * L : nullptr;
-        col_scatter<N, PI>(buf, runs, nruns, cellv, crow, kl, live, tb.twiddle, t, p, xf * R + p);
+        col_scatter<N, PI>(buf, runs, nruns, cellv, crow, kl, live, rtw, t, p, xf * R + p);
         col_fft_store<N>(buf, tb.twiddle_col, t, xf * R + p, dst);
       }
     }
@@ -622,7 +635,8 @@ __global__ void __launch_bounds__(FusedCfg<N>::THREADS, 2)
   st0 += (1024u - (smem_u32(st0) & 1023u)) & 1023u;  // swizzle atom alignment of the tile
   float4* tile = reinterpret_cast<float4*>(st0);                           // row role: [rows][CH]
   float2* cellv = reinterpret_cast<float2*>(st0);                          // column role: [max_cells][CI]
-  int* crow = reinterpret_cast<int*>(cellv + (size_t)g.max_cells * CI);    // [max_cells]
+  float2* rtw = cellv + (size_t)g.max_cells * CI;                           // [max_cells][R - 1]
+  int* crow = reinterpret_cast<int*>(rtw + (size_t)g.max_cells * (R - 1));  // [max_cells]
   int* runs = crow + g.max_cells;                                           // [max_cells]
   __shared__ __align__(8) unsigned long long tbar;
   __shared__ int s_q;     // the item after next
@@ -643,21 +657,36 @@ __global__ void __launch_bounds__(FusedCfg<N>::THREADS, 2)
   const int xfb = tid / K::TB, tb_ = tid - xfb * K::TB;                // row role
   const int xfa = tid / (R * TL), pa = (tid / TL) % R, ta = tid % TL;  // column role
 
-  // item q's kind: 0 none, 1 column (chunk c, column a), 2 row (chunk c, image a, block b)
-  auto decode = [&](long qq, int& c, int& a, int& b) -> int {
-    if (qq >= total) return 0;
+  // An item's place in the order: kind 0 none, 1 column (chunk c, column a),
+  // 2 row (chunk c, image a, block b), with its chunk and the wave slot of the
+  // chunk's first image.  The chunk and group loads are issued one item ahead.
+  struct Item {
+    int kind, c, a, b, slot0;
+    FusedChunk ch;
+  };
+  auto locate = [&](long qq) -> Item {  // arithmetic, then the chunk's loads
+    Item it{0, 0, 0, 0, 0, {0, 0, 0, 0}};
+    if (qq >= total) return it;
     const int st = (int)(qq / ips), o = (int)(qq - (long)st * ips);
     if (o < ncol) {
-      c = st;
-      a = o;
-      return st < nchunks ? 1 : 0;
+      it.c = st;
+      it.a = o;
+      it.kind = st < nchunks ? 1 : 0;
+    } else {
+      it.c = st - 1;
+      const int j = o - ncol;
+      it.a = j / NRB;
+      it.b = j - it.a * NRB;
+      it.kind = (it.c >= 0 && it.c < nchunks) ? 2 : 0;
     }
-    c = st - 1;
-    const int j = o - ncol;
-    a = j / NRB;
-    b = j - a * NRB;
-    return (c >= 0 && c < nchunks && a < chunks[c].nk) ? 2 : 0;
+    if (it.kind != 0) {
+      it.ch = chunks[it.c];
+      it.slot0 = groups[it.ch.g].img0 + it.ch.kbase - img_base;
+    }
+    return it;
   };
+  // the kind once the chunk is known: a row item past the chunk's images is none
+  auto kind_of = [&](const Item& it) { return (it.kind == 2 && it.a >= it.ch.nk) ? 0 : it.kind; };
   auto ring_slot = [&](int c, int jj) { return (c % ring) * CI + jj; };
   auto issue_tile = [&](int c, int jj, int rb) {  // thread 0
     fence_proxy_async_global();
@@ -666,14 +695,15 @@ __global__ void __launch_bounds__(FusedCfg<N>::THREADS, 2)
       tma_load_3d(tile + (size_t)bx * tma_rows * K::CH, &tmap, 2 * rb * K::RB, bx * tma_rows, ring_slot(c, jj),
                   &tbar);
   };
-  auto issue_stage = [&](int c, int u) {  // all threads: the column's rows, runs and cells
-    const FusedChunk ch = chunks[c];
+  auto issue_stage = [&](const FusedChunk& ch, int u) {  // all threads: the column's rows, runs and cells
     const int cell0 = tb.col_cell_ptr[u];
     const int nc = tb.col_cell_ptr[u + 1] - cell0;
     const int run0 = tb.col_run_ptr[u];
     const int nr = tb.col_run_ptr[u + 1] - run0;
     for (int cc = tid; cc < nc; cc += F::THREADS) cp_async4(crow + cc, tb.cell_row + cell0 + cc);
     for (int j = tid; j < nr; j += F::THREADS) cp_async4(runs + j, tb.col_runs + run0 + j);
+    if constexpr (R > 1)
+      for (int i = tid; i < nr * (R - 1); i += F::THREADS) cp_async8(rtw + i, tb.col_run_tw + (size_t)run0 * (R - 1) + i);
     const float2* src = cellbuf + ((size_t)(ch.g - g_begin) * g.ncells + cell0) * 32 + ch.kbase;
     for (int i = tid; i < nc * CPC; i += F::THREADS) {
       const int cc = i / CPC;
@@ -685,17 +715,16 @@ __global__ void __launch_bounds__(FusedCfg<N>::THREADS, 2)
   // fill the staging area for item qn after the current item has read it:
   // a column item's stage (all threads), or a row item's tile if its chunk is
   // complete (thread 0; *pf tells)
-  auto prefetch = [&](long qn, bool& stage_ready, int& pf) {
-    int c2 = 0, a2 = 0, b2 = 0;
-    const int k2 = decode(qn, c2, a2, b2);
+  auto prefetch = [&](const Item& nx, bool& stage_ready, int& pf) {
+    const int k2 = kind_of(nx);
     stage_ready = false;
     if (k2 == 2) {
-      if (tid == 0 && ld_acquire_gpu(colcnt + c2) >= ncol * WPB) {
-        issue_tile(c2, a2, b2);
+      if (tid == 0 && ld_acquire_gpu(colcnt + nx.c) >= ncol * WPB) {
+        issue_tile(nx.c, nx.a, nx.b);
         pf = 1;
       }
     } else if (k2 == 1) {
-      issue_stage(c2, a2);
+      issue_stage(nx.ch, nx.a);
       stage_ready = true;
     }
   };
@@ -715,14 +744,16 @@ __global__ void __launch_bounds__(FusedCfg<N>::THREADS, 2)
   unsigned phase = 0;
   bool tile_ready = false;   // a tile copy for item q is in flight
   bool stage_ready = false;  // item q's column stage is in flight (cp.async)
+  Item cur = locate(q);
 
   while (q < total) {
     int qf = 0;
     if (tid == 0) qf = atomicAdd(work, 1);  // the item after next, used at the item's end
+    const Item nxt = locate(qn);             // its loads complete during this item
     int pf = 0;                              // thread 0: a tile copy for item qn was issued
     bool next_stage = false;
-    int c = 0, a = 0, b = 0;
-    const int kind = decode(q, c, a, b);
+    const int kind = kind_of(cur);
+    const int c = cur.c, a = cur.a, b = cur.b;
     if (kind == 2) {
       // ------------------------------------------------------------ row item
       if (!tile_ready) {
@@ -757,21 +788,20 @@ __global__ void __launch_bounds__(FusedCfg<N>::THREADS, 2)
       float2 v[K::EB];
       row_zbuild<N>(v, tile, tb_, xfb, ncol);
       __syncthreads();  // the staging area is read
-      prefetch(qn, next_stage, pf);
-      const FusedChunk ch = chunks[c];
-      const int slot = groups[ch.g].img0 + ch.kbase + a - img_base;
+      prefetch(nxt, next_stage, pf);
+      const int slot = cur.slot0 + a;
       row_finish<N, false>(v, fbuf + xfb * K::STRIDE, tb.twiddle, tb_, xfb, slot, b * K::RB, g.tsplit, log2l,
                            nullptr, img_base, nullptr, partials, nullptr);
     } else if (kind == 1) {
       // --------------------------------------------------------- column item
-      const FusedChunk ch = chunks[c];
+      const FusedChunk ch = cur.ch;
       const int u = a;
       const int ncells = tb.col_cell_ptr[u + 1] - tb.col_cell_ptr[u];
       const int nruns = tb.col_run_ptr[u + 1] - tb.col_run_ptr[u];
-      if (!stage_ready) issue_stage(c, u);
+      if (!stage_ready) issue_stage(ch, u);
       cp_async_wait_all();
       __syncthreads();
-      const int wslot0 = groups[ch.g].img0 + ch.kbase - img_base;
+      const int wslot0 = cur.slot0;
       // Parseval sums of the column, one warp per image
       if (warp < ch.nk) {
         const int kl = warp;
@@ -788,9 +818,9 @@ __global__ void __launch_bounds__(FusedCfg<N>::THREADS, 2)
         }
       }
       float2* buf = fbuf + (xfa * R + pa) * C::STRIDE;
-      col_scatter<N, CI>(buf, runs, nruns, cellv, crow, xfa, xfa < ch.nk, tb.twiddle, ta, pa, xfa * R + pa);
+      col_scatter<N, CI>(buf, runs, nruns, cellv, crow, xfa, xfa < ch.nk, rtw, ta, pa, xfa * R + pa);
       __syncthreads();  // the staging area is read
-      prefetch(qn, next_stage, pf);
+      prefetch(nxt, next_stage, pf);
       // this warp's slot rows are free once the row items of chunk c - ring have read them
       bool ok = true;
       if (c >= ring) {
@@ -801,16 +831,20 @@ __global__ void __launch_bounds__(FusedCfg<N>::THREADS, 2)
       float2* dst = (ok && xfa < ch.nk) ? Tring + ((size_t)ring_slot(c, xfa) * ncol + u) * N + pa * L : nullptr;
       col_fft_store<N>(buf, tb.twiddle_col, ta, xfa * R + pa, dst);
       if (ok) {
-        __threadfence();
-        fence_proxy_async_global();
+        // the warp's stores, then one cumulative fence and the count (the
+        // row items read the slot through the async proxy)
         __syncwarp();
-        if (lane == 0) atomicAdd(colcnt + c, 1);
+        if (lane == 0) {
+          fence_proxy_async_global();
+          __threadfence();
+          atomicAdd(colcnt + c, 1);
+        }
       }
     } else {
       // an empty place of the order (a missing image of a short chunk, the
       // first and last steps): nothing was staged for it
       __syncthreads();
-      prefetch(qn, next_stage, pf);
+      prefetch(nxt, next_stage, pf);
     }
     // end of the item: publish the item after next and the prefetch; stop
     // if any block has given up
@@ -824,6 +858,7 @@ __global__ void __launch_bounds__(FusedCfg<N>::THREADS, 2)
     stage_ready = next_stage;
     q = qn;
     qn = s_q;
+    cur = nxt;
     if (s_fail) {
       if (tid == 0 && tile_ready) mbar_wait(&tbar, phase);
       cp_async_wait_all();
@@ -853,10 +888,6 @@ int max_dynamic_smem(Kernel kern) {
 }
 
 
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
-}
 
 // Periodicity row pass (Sec. 3.1 footnote).  A pair is the two quadrature
 // images (U and Q) of one (DM trial, fluctuation frequency); work item =
@@ -1107,7 +1138,7 @@ cudaError_t run_image_fused(const SegmentGeom& g, const DevTables& tb, const Gro
   if (nchunks <= 0) return cudaSuccess;
   if (tm.nbox <= 0 || ring < 2) return cudaErrorInvalidValue;
   const int tile = rowfft_tile_rows<N>(g.ncol) * K::CH * 16;
-  const int cols = g.max_cells * (F::CI * 8 + 8);
+  const int cols = g.max_cells * (F::CI * 8 + 8 + (C::R - 1) * 8);
   const int smem = F::FB * 8 + 1024 + std::max(tile, cols);
   auto kern = k_image_fused<N>;
   const int smem_max = max_dynamic_smem(kern);

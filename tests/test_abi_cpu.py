@@ -219,7 +219,7 @@ def test_fused_and_ring_tuning_keys(L):
     kw = _desc_kwargs(synth.config("tiny"))
     with rf.Plan(**kw) as p:
         assert rf.rf_plan_get_tuning(p.handle, rf.RF_TUNE_FUSED) == 0
-        assert rf.rf_plan_get_tuning(p.handle, rf.RF_TUNE_RING) == 2
+        assert rf.rf_plan_get_tuning(p.handle, rf.RF_TUNE_RING) == 3
         p.set_fused(True)
         assert rf.rf_plan_get_tuning(p.handle, rf.RF_TUNE_FUSED) == 1
         for bad_key, bad in ((rf.RF_TUNE_FUSED, 2), (rf.RF_TUNE_RING, 1), (rf.RF_TUNE_RING, 9)):
