@@ -110,14 +110,18 @@ struct CandRef {
 // [0, n) hold exp(+2 pi i m / n); when the transform has a second pass
 // (n >= 64) entries n + (r / 2) 64 + 2 k + (r mod 2), r < P2, k < 32, hold
 // that pass's twiddles exp(+2 pi i k r / (32 P2)), P2 = fft_pass2_radix(n)
-// (the two r of a pair side by side, for 16-byte loads).  All are computed
-// in FP64 and rounded to FP32.
+// (the two r of a pair side by side, for 16-byte loads).  For n = 2048 a
+// third section of the same layout, at n + 1024, holds
+// exp(+2 pi i r (2k + 1) / 2048): the second-pass twiddles of the odd-pixel
+// half of a row transform split into two length-1024 transforms, with the
+// split's twiddle exp(+2 pi i r / 2048) folded in.  All are computed in FP64
+// and rounded to FP32.
 constexpr int fft_ilog2(int n) { return n <= 1 ? 0 : 1 + fft_ilog2(n >> 1); }
 constexpr int fft_pass2_radix(int n) {
   // radix-E passes (E = 32, 16 for n = 16), the last of radix n / E^k
   return n < 64 ? 0 : (fft_ilog2(n) < 10 ? (1 << (fft_ilog2(n) - 5)) : 32);
 }
-constexpr int fft_twiddle_len(int n) { return n + 32 * fft_pass2_radix(n); }
+constexpr int fft_twiddle_len(int n) { return n + 32 * fft_pass2_radix(n) + (n == 2048 ? 1024 : 0); }
 // Fills out[0 .. fft_twiddle_len(n)).
 void fft_twiddle_table(int n, float2* out);
 

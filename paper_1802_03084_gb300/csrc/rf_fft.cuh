@@ -89,6 +89,19 @@ __device__ __forceinline__ float2 cmul_i(float2 a) { return make_float2(-a.y, a.
 #define RF_S32_3 0.55557023301960222474f
 #define RF_R2_2 0.70710678118654752440f
 
+// cos(pi k / 32), k = 0 .. 16.
+__host__ __device__ constexpr float cos_pi32(int k) {
+  return k == 0 ? 1.f : k == 1 ? 0.99518472667219688624f : k == 2 ? 0.98078528040323044913f
+       : k == 3 ? 0.95694033573220886494f : k == 4 ? 0.92387953251128675613f : k == 5 ? 0.88192126434835502971f
+       : k == 6 ? 0.83146961230254523708f : k == 7 ? 0.77301045336273696081f : k == 8 ? 0.70710678118654752440f
+       : k == 9 ? 0.63439328416364549822f : k == 10 ? 0.55557023301960222474f : k == 11 ? 0.47139673682599764856f
+       : k == 12 ? 0.38268343236508977173f : k == 13 ? 0.29028467725446236764f : k == 14 ? 0.19509032201612826785f
+       : k == 15 ? 0.09801714032956060199f : 0.f;
+}
+// exp(+2 pi i r / 64) = exp(+i pi r / 32), r = 0 .. 31.
+__host__ __device__ constexpr float cos_r64(int r) { return r <= 16 ? cos_pi32(r) : -cos_pi32(32 - r); }
+__host__ __device__ constexpr float sin_r64(int r) { return cos_pi32(r < 16 ? 16 - r : r - 16); }
+
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
 
 // Padded shared-memory index: one spare slot every 32 complex values.

@@ -58,7 +58,12 @@ struct ImgCfg {
   static constexpr int PARTIALS = (N / 2) * (TB > 32 ? TB / 32 : 1);  // row-pass partials per image
   static constexpr int CH = XB;                                  // 16-byte chunks per tile row
   static constexpr int STRIDE = fft_stride<N>();
-  static constexpr int SMEM_B_FIXED = XB * STRIDE * 8;
+  // N = 2048 (32 values a thread): each row-pair transform is split by one
+  // decimation-in-frequency step into two length-N/2 transforms, the even
+  // and the odd pixels, one per warp of the transform (see row_zbuild)
+  static constexpr int RSPLIT = (N == 2048 && EB == 32) ? 2 : 1;
+  static constexpr int STRIDE_B = RSPLIT * fft_stride<N / RSPLIT>();  // float2 per row transform
+  static constexpr int SMEM_B_FIXED = XB * STRIDE_B * 8;
   // N >= 1024: the row-pass tile arrives by tensor copies (TMA) whose
   // 16 CH-byte rows are swizzled by the hardware: chunk c of row u lands at
   // c ^ ((u >> SWZ_SH) & (CH - 1)) for 128-, 64- and 32-byte rows.  The same
@@ -310,7 +315,44 @@ __device__ __forceinline__ void row_zbuild(float2 (&v)[ImgCfg<N>::EB], const flo
   // Hermitian mirror conj(a) + i conj(b) for N - u < ncol, real parts at
   // u = 0, zero elsewhere (columns beyond iu_max are empty).  N/2 = (EB/2) TB,
   // so r < EB/2 can only be a direct column and r >= EB/2 only a mirror.
-  if constexpr (TB % (K::CH << K::SWZ_SH) == 0) {
+  if constexpr (K::RSPLIT == 2) {
+    // split transform: pixel x = 2 k + s is output k of the length-H = N/2
+    // inverse DFT of Y_s[u'] = (Z[u'] + (-1)^s Z[u' + H]) exp(+2 pi i u' s / N)
+    // (one decimation-in-frequency step).  Warp s of the transform builds
+    // Y_s at u' = j + 32 r (lane j, r < 32): Z[u'] is a direct column or
+    // zero, Z[u' + H] the mirror of column H - u' or zero.  For s = 1 the
+    // factor exp(+2 pi i r / 64) of u' is applied here and exp(+2 pi i j / N)
+    // rides on the second-pass twiddles (see row_finish).
+    constexpr int H = N / 2;
+    static_assert(EB == 32 && TB == 64 && 32 % (K::CH << K::SWZ_SH) == 0, "split row transform layout");
+    const int s = t >> 5, j = t & 31;
+    const int rd_end = ncol > j ? (ncol - j + 31) / 32 : 0;  // j + 32 r < ncol
+    const int xm = H - j - ncol;                              // H - j - 32 r < ncol  <=>  32 r > xm
+    const int rm_beg = xm < 0 ? 0 : xm / 32 + 1;
+    // the swizzle term of u = j + 32 r (H - j - 32 r) is that of j (H - j)
+    const float4* pd = tile + j * K::CH + K::swz(j, xf);
+    const float4* pm = tile + (size_t)(H - j) * K::CH + K::swz(H - j, xf);
+    auto za = [&](int r) {
+      float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < rd_end) ab = pd[r * 32 * K::CH];
+      return (r == 0 && j == 0) ? make_float2(ab.x, ab.z) : make_float2(ab.x - ab.w, ab.y + ab.z);
+    };
+    auto zb = [&](int r) {
+      float4 cd = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r >= rm_beg) cd = pm[-r * 32 * K::CH];
+      return make_float2(cd.x + cd.w, cd.z - cd.y);
+    };
+    if (s == 0) {
+#pragma unroll
+      for (int r = 0; r < 32; ++r) v[r] = cadd(za(r), zb(r));
+    } else {
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        const float2 d = csub(za(r), zb(r));
+        v[r] = r == 0 ? d : (r == 16 ? cmul_i(d) : cmul_c<false>(d, cos_r64(r), sin_r64(r)));
+      }
+    }
+  } else if constexpr (TB % (K::CH << K::SWZ_SH) == 0) {
     // the swizzle term of u = t + r T (or N - t - r T) is that of t (N - t)
     const int rd_end = ncol > t ? (ncol - t + TB - 1) / TB : 0;
     const int rm_beg = (N - ncol - t) / TB + 1;
@@ -358,7 +400,24 @@ __device__ __forceinline__ void row_finish(float2 (&v)[ImgCfg<N>::EB], float2* b
                                            const float2* __restrict__ clip) {
   using K = ImgCfg<N>;
   constexpr int EB = K::EB, TB = K::TB;
-  fft_inverse_from_regs<N, false, EB>(v, buf, tw, t, xf);
+  constexpr int H = N / K::RSPLIT;  // transform length per warp group
+  // split transform (see row_zbuild): warp s runs the length-H transform of
+  // Y_s in its own buffer; its second pass takes the pair table of
+  // exp(+2 pi i k r / H) (s = 0, the table's section at N) or of
+  // exp(+2 pi i r (2k + 1) / N) (s = 1, at N + H), so it is given the
+  // table base tw + H + s H (the transform reads only its pair table)
+  const int s = K::RSPLIT == 2 ? t >> 5 : 0;
+  const int tt = K::RSPLIT == 2 ? t & 31 : t;
+  if constexpr (K::RSPLIT == 2) {
+    fft_inverse_from_regs<H, false, EB>(v, buf + s * fft_stride<H>(), tw + H + s * H, tt, xf);
+  } else {
+    fft_inverse_from_regs<N, false, EB>(v, buf, tw, t, xf);
+  }
+  // pixel of output register (m, q): output o of the transform, or of
+  // sub-transform s as pixel 2 o + s
+  auto pix = [&](int m, int q) {
+    return K::RSPLIT == 2 ? 2 * fft_out_index<H, EB>(tt, m, q) + s : fft_out_index<N, EB>(t, m, q);
+  };
 
   // per-row-pair statistics: the max pixel and its lowest index (the
   // noise comes from the grid by Parseval's identity, see k_colfft).  The
@@ -367,7 +426,7 @@ __device__ __forceinline__ void row_finish(float2 (&v)[ImgCfg<N>::EB], float2* b
   const int i = y0 + 2 * xf;
   const int ya = t_row(i, tsplit, log2l);
   const int yb = t_row(i + 1, tsplit, log2l);
-  constexpr int LP = FftShape<N, EB>::LAST_P;
+  constexpr int LP = FftShape<H, EB>::LAST_P;
   constexpr int EM = EB / LP;
   if (images != nullptr) {
     const double W = weight[img_base + slot];
@@ -379,7 +438,7 @@ __device__ __forceinline__ void row_finish(float2 (&v)[ImgCfg<N>::EB], float2* b
 #pragma unroll
       for (int q = 0; q < LP; ++q) {
         const float2 z = v[m * LP + dft_perm<LP>(q)];
-        const int o = fft_out_index<N, EB>(t, m, q);
+        const int o = pix(m, q);
         ima[o] = z.x * scale;
         imb[o] = z.y * scale;
       }
@@ -413,7 +472,7 @@ __device__ __forceinline__ void row_finish(float2 (&v)[ImgCfg<N>::EB], float2* b
 #pragma unroll
         for (int m = 0; m < EM; ++m)
           if (v[m * LP + dft_perm<LP>(q)].x == wmax) {
-            best = ya * N + fft_out_index<N, EB>(t, m, q);
+            best = ya * N + pix(m, q);
             goto found;
           }
     } else {
@@ -422,7 +481,7 @@ __device__ __forceinline__ void row_finish(float2 (&v)[ImgCfg<N>::EB], float2* b
 #pragma unroll
         for (int m = 0; m < EM; ++m)
           if (v[m * LP + dft_perm<LP>(q)].y == wmax) {
-            best = yb * N + fft_out_index<N, EB>(t, m, q);
+            best = yb * N + pix(m, q);
             goto found;
           }
     }
@@ -505,8 +564,8 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
                    int tma_rows, int* __restrict__ err, const float2* __restrict__ clip) {
   using K = ImgCfg<N>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* fbuf = reinterpret_cast<float2*>(smraw);  // [XB][STRIDE]
-  unsigned char* tb0 = smraw + K::XB * K::STRIDE * 8;
+  float2* fbuf = reinterpret_cast<float2*>(smraw);  // [XB][STRIDE_B]
+  unsigned char* tb0 = smraw + K::XB * K::STRIDE_B * 8;
   if constexpr (K::TILE_TMA) tb0 += (1024u - (smem_u32(tb0) & 1023u)) & 1023u;  // swizzle atom alignment
   float4* tile = reinterpret_cast<float4*>(tb0);    // [rows][CH]
   __shared__ __align__(8) unsigned long long tbar;
@@ -570,7 +629,7 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     row_zbuild<N>(v, tile, t, xf, ncol);
     __syncthreads();  // tile consumed: prefetch the next item
     if (item + (int)gridDim.x < nitems) fetch(item + gridDim.x);
-    row_finish<N, CLIP>(v, fbuf + xf * K::STRIDE, tb.twiddle, t, xf, slot, y0, g.tsplit, log2l,
+    row_finish<N, CLIP>(v, fbuf + xf * K::STRIDE_B, tb.twiddle, t, xf, slot, y0, g.tsplit, log2l,
                         images != nullptr ? weight : nullptr, img_base, images, partials, clip);
   }
 }
@@ -585,7 +644,7 @@ struct FusedCfg {
   using C = ColCfg<N>;
   static constexpr int CI = C::XA;                    // images per chunk
   static constexpr int NRB = N / K::RB;               // row items per image
-  static constexpr int FB = cmax(K::XB * K::STRIDE, C::XA * C::R * C::STRIDE);  // float2 of FFT buffers
+  static constexpr int FB = cmax(K::XB * K::STRIDE_B, C::XA * C::R * C::STRIDE);  // float2 of FFT buffers
   static constexpr int THREADS = K::THREADS_B;
   static_assert(K::THREADS_B == C::THREADS, "one block shape for both roles");
   static_assert(K::TILE_TMA && CI >= 2, "fused pass: N = 1024 .. 4096");
@@ -790,7 +849,7 @@ __global__ void __launch_bounds__(FusedCfg<N>::THREADS, 2)
       __syncthreads();  // the staging area is read
       prefetch(nxt, next_stage, pf);
       const int slot = cur.slot0 + a;
-      row_finish<N, false>(v, fbuf + xfb * K::STRIDE, tb.twiddle, tb_, xfb, slot, b * K::RB, g.tsplit, log2l,
+      row_finish<N, false>(v, fbuf + xfb * K::STRIDE_B, tb.twiddle, tb_, xfb, slot, b * K::RB, g.tsplit, log2l,
                            nullptr, img_base, nullptr, partials, nullptr);
     } else if (kind == 1) {
       // --------------------------------------------------------- column item
@@ -903,8 +962,8 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
   using K = ImgCfg<N>;
   constexpr int EB = K::EB, TB = K::TB;
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* fbuf = reinterpret_cast<float2*>(smraw);                     // [XB][STRIDE]
-  float4* tile = reinterpret_cast<float4*>(fbuf + K::XB * K::STRIDE);  // [ncol][CH]
+  float2* fbuf = reinterpret_cast<float2*>(smraw);                       // [XB][STRIDE_B]
+  float4* tile = reinterpret_cast<float4*>(fbuf + K::XB * K::STRIDE_B);  // [ncol][CH]
   __shared__ float w_max[32];
   __shared__ int w_idx[32];
   const int tid = threadIdx.x;
@@ -979,7 +1038,7 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     }
     __syncthreads();  // tile consumed: prefetch the next item
     if (item + (int)gridDim.x < nitems) prefetch(item + gridDim.x);
-    fft_inverse_from_regs<N, false, EB>(v, fbuf + xf * K::STRIDE, tb.twiddle, t, xf);
+    fft_inverse_from_regs<N, false, EB>(v, fbuf + xf * K::STRIDE_B, tb.twiddle, t, xf);
 
     constexpr int LP = FftShape<N, EB>::LAST_P;
     constexpr int EM = EB / LP;

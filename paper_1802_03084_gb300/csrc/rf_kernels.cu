@@ -29,6 +29,12 @@ void fft_twiddle_table(int n, float2* out) {
       const double a = two_pi * (double)((k * r) % len) / (double)len;
       out[n + (r >> 1) * 64 + 2 * k + (r & 1)] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
+  if (n == 2048)
+    for (int r = 0; r < 32; ++r)
+      for (int k = 0; k < 32; ++k) {
+        const double a = two_pi * (double)((r * (2 * k + 1)) % n) / (double)n;
+        out[n + len + (r >> 1) * 64 + 2 * k + (r & 1)] = make_float2((float)std::cos(a), (float)std::sin(a));
+      }
 }
 
 int sm_count() {

@@ -140,6 +140,47 @@ def test_random_shapes(case):
             assert rel_rms(g[i], o[k]) < IMG_RMS_FP32, (case, k)
 
 
+@pytest.mark.parametrize("npix,width", [(2048, "wide"), (2048, "narrow"), (1024, "wide")])
+def test_row_transform_edge_columns(npix, width):
+    """The row transform's inputs at the edges of the half-plane grid.
+
+    "wide": the cell is set so that the longest baseline at the top channel
+    lands on the last on-grid column, |iu| = N/2 - 1, whose Hermitian mirror
+    is the row input next to the middle (at N = 2048 the split transform's
+    odd-pixel half reads it at u' = 1).  "narrow": a few dozen columns, so
+    most row inputs are zero.  Every image's statistics and candidates, and
+    a few rendered images, against the oracle.
+    """
+    rng = np.random.default_rng(4242 + npix + len(width))
+    nant, nchan, nint = 12, 6, 6
+    seg = small_random_segment(rng, nant, nchan, nint, npix)
+    seg["ant_uvw"][:, 1] *= 0.25                 # east-west: |v| well below |u|
+    bl = oracle.baseline_uvw(seg["ant_uvw"])
+    s_top = seg["freq_hz"].max() / oracle.C_LIGHT
+    k = int(np.argmax(np.abs(bl[:, 0])))
+    target = npix // 2 - 1 if width == "wide" else 24
+    cell = target / (abs(bl[k, 0]) * s_top * npix)
+    spec = synth.SegmentSpec(name="edge", nchan=nchan, f_lo_hz=1e9, bw_hz=1e9, nint=nint, inttime_s=2e-3,
+                             npix=npix, dm_list=np.linspace(0, 20.0, 2), dt_list=[1, 2], threshold=3.0,
+                             nant=nant, cell_rad=cell, edge="partial")
+    gp, op = plans_for(spec, seg)
+    iu_max = int(np.abs(op.iu[op.ongrid]).max())
+    assert iu_max == target, (iu_max, target)
+    with gp:
+        gc, gst = gp.search_stats(seg["vis"])
+        oc, ost = oracle.search_segment(op, seg["vis"], with_stats=True)
+        ok = {k: v for k, v in ost.items()}
+        gst = gst[gst["weight"] > 0]
+        assert len(gst) == len(ok)
+        compare_stats(gst, ok, oracle_images(op, seg["vis"], list(ok)))
+        compare_candidates(gc, oc, spec.threshold, ok)
+        keys = list(ok)[:: max(1, len(ok) // 4)]
+        g = gp.render(seg["vis"], keys)
+        o = oracle_images(op, seg["vis"], keys)
+        for i, key in enumerate(keys):
+            assert rel_rms(g[i], o[key]) < IMG_RMS_FP32, (npix, width, key)
+
+
 def test_fp16_storage_precision(tiny):
     spec, seg, _, op, ocands, ost = tiny
     spec16 = synth.config("tiny")
