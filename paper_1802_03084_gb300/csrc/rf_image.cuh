@@ -332,25 +332,26 @@ __device__ __forceinline__ void row_zbuild(float2 (&v)[ImgCfg<N>::EB], const flo
     // the swizzle term of u = j + 32 r (H - j - 32 r) is that of j (H - j)
     const float4* pd = tile + j * K::CH + K::swz(j, xf);
     const float4* pm = tile + (size_t)(H - j) * K::CH + K::swz(H - j, xf);
-    auto za = [&](int r) {
-      float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
+    // with a = (T[u][y], T[u][y+1]) chunks (ab.x, ab.y), (ab.z, ab.w) of the
+    // direct column and c, d those of the mirror column:
+    //   Z[u'] +- Z[u' + H] = (P.x - Q.y, P.y + Q.x),
+    //   P = a +- conj(c), Q = b +- conj(d)  (one packed FMA each)
+    // except at u' = 0, where Z[0] takes the real parts (a.x, b.x)
+    const float2 pm1 = make_float2(s == 0 ? 1.f : -1.f, s == 0 ? -1.f : 1.f);
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      float4 ab = make_float4(0.f, 0.f, 0.f, 0.f), cd = make_float4(0.f, 0.f, 0.f, 0.f);
       if (r < rd_end) ab = pd[r * 32 * K::CH];
-      return (r == 0 && j == 0) ? make_float2(ab.x, ab.z) : make_float2(ab.x - ab.w, ab.y + ab.z);
-    };
-    auto zb = [&](int r) {
-      float4 cd = make_float4(0.f, 0.f, 0.f, 0.f);
       if (r >= rm_beg) cd = pm[-r * 32 * K::CH];
-      return make_float2(cd.x + cd.w, cd.z - cd.y);
-    };
-    if (s == 0) {
-#pragma unroll
-      for (int r = 0; r < 32; ++r) v[r] = cadd(za(r), zb(r));
-    } else {
-#pragma unroll
-      for (int r = 0; r < 32; ++r) {
-        const float2 d = csub(za(r), zb(r));
-        v[r] = r == 0 ? d : (r == 16 ? cmul_i(d) : cmul_c<false>(d, cos_r64(r), sin_r64(r)));
+      const float2 P = f2_fma(make_float2(cd.x, cd.y), pm1, make_float2(ab.x, ab.y));
+      const float2 Q = f2_fma(make_float2(cd.z, cd.w), pm1, make_float2(ab.z, ab.w));
+      float2 d = make_float2(P.x - Q.y, P.y + Q.x);
+      if (r == 0 && j == 0) {
+        const float sg = s == 0 ? 1.f : -1.f;
+        d = make_float2(fmaf(sg, cd.x + cd.w, ab.x), fmaf(sg, cd.z - cd.y, ab.z));
       }
+      if (s != 0 && r > 0) d = r == 16 ? cmul_i(d) : cmul_c<false>(d, cos_r64(r), sin_r64(r));
+      v[r] = d;
     }
   } else if constexpr (TB % (K::CH << K::SWZ_SH) == 0) {
     // the swizzle term of u = t + r T (or N - t - r T) is that of t (N - t)
@@ -569,6 +570,7 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
   if constexpr (K::TILE_TMA) tb0 += (1024u - (smem_u32(tb0) & 1023u)) & 1023u;  // swizzle atom alignment
   float4* tile = reinterpret_cast<float4*>(tb0);    // [rows][CH]
   __shared__ __align__(8) unsigned long long tbar;
+  __shared__ int s_done;  // warps done reading the tile in hand (warp-local transforms)
   const int tid = threadIdx.x;
   const int ncol = g.ncol;
   constexpr int nrb = N / K::RB;
@@ -577,20 +579,32 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
   const int t = tid - xf * K::TB;
   const int log2l = FftShape<N>::LOG2N - (g.tsplit > 1 ? __ffs(g.tsplit) - 1 : 0);
   const bool use_tma = K::TILE_TMA && tma_boxes > 0;
+  // With tensor copies and transforms that synchronise only within a warp,
+  // the warps of a block do not wait for one another: each waits for the
+  // tile on its own, and the last warp to finish reading it issues the next
+  // item's copy.  Otherwise two block barriers per item.
+  constexpr bool WARP_LOCAL = K::TILE_TMA && (K::TB <= 32 || K::RSPLIT == 2);
+  constexpr int NWB = K::THREADS_B / 32;
   unsigned phase = 0;
   if (use_tma) {
-    if (tid == 0) mbar_init(&tbar, 1);
+    if (tid == 0) {
+      mbar_init(&tbar, 1);
+      s_done = 0;
+    }
     __syncthreads();
   }
+  auto issue_tma = [&](int it) {  // by one thread
+    const int sl = it / nrb;
+    const int yb = (it - sl * nrb) * K::RB;
+    mbar_expect_tx(&tbar, (unsigned)(tma_boxes * tma_rows * K::CH * 16));
+    for (int b = 0; b < tma_boxes; ++b)
+      tma_load_3d(tile + (size_t)b * tma_rows * K::CH, &tmap, 2 * yb, b * tma_rows, sl, &tbar);
+  };
   auto fetch = [&](int it) {
     const int sl = it / nrb;
     const int yb = (it - sl * nrb) * K::RB;
     if (use_tma) {
-      if (tid == 0) {
-        mbar_expect_tx(&tbar, (unsigned)(tma_boxes * tma_rows * K::CH * 16));
-        for (int b = 0; b < tma_boxes; ++b)
-          tma_load_3d(tile + (size_t)b * tma_rows * K::CH, &tmap, 2 * yb, b * tma_rows, sl, &tbar);
-      }
+      if (tid == 0) issue_tma(it);
     } else {
       const float2* src = Tbuf + (size_t)sl * ncol * N + yb;
       for (int i = tid; i < ncol * K::CH; i += K::THREADS_B) {
@@ -605,7 +619,18 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
   int item = blockIdx.x;
   if (item < nitems) fetch(item);
   for (; item < nitems; item += gridDim.x) {
-    if (use_tma) {
+    if (use_tma && WARP_LOCAL) {
+      // a warp whose bounded wait gives up reports it, waits once more (so
+      // that a late copy does not land after the block has left) and leaves;
+      // no later copy is issued without its arrival below, so the other
+      // warps' waits run out in turn
+      if (!__all_sync(0xffffffffu, mbar_wait(&tbar, phase))) {
+        if ((tid & 31) == 0) atomicExch(err, 1);
+        mbar_wait(&tbar, phase);
+        return;
+      }
+      phase ^= 1u;
+    } else if (use_tma) {
       const bool ok = mbar_wait(&tbar, phase);
       if (__syncthreads_or(!ok)) {
         // the item's tile copy has not completed: give it one more bounded
@@ -627,8 +652,25 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     const int y0 = (item - slot * nrb) * K::RB;
     float2 v[K::EB];
     row_zbuild<N>(v, tile, t, xf, ncol);
-    __syncthreads();  // tile consumed: prefetch the next item
-    if (item + (int)gridDim.x < nitems) fetch(item + gridDim.x);
+    if (use_tma && WARP_LOCAL) {
+      // tile consumed by this warp; the last of the block's warps resets the
+      // count and issues the next item's copy (no warp waits for the tile
+      // of item + 2 grid strides before every warp has read item + 1's)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if ((tid & 31) == 0) {
+        __threadfence_block();
+        if (atomicAdd(&s_done, 1) == NWB - 1) {
+          s_done = 0;
+          __threadfence_block();
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          if (item + (int)gridDim.x < nitems) issue_tma(item + gridDim.x);
+        }
+      }
+    } else {
+      __syncthreads();  // tile consumed: prefetch the next item
+      if (item + (int)gridDim.x < nitems) fetch(item + gridDim.x);
+    }
     row_finish<N, CLIP>(v, fbuf + xf * K::STRIDE_B, tb.twiddle, t, xf, slot, y0, g.tsplit, log2l,
                         images != nullptr ? weight : nullptr, img_base, images, partials, clip);
   }
