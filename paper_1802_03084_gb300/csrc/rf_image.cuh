@@ -332,8 +332,8 @@ __device__ __forceinline__ void row_zbuild(float2 (&v)[ImgCfg<N>::EB], const flo
     // the swizzle term of u = j + 32 r (H - j - 32 r) is that of j (H - j)
     const float4* pd = tile + j * K::CH + K::swz(j, xf);
     const float4* pm = tile + (size_t)(H - j) * K::CH + K::swz(H - j, xf);
-    // with a = (T[u][y], T[u][y+1]) chunks (ab.x, ab.y), (ab.z, ab.w) of the
-    // direct column and c, d those of the mirror column:
+    // with a = T[u'][y] = (ab.x, ab.y) and b = T[u'][y+1] = (ab.z, ab.w) of
+    // the direct column u', and c, d the same of the mirror column H - u':
     //   Z[u'] +- Z[u' + H] = (P.x - Q.y, P.y + Q.x),
     //   P = a +- conj(c), Q = b +- conj(d)  (one packed FMA each)
     // except at u' = 0, where Z[0] takes the real parts (a.x, b.x)
