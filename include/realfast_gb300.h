@@ -526,7 +526,8 @@ typedef struct rf_periodic_candidate {
  * order, with snr etc. set whether or not it is a candidate; *n_stats =
  * (DM trials that fit) * (kmax - kmin + 1).  Device scratch is allocated for
  * the call.  Errors: RF_ERR_INVALID_ARG, RF_ERR_SHAPE, RF_ERR_NO_MEMORY,
- * RF_ERR_BUSY, RF_ERR_CAPACITY. */
+ * RF_ERR_BUSY, RF_ERR_CAPACITY, RF_ERR_TIMEOUT (a bounded device-side wait
+ * for a row-pass tile copy gave up; the plan stays usable). */
 rf_status rf_periodicity_search(struct rf_plan* plan, const void* vis, int32_t nint, int32_t L, int32_t kmin,
                                 int32_t kmax, double threshold, void* stream, rf_periodic_candidate* out,
                                 size_t cap, size_t* n_out, rf_periodic_candidate* stats, size_t stats_cap,

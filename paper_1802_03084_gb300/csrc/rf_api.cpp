@@ -238,6 +238,7 @@ struct rf_plan {
   int2* d_cellbc = nullptr;     // [nchan * nbl] (iu, iv) per row, for candidate spectra
   int* d_err = nullptr;         // set by a kernel whose bounded wait gave up
   rf::TileMap tmap_T{};         // tensor map of d_T for the row pass (nbox 0: none)
+  rf::TileMap tmap_P{};         // tensor map of d_T for the periodicity row pass (N = 1024)
   float2* d_stage = nullptr;
   int stage_nint = 0;
 
@@ -671,23 +672,27 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // work item's 2 XB rows (XB 16-byte chunks) by `rows` columns u, swizzled so
 // that chunk c of column u lands at c ^ ((u >> sh) & (XB - 1)).  Where the
 // encoder is unavailable the row pass copies with cp.async (nbox = 0).
-void encode_tile_map(rf_plan* p, rf::TileMap& tm, float2* base, int slots) {
+// Tensor map of T ([slot][u][N complex]) whose boxes hold `trows` T rows of
+// `rows` u rows; box rows of 128, 64 or 32 bytes are swizzled in that mode.
+// The search's row pass takes the 2 XB rows of a work item (trows = 2 XB),
+// the periodicity row pass the XB rows of one image (trows = XB).
+void encode_tile_map(rf_plan* p, rf::TileMap& tm, float2* base, int slots, int trows) {
   tm.nbox = 0;
   const int N = p->npix;
   if (N < 1024 || !base || slots <= 0) return;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return;
-  const int xb = std::min(256 / (N / 32), N / 2);
   int nbox, rows;
   rf::tile_boxes(p->ncol, &nbox, &rows);
+  const int row_bytes = trows * 8;
   const cuuint64_t dims[3] = {(cuuint64_t)2 * N, (cuuint64_t)p->ncol, (cuuint64_t)slots};
   const cuuint64_t strides[2] = {(cuuint64_t)N * 8, (cuuint64_t)p->ncol * N * 8};
-  const cuuint32_t box[3] = {(cuuint32_t)(4 * xb), (cuuint32_t)rows, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * trows), (cuuint32_t)rows, 1};
   const cuuint32_t es[3] = {1, 1, 1};
-  const CUtensorMapSwizzle sw = xb == 8   ? CU_TENSOR_MAP_SWIZZLE_128B
-                                : xb == 4 ? CU_TENSOR_MAP_SWIZZLE_64B
-                                : xb == 2 ? CU_TENSOR_MAP_SWIZZLE_32B
-                                          : CU_TENSOR_MAP_SWIZZLE_NONE;
+  const CUtensorMapSwizzle sw = row_bytes == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                : row_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                                  : CU_TENSOR_MAP_SWIZZLE_NONE;
   const CUresult r = enc(&tm.map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -704,7 +709,8 @@ rf_status alloc_wave_scratch(rf_plan* p, int slots) {
   slots = std::max(std::min(slots, 32768), B);
   const size_t per_slot = (size_t)p->ncol * p->npix;
   const int nrb = p->shape.partials_per_image;
-  p->tmap_T.nbox = 0;  // the map describes d_T, about to be freed
+  p->tmap_T.nbox = 0;  // the maps describe d_T, about to be freed
+  p->tmap_P.nbox = 0;
   if (p->d_T) {
     p->device_bytes -= (uint64_t)p->slots_max * per_slot * sizeof(float2);
     p->dfree(p->d_T);
@@ -742,7 +748,11 @@ rf_status alloc_wave_scratch(rf_plan* p, int slots) {
   if ((s = p->dalloc(&p->d_colsq, (size_t)slots * p->ncol)) != RF_OK) return s;
   if ((s = p->dalloc(&p->d_mean0, (size_t)slots)) != RF_OK) return s;
   if ((p->flags & RF_NOISE_CLIPPED) && (s = p->dalloc(&p->d_clip, (size_t)slots)) != RF_OK) return s;
-  encode_tile_map(p, p->tmap_T, p->d_T, p->slots_max);
+  const int xb = std::min(256 / (p->npix / 32), p->npix / 2);  // row pairs of a row-pass work item
+  encode_tile_map(p, p->tmap_T, p->d_T, p->slots_max, 2 * xb);
+  // the periodicity row pass's tensor-copy tiles (one image's XB rows), at
+  // N = 1024, where its transforms fit one warp
+  if (p->npix == 1024) encode_tile_map(p, p->tmap_P, p->d_T, p->slots_max, xb);
   // fused pass: counters for the most chunks a wave can hold
   if (p->chunk_images > 0) {
     const int cap = 1 + 2 * p->gslots_max * ((p->shape.images_per_group + p->chunk_images - 1) / p->chunk_images);
@@ -771,7 +781,8 @@ rf_status alloc_ring(rf_plan* p, int ring) {
   rf_status s = p->dalloc(&p->d_Tring, (size_t)ring * per_ring);
   if (s != RF_OK) return s;
   p->ring = p->ring_alloc = ring;
-  encode_tile_map(p, p->tmap_ring, p->d_Tring, ring * p->chunk_images);
+  encode_tile_map(p, p->tmap_ring, p->d_Tring, ring * p->chunk_images,
+                  2 * std::min(256 / (p->npix / 32), p->npix / 2));
   return RF_OK;
 }
 
@@ -1757,13 +1768,23 @@ rf_status rf_periodicity_search(rf_plan* p, const void* vis, int32_t nint, int32
       const int np = v.p1 - v.p0;
       RF_CUDA(rf::launch_grid_cells(gp, tbp, d_grp, v.g0, ng, p->d_cellbuf, st));
       RF_CUDA(rf::launch_colfft(gp, tbp, d_grp, v.g0, ng, v.i0, p->d_cellbuf, p->d_T, p->d_colsq, p->d_mean0, st));
-      RF_CUDA(rf::launch_rowfft_power(gp, tbp, p->d_T, d_pairs + v.p0, np, p->d_partials, st));
+      RF_CUDA(rf::launch_rowfft_power(gp, tbp, p->d_T, d_pairs + v.p0, np, p->d_partials,
+                                      p->tmap_P.nbox > 0 ? &p->tmap_P : nullptr, p->d_err, st));
       RF_CUDA(rf::launch_finalize_power(gp, p->d_partials, p->d_colsq, p->d_mean0, d_pairs + v.p0, np,
                                         (int)(pbase + v.p0), (double)p->n_on, threshold, d_pst, d_pc, d_npc,
                                         (int)npairs_total, st));
     }
     // the host lists above are reused by the next batch
     RF_CUDA(cudaStreamSynchronize(st));
+  }
+  {
+    int kerr = 0;
+    RF_CUDA(cudaMemcpyAsync(&kerr, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RF_CUDA(cudaStreamSynchronize(st));
+    if (kerr) {
+      cudaMemset(p->d_err, 0, sizeof(int));
+      return fail(RF_ERR_TIMEOUT, "a periodicity row-pass tile copy did not complete within its wait limit");
+    }
   }
   int npc = 0;
   RF_CUDA(cudaMemcpyAsync(&npc, d_npc, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -329,8 +329,10 @@ cudaError_t launch_image_moments(const float* images, int n, size_t npx, int nsl
 cudaError_t launch_period_dft(const SegmentGeom& g, const void* S, const int* delays, const int* dms, int nb,
                               int L, const float2* twl, int kmin, int K, int kpad, float2* out, cudaStream_t st);
 // Row pass over npairs (U, Q) image pairs: partials[j * N + y] = row maxima of I_U^2 + I_Q^2.
+// tm (may be null): tensor map of Tbuf with boxes of one image's XB rows, for
+// the tensor-copy tiles at N = 1024; err: set when a bounded tile wait gives up.
 cudaError_t launch_rowfft_power(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, const int4* pairs,
-                                int npairs, StatPartial* partials, cudaStream_t st);
+                                int npairs, StatPartial* partials, const TileMap* tm, int* err, cudaStream_t st);
 // Per pair: amplitude, sigma, snr, pixel; stats[pair_base + j]; candidates appended.
 cudaError_t launch_finalize_power(const SegmentGeom& g, const StatPartial* partials, const float* colsq,
                                   const float* mean0, const int4* pairs, int npairs, int pair_base, double W,

@@ -997,17 +997,39 @@ int max_dynamic_smem(Kernel kern) {
 // pass), so its output holds row y of I_U in the real parts and of I_Q in
 // the imaginary parts.  Per row it writes the maximum of I_U^2 + I_Q^2 (raw
 // pixel units) and its lowest index.  pairs[j] = {U slot, Q slot, -, -}.
+// The tile is [ncol][CH] 16-byte chunks {U[u][y], Q[u][y]} copied with
+// cp.async, or, where every transform fits one warp and tma_boxes > 0
+// (N = 1024), two tiles [rows][XB] of U and of Q rows, each filled by
+// tma_boxes tensor copies of tma_rows u rows from `tmap` ([slot][u][2N
+// floats], boxes of XB complex values, 64-byte rows swizzled by the hardware:
+// chunk c of row u at c ^ ((u >> 1) & 3)).  Then, as in the search's row
+// pass, no block barrier is left: each warp waits for the tiles on an
+// mbarrier (bounded; a warp that gives up sets *err, waits once more and
+// leaves) and the last warp to read them issues the next item's copies.
 template <int N>
 __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
     k_rowfft_power(SegmentGeom g, DevTables tb, const float2* __restrict__ Tbuf, const int4* __restrict__ pairs,
-                   int npairs, StatPartial* __restrict__ partials) {
+                   int npairs, StatPartial* __restrict__ partials, const __grid_constant__ CUtensorMap tmap,
+                   int tma_boxes, int tma_rows, int* __restrict__ err) {
   using K = ImgCfg<N>;
   constexpr int EB = K::EB, TB = K::TB;
+  constexpr bool PTMA = K::TILE_TMA && TB <= 32;  // warp-local transforms (N = 1024)
+  static_assert(!PTMA || (K::XB == 8 && EB == 32), "power tiles: 64-byte rows of 8 complex values");
+  constexpr int NWB = K::THREADS_B / 32;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* fbuf = reinterpret_cast<float2*>(smraw);                       // [XB][STRIDE_B]
   float4* tile = reinterpret_cast<float4*>(fbuf + K::XB * K::STRIDE_B);  // [ncol][CH]
+  // tensor-copy tiles of U and Q rows, [rows][4 chunks]: U 1024-byte
+  // aligned, Q 512 bytes after it (the 64-byte swizzle repeats every 8 rows)
+  unsigned char* tu0 = smraw + K::XB * K::STRIDE_B * 8;
+  tu0 += (1024u - (smem_u32(tu0) & 1023u)) & 1023u;
+  const unsigned tsz = ((unsigned)(tma_boxes * tma_rows * K::XB * 8) + 511u) & ~511u;
+  float2* tileU = reinterpret_cast<float2*>(tu0);
+  float2* tileQ = reinterpret_cast<float2*>(tu0 + tsz);
   __shared__ float w_max[32];
   __shared__ int w_idx[32];
+  __shared__ __align__(8) unsigned long long tbar;
+  __shared__ int s_done;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int wid = tid >> 5;
@@ -1018,7 +1040,30 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
   const int t = tid - xf * TB;
   const int log2l = FftShape<N>::LOG2N - (g.tsplit > 1 ? __ffs(g.tsplit) - 1 : 0);
 
+  const bool use_tma = PTMA && tma_boxes > 0;
+  unsigned phase = 0;
+  if (use_tma) {
+    if (tid == 0) {
+      mbar_init(&tbar, 1);
+      s_done = 0;
+    }
+    __syncthreads();
+  }
+  auto issue_tma = [&](int it) {  // by one thread
+    const int pj = it / nrb;
+    const int yb = (it - pj * nrb) * K::XB;
+    const int4 pr = pairs[pj];
+    mbar_expect_tx(&tbar, (unsigned)(2 * tma_boxes * tma_rows * K::XB * 8));
+    for (int b = 0; b < tma_boxes; ++b) {
+      tma_load_3d(tileU + (size_t)b * tma_rows * K::XB, &tmap, 2 * yb, b * tma_rows, pr.x, &tbar);
+      tma_load_3d(tileQ + (size_t)b * tma_rows * K::XB, &tmap, 2 * yb, b * tma_rows, pr.y, &tbar);
+    }
+  };
   auto prefetch = [&](int it) {
+    if (use_tma) {
+      if (tid == 0) issue_tma(it);
+      return;
+    }
     const int pj = it / nrb;
     const int yb = (it - pj * nrb) * K::XB;
     const int4 pr = pairs[pj];
@@ -1037,13 +1082,52 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
   int item = blockIdx.x;
   if (item < nitems) prefetch(item);
   for (; item < nitems; item += gridDim.x) {
-    cp_async_wait_all();
-    __syncthreads();
+    if (use_tma) {
+      if (!__all_sync(0xffffffffu, mbar_wait(&tbar, phase))) {
+        if (lane == 0) atomicExch(err, 1);
+        mbar_wait(&tbar, phase);
+        return;
+      }
+      phase ^= 1u;
+    } else {
+      cp_async_wait_all();
+      __syncthreads();
+    }
     const int pj = item / nrb;
     const int iy = (item - pj * nrb) * K::XB + xf;   // T row; image row y below
     const int y = t_row(iy, g.tsplit, log2l);
     float2 v[EB];
-    if constexpr (TB % K::CH == 0) {
+    if (PTMA && use_tma) {
+      // the U and Q tiles: complex value xf of u row u is half (xf & 1) of
+      // chunk (xf >> 1) ^ ((u >> 1) & 3); for u = t + 32 r (N - t - 32 r)
+      // the swizzle term is that of t (N - t)
+      const int rd_end = ncol > t ? (ncol - t + TB - 1) / TB : 0;
+      const int rm_beg = (N - ncol - t) / TB + 1;
+      auto at = [&](int u) { return (u * 4 + ((xf >> 1) ^ ((u >> 1) & 3))) * 2 + (xf & 1); };
+      const float2* pdu = tileU + at(t);
+      const float2* pdq = tileQ + at(t);
+      const float2* pmu = tileU + at(N - t);
+      const float2* pmq = tileQ + at(N - t);
+      constexpr int RS = TB * 4 * 2;  // float2 per 32 u rows
+#pragma unroll
+      for (int r = 0; r < EB / 2; ++r) {
+        float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+        if (r < rd_end) {
+          a = pdu[r * RS];
+          b = pdq[r * RS];
+        }
+        v[r] = (r == 0 && t == 0) ? make_float2(a.x, b.x) : make_float2(a.x - b.y, a.y + b.x);
+      }
+#pragma unroll
+      for (int r = EB / 2; r < EB; ++r) {
+        float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+        if (r >= rm_beg) {
+          a = pmu[-r * RS];
+          b = pmq[-r * RS];
+        }
+        v[r] = make_float2(a.x + b.y, b.x - a.y);
+      }
+    } else if constexpr (TB % K::CH == 0) {
       // as in the search's row pass: u = t + r T (or N - t - r T) has the
       // swizzle term of t (N - t), and the loads are predicated, not branched
       const int rd_end = ncol > t ? (ncol - t + TB - 1) / TB : 0;
@@ -1078,8 +1162,24 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
         v[r] = z;
       }
     }
-    __syncthreads();  // tile consumed: prefetch the next item
-    if (item + (int)gridDim.x < nitems) prefetch(item + gridDim.x);
+    if (use_tma) {
+      // tiles read by this warp; the last of the block's warps issues the
+      // next item's copies
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence_block();
+        if (atomicAdd(&s_done, 1) == NWB - 1) {
+          s_done = 0;
+          __threadfence_block();
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          if (item + (int)gridDim.x < nitems) issue_tma(item + gridDim.x);
+        }
+      }
+    } else {
+      __syncthreads();  // tile consumed: prefetch the next item
+      if (item + (int)gridDim.x < nitems) prefetch(item + gridDim.x);
+    }
     fft_inverse_from_regs<N, false, EB>(v, fbuf + xf * K::STRIDE_B, tb.twiddle, t, xf);
 
     constexpr int LP = FftShape<N, EB>::LAST_P;
@@ -1142,9 +1242,12 @@ __global__ void __launch_bounds__(ImgCfg<N>::THREADS_B, 2)
 
 template <int N>
 cudaError_t run_rowfft_power(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, const int4* pairs,
-                             int npairs, StatPartial* partials, cudaStream_t st) {
+                             int npairs, StatPartial* partials, const TileMap* tm, int* err, cudaStream_t st) {
   using K = ImgCfg<N>;
-  const int smem = K::SMEM_B_FIXED + g.ncol * K::CH * 16;
+  // tensor-copy tiles where every transform fits one warp (see k_rowfft_power)
+  const bool tma = K::TILE_TMA && K::TB <= 32 && tm != nullptr && tm->nbox > 0 && err != nullptr;
+  const int tsz = tma ? (tm->nbox * tm->rows * K::XB * 8 + 511) / 512 * 512 : 0;
+  const int smem = tma ? K::SMEM_B_FIXED + 1024 + 2 * tsz : K::SMEM_B_FIXED + g.ncol * K::CH * 16;
   const int smem_max = max_dynamic_smem(k_rowfft_power<N>);
   if (smem > smem_max) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_rowfft_power<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
@@ -1158,7 +1261,11 @@ cudaError_t run_rowfft_power(const SegmentGeom& g, const DevTables& tb, const fl
   if (e != cudaSuccess) return e;
   const long nitems = (long)npairs * (N / K::XB);
   const long grid = std::min<long>(nitems, (long)std::max(per_sm, 1) * sm_count());
-  k_rowfft_power<N><<<(int)grid, K::THREADS_B, smem, st>>>(g, tb, Tbuf, pairs, npairs, partials);
+  CUtensorMap none;
+  memset(&none, 0, sizeof(none));
+  k_rowfft_power<N><<<(int)grid, K::THREADS_B, smem, st>>>(g, tb, Tbuf, pairs, npairs, partials,
+                                                           tma ? tm->map : none, tma ? tm->nbox : 0,
+                                                           tma ? tm->rows : 0, err);
   return cudaGetLastError();
 }
 
@@ -1285,7 +1392,7 @@ void fill_shape(ImageKernelShape* o) {
                                            cudaStream_t, const float2*);                                    \
   template void fill_shape<N>(ImageKernelShape*);                                                           \
   template cudaError_t run_rowfft_power<N>(const SegmentGeom&, const DevTables&, const float2*, const int4*, \
-                                           int, StatPartial*, cudaStream_t);
+                                           int, StatPartial*, const TileMap*, int*, cudaStream_t);
 
 #define RF_INSTANTIATE_FUSED(N)                                                                              \
   template cudaError_t run_image_fused<N>(const SegmentGeom&, const DevTables&, const Group*, int,            \

@@ -584,7 +584,7 @@ template <int N>
 void fill_shape(ImageKernelShape*);
 template <int N>
 cudaError_t run_rowfft_power(const SegmentGeom&, const DevTables&, const float2*, const int4*, int, StatPartial*,
-                             cudaStream_t);
+                             const TileMap*, int*, cudaStream_t);
 
 template <int N>
 cudaError_t run_image_fused(const SegmentGeom&, const DevTables&, const Group*, int, const FusedChunk*, int, int,
@@ -650,11 +650,11 @@ cudaError_t launch_rowfft_stats(const SegmentGeom& g, const DevTables& tb, const
 }
 
 cudaError_t launch_rowfft_power(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, const int4* pairs,
-                                int npairs, StatPartial* partials, cudaStream_t st) {
+                                int npairs, StatPartial* partials, const TileMap* tm, int* err, cudaStream_t st) {
   switch (g.npix) {
 #define RF_CASE(N) \
   case N:          \
-    return run_rowfft_power<N>(g, tb, Tbuf, pairs, npairs, partials, st);
+    return run_rowfft_power<N>(g, tb, Tbuf, pairs, npairs, partials, tm, err, st);
     RF_FOR_EACH_N(RF_CASE)
 #undef RF_CASE
     default:

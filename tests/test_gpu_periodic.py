@@ -23,8 +23,10 @@ def engine():
     yield
 
 
-def _train_spec(store="fp32", nint=160):
+def _train_spec(store="fp32", nint=160, npix=None):
     spec = synth.config("tiny")
+    if npix:
+        spec.npix = npix
     spec.store = store
     spec.edge = "full"
     spec.nint = nint
@@ -50,10 +52,12 @@ def _compare(gst, ost, op, S, L, rtol):
             assert o.amplitude ** 2 - P[int(r["y"]), int(r["x"])] <= 4 * rtol * o.amplitude ** 2, key
 
 
-@pytest.mark.parametrize("store,L,kmin,kmax,nint", [("fp32", 64, 1, 32, 160), ("fp32", 128, 3, 40, 224),
-                                                    ("fp16", 64, 1, 32, 160)])
-def test_periodicity_search_matches_oracle(store, L, kmin, kmax, nint):
-    spec = _train_spec(store, nint)
+@pytest.mark.parametrize("store,L,kmin,kmax,nint,npix", [
+    ("fp32", 64, 1, 32, 160, None), ("fp32", 128, 3, 40, 224, None), ("fp16", 64, 1, 32, 160, None),
+    # 1024^2: the row pass's tiles by tensor copies, warps without block barriers
+    ("fp32", 64, 1, 32, 160, 1024), ("fp16", 64, 5, 12, 160, 1024)])
+def test_periodicity_search_matches_oracle(store, L, kmin, kmax, nint, npix):
+    spec = _train_spec(store, nint, npix)
     seg = synth.make_segment(spec)
     gp, op = plans_for(spec, seg)
     nint = seg["vis"].shape[0]
