@@ -55,7 +55,9 @@ def _compare(gst, ost, op, S, L, rtol):
 @pytest.mark.parametrize("store,L,kmin,kmax,nint,npix", [
     ("fp32", 64, 1, 32, 160, None), ("fp32", 128, 3, 40, 224, None), ("fp16", 64, 1, 32, 160, None),
     # 1024^2: the row pass's tiles by tensor copies, warps without block barriers
-    ("fp32", 64, 1, 32, 160, 1024), ("fp16", 64, 5, 12, 160, 1024)])
+    ("fp32", 64, 1, 32, 160, 1024), ("fp16", 64, 5, 12, 160, 1024),
+    # 2048^2: cp.async tiles, transforms of two warps
+    ("fp32", 64, 7, 10, 160, 2048)])
 def test_periodicity_search_matches_oracle(store, L, kmin, kmax, nint, npix):
     spec = _train_spec(store, nint, npix)
     seg = synth.make_segment(spec)
