@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--fused", type=int, default=-1, choices=[-1, 0, 1],
                     help="force the fused imaging pass off (0) or on (1); -1: the autotuner's or default choice")
     ap.add_argument("--ring", type=int, default=0, help="chunk slots of the fused pass's ring (0: default)")
+    ap.add_argument("--overlap", type=int, default=-1, choices=[-1, 0, 1],
+                    help="force overlapped waves off (0) or on (1); -1: the autotuner's or default choice")
     ap.add_argument("--tune-cache", default=os.path.expanduser("~/.cache/realfast_gb300/tune.json"))
     ap.add_argument("--serving", action="store_true",
                     help="Poisson stream of mixed-shape segments at 1.0x real time through rf_server_*")
@@ -677,6 +679,8 @@ def run_workload(args, config, rank, world, dist, local_rank, lite=False):
         tuning = plan.autotune(vis_dev, nint, cache_path=args.tune_cache)
     if args.fused >= 0:
         plan.set_fused(bool(args.fused))
+    if args.overlap >= 0:
+        plan.set_overlap(bool(args.overlap))
     if args.ring:
         plan.set_ring(args.ring)
     info = plan.info()

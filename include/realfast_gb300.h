@@ -286,15 +286,29 @@ rf_status rf_plan_set_form(struct rf_plan* plan, int32_t form);
 /* RF_TUNE_RING         chunk slots of the fused pass's ring, 2 .. 8
  *                      (default 3). */
 #define RF_TUNE_RING 5
+/* RF_TUNE_OVERLAP      1: waves hold at most half of RF_TUNE_WAVE_IMAGES
+ *                      images and alternate between the two halves of the
+ *                      scratch, so that one wave's gridding and column pass
+ *                      run on the caller's stream while the previous wave's
+ *                      row pass and finalize run on a second stream of the
+ *                      plan (the column pass at the higher priority, at most
+ *                      one of its blocks per SM, the row pass in short
+ *                      blocks that take the rest); the caller's stream waits
+ *                      for both before the call returns.  0 (default): one
+ *                      wave after another on the caller's stream.  Without
+ *                      effect with RF_TUNE_FUSED, RF_NOISE_CLIPPED and for
+ *                      rendered images.  The autotuner times both. */
+#define RF_TUNE_OVERLAP 6
 rf_status rf_plan_set_tuning(struct rf_plan* plan, int32_t key, int64_t value);
 rf_status rf_plan_get_tuning(const struct rf_plan* plan, int32_t key, int64_t* value);
 
 /*
  * rf_plan_autotune: pick the tuning that searches `vis` fastest and apply
  * it.  Candidates: where the fused pass exists (npix 1024 .. 4096, no
- * clipped noise), RF_TUNE_FUSED on with RF_TUNE_RING 2, 3 and 4 and off, at
- * waves of 2048 and 8192 images, graphs on; elsewhere a ladder of wave sizes
- * (256 .. 8192 images) with RF_TUNE_GRAPHS on and off.  Wave sizes whose
+ * clipped noise), RF_TUNE_FUSED on with RF_TUNE_RING 2, 3 and 4, and off with
+ * RF_TUNE_OVERLAP off and on, at waves of 2048 and 8192 images, graphs on;
+ * elsewhere a ladder of wave sizes (256 .. 8192 images) with RF_TUNE_GRAPHS
+ * on and off, and from 2048 images RF_TUNE_OVERLAP on.  Wave sizes whose
  * column-FFT buffer would not fit in half the free device memory are
  * skipped.  Each candidate is timed with CUDA events on `stream`, after one
  * warm-up, on a search of the segment in which every (DM, dt) is limited to
@@ -314,6 +328,8 @@ typedef struct rf_tune_report {
   int32_t best_ring;
   int32_t tried_fused[16];
   int32_t tried_ring[16];
+  int32_t best_overlap;
+  int32_t tried_overlap[16];
 } rf_tune_report;
 rf_status rf_plan_autotune(struct rf_plan* plan, const void* vis, int32_t nint, void* stream,
                            rf_tune_report* report);

@@ -29,7 +29,7 @@ __all__ = [
     "Stream", "RfStreamInfo", "RfCandidateFeatures", "FEATURES_DTYPE", "rf_candidate_products",
     "RfPeriodicCandidate", "PERIODIC_DTYPE", "rf_periodicity_search", "rf_selftest_bounded_wait",
     "Plan", "CANDIDATE_DTYPE", "STAT_DTYPE", "declared_symbols",
-    "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_MEAN_SUBTRACT", "RF_NOISE_CLIPPED", "RF_TUNE_WIDE_INDEX", "RF_TUNE_FUSED", "RF_TUNE_RING", "RF_STREAM_KEEP_STATS", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
+    "RF_STORE_FP16", "RF_EDGE_PARTIAL", "RF_MEAN_SUBTRACT", "RF_NOISE_CLIPPED", "RF_TUNE_WIDE_INDEX", "RF_TUNE_FUSED", "RF_TUNE_RING", "RF_TUNE_OVERLAP", "RF_STREAM_KEEP_STATS", "RF_HOST_ONLY", "RF_FORM_BATCHED", "RF_FORM_PLAIN",
 ]
 
 RF_OK = 0
@@ -59,6 +59,7 @@ RF_TUNE_GRAPHS = 2
 RF_TUNE_WIDE_INDEX = 3
 RF_TUNE_FUSED = 4
 RF_TUNE_RING = 5
+RF_TUNE_OVERLAP = 6
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
                       "realfast_gb300.h")
@@ -110,7 +111,8 @@ class RfTuneReport(ctypes.Structure):
     _fields_ = [("best_wave_images", ctypes.c_int32), ("best_graphs", ctypes.c_int32), ("ntried", ctypes.c_int32),
                 ("tried_wave_images", ctypes.c_int32 * 16), ("tried_graphs", ctypes.c_int32 * 16),
                 ("tried_ms", ctypes.c_float * 16), ("best_fused", ctypes.c_int32), ("best_ring", ctypes.c_int32),
-                ("tried_fused", ctypes.c_int32 * 16), ("tried_ring", ctypes.c_int32 * 16)]
+                ("tried_fused", ctypes.c_int32 * 16), ("tried_ring", ctypes.c_int32 * 16),
+                ("best_overlap", ctypes.c_int32), ("tried_overlap", ctypes.c_int32 * 16)]
 
 
 class RfServerDesc(ctypes.Structure):
@@ -436,9 +438,9 @@ def rf_plan_autotune(plan, vis, nint: int, stream=None) -> dict:
     rep = RfTuneReport()
     _check(lib().rf_plan_autotune(plan, _ptr(vis), nint, _stream(stream), ctypes.byref(rep)))
     return {"wave_images": rep.best_wave_images, "graphs": rep.best_graphs, "fused": rep.best_fused,
-            "ring": rep.best_ring,
+            "ring": rep.best_ring, "overlap": rep.best_overlap,
             "tried": [(rep.tried_wave_images[i], rep.tried_graphs[i], rep.tried_fused[i], rep.tried_ring[i],
-                       float(rep.tried_ms[i])) for i in range(rep.ntried)]}
+                       rep.tried_overlap[i], float(rep.tried_ms[i])) for i in range(rep.ntried)]}
 
 
 def rf_image_stats_noalloc(half_plane, npix: int, weight: float, stat, stream=None) -> None:
@@ -658,6 +660,10 @@ class Plan:
         """Chunk slots of the fused pass's L2-resident ring (2 .. 8)."""
         rf_plan_set_tuning(self.handle, RF_TUNE_RING, slots)
 
+    def set_overlap(self, enable: bool):
+        """Overlapped waves: one wave's column pass beside the previous wave's row pass."""
+        rf_plan_set_tuning(self.handle, RF_TUNE_OVERLAP, 1 if enable else 0)
+
     def autotune(self, vis, nint=None, stream=None, cache_path=None, key_extra=""):
         """Apply a cached tuning for this shape, or run the autotuner and cache it.
 
@@ -681,16 +687,17 @@ class Plan:
                     cache = json.load(f)
             except (OSError, ValueError):
                 cache = {}
-        if key in cache and "fused" in cache[key]:
+        if key in cache and "overlap" in cache[key]:
             rf_plan_set_tuning(self.handle, RF_TUNE_WAVE_IMAGES, int(cache[key]["wave_images"]))
             rf_plan_set_tuning(self.handle, RF_TUNE_GRAPHS, int(cache[key]["graphs"]))
             rf_plan_set_tuning(self.handle, RF_TUNE_FUSED, int(cache[key]["fused"]))
             rf_plan_set_tuning(self.handle, RF_TUNE_RING, int(cache[key]["ring"]))
+            rf_plan_set_tuning(self.handle, RF_TUNE_OVERLAP, int(cache[key]["overlap"]))
             return dict(cache[key], cached=True)
         res = rf_plan_autotune(self.handle, vis, n, stream)
         if cache_path:
             cache[key] = {"wave_images": res["wave_images"], "graphs": res["graphs"], "fused": res["fused"],
-                          "ring": res["ring"]}
+                          "ring": res["ring"], "overlap": res["overlap"]}
             os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
             with open(cache_path, "w") as f:
                 json.dump(cache, f, indent=1)

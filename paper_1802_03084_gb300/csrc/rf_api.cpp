@@ -56,6 +56,7 @@ constexpr int kRangeEntries = 64;                // target entries per gridding 
 constexpr size_t kPeriodicBudgetBytes = 1ull << 30;  // transformed series per DM batch
 constexpr size_t kPlainBudgetBytes = 4096ull << 20;  // plain form: intermediates of one chunk
 constexpr int kDefaultRing = 3;                      // fused pass: chunk slots of the ring
+constexpr int kOverlapRowItems = 16;                 // overlapped waves: work items per row-pass block
 
 // Round half away from zero: sign(x) floor(|x| + 1/2).
 inline double round_half_away(double x) { return x >= 0.0 ? std::floor(x + 0.5) : -std::floor(-x + 0.5); }
@@ -239,6 +240,7 @@ struct rf_plan {
   int* d_err = nullptr;         // set by a kernel whose bounded wait gave up
   rf::TileMap tmap_T{};         // tensor map of d_T for the row pass (nbox 0: none)
   rf::TileMap tmap_P{};         // tensor map of d_T for the periodicity row pass (N = 1024)
+  rf::TileMap tmap_H[2]{};      // tensor maps of the two halves of d_T (overlapped waves)
   float2* d_stage = nullptr;
   int stage_nint = 0;
 
@@ -270,6 +272,16 @@ struct rf_plan {
   float2* d_Tring = nullptr;
   int ring_alloc = 0;
   rf::TileMap tmap_ring{};
+
+  // overlapped waves (RF_TUNE_OVERLAP): waves of at most half the slots
+  // alternate between the halves of the scratch; wave w + 1's gridding and
+  // column pass run on the caller's stream beside wave w's row pass and
+  // finalize on ostream.  oev: column pass done [2], row pass and finalize
+  // done [2] (per half), and the join back to the caller's stream.
+  bool overlap = false;
+  bool waves_overlap = false;   // the current wave list was built for it
+  cudaStream_t ostream = nullptr;
+  cudaEvent_t oev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 
   // CUDA graph of the batched wave loop for the current image list
   bool use_graphs = true;
@@ -321,11 +333,14 @@ struct rf_plan {
   }
 
   ~rf_plan() {
-    if (!allocs.empty() || !prof.ev.empty() || gstream) {
+    if (!allocs.empty() || !prof.ev.empty() || gstream || ostream) {
       DeviceGuard dg(device);
       drop_graph();
       if (gstream) cudaStreamDestroy(gstream);
       for (cudaEvent_t e : join)
+        if (e) cudaEventDestroy(e);
+      if (ostream) cudaStreamDestroy(ostream);
+      for (cudaEvent_t e : oev)
         if (e) cudaEventDestroy(e);
       for (void* p : allocs) cudaFree(p);
       prof.destroy();
@@ -597,6 +612,14 @@ rf_status build_tables(rf_plan* p) {
   return RF_OK;
 }
 
+// Whether waves can be overlapped: asked for, two halves of the scratch hold
+// a group each, and neither the fused pass nor the clipped noise (whose
+// window buffer is per slot of the whole scratch) is in use.
+bool overlap_possible(const rf_plan* p) {
+  return p->overlap && !p->fused && !(p->flags & RF_NOISE_CLIPPED) &&
+         p->slots_max / 2 >= p->shape.images_per_group;
+}
+
 // Image and group lists for a segment of nint integrations, in (d, s, t') order.
 void build_lists(rf_plan* p, int nint) {
   const int B = p->shape.images_per_group;
@@ -617,10 +640,13 @@ void build_lists(rf_plan* p, int nint) {
         for (int k = 0; k < g.nimg; ++k) p->img_info.push_back(make_int4(d, s, t0 + k, 0));
       }
     }
+  // overlapped waves take half the slots each (see run_waves)
+  p->waves_overlap = overlap_possible(p);
+  const int cap = p->waves_overlap ? p->slots_max / 2 : p->slots_max;
   Wave w{0, 0, 0, 0};
   for (int gi = 0; gi < (int)p->groups.size(); ++gi) {
     const Group& g = p->groups[gi];
-    if (g.img0 + g.nimg - w.img_begin > p->slots_max || gi - w.g_begin >= p->gslots_max) {
+    if (g.img0 + g.nimg - w.img_begin > cap || gi - w.g_begin >= p->gslots_max) {
       w.g_end = gi;
       w.img_end = g.img0;
       p->waves.push_back(w);
@@ -711,6 +737,7 @@ rf_status alloc_wave_scratch(rf_plan* p, int slots) {
   const int nrb = p->shape.partials_per_image;
   p->tmap_T.nbox = 0;  // the maps describe d_T, about to be freed
   p->tmap_P.nbox = 0;
+  p->tmap_H[0].nbox = p->tmap_H[1].nbox = 0;
   if (p->d_T) {
     p->device_bytes -= (uint64_t)p->slots_max * per_slot * sizeof(float2);
     p->dfree(p->d_T);
@@ -750,6 +777,12 @@ rf_status alloc_wave_scratch(rf_plan* p, int slots) {
   if ((p->flags & RF_NOISE_CLIPPED) && (s = p->dalloc(&p->d_clip, (size_t)slots)) != RF_OK) return s;
   const int xb = std::min(256 / (p->npix / 32), p->npix / 2);  // row pairs of a row-pass work item
   encode_tile_map(p, p->tmap_T, p->d_T, p->slots_max, 2 * xb);
+  // the halves of d_T, each a wave's scratch when waves are overlapped
+  const int half = p->slots_max / 2;
+  if (half >= B) {
+    encode_tile_map(p, p->tmap_H[0], p->d_T, half, 2 * xb);
+    encode_tile_map(p, p->tmap_H[1], p->d_T + (size_t)half * per_slot, half, 2 * xb);
+  }
   // the periodicity row pass's tensor-copy tiles (one image's XB rows), at
   // N = 1024, where its transforms fit one warp
   if (p->npix == 1024) encode_tile_map(p, p->tmap_P, p->d_T, p->slots_max, xb);
@@ -1026,6 +1059,64 @@ rf_status resample_all(rf_plan* p, int nint, cudaStream_t st) {
   return RF_OK;
 }
 
+// Overlapped waves (RF_TUNE_OVERLAP).  Wave w images into half w mod 2 of
+// the column-FFT scratch (and of the partials and Parseval sums), so that
+// wave w + 1's gridding and column pass, on `st`, can run while wave w's row
+// pass and finalize run on the plan's second stream.  Each pass does the same
+// arithmetic on the same image as in the serial order and the finalizes keep
+// their order, so results are identical.  The column pass takes the higher
+// priority and at most one block per SM; the row pass runs short-lived blocks
+// of kOverlapRowItems work items, which fill whatever the column pass leaves.
+// Before a half is reused its previous wave's row pass and finalize must be
+// done (an event per half); the caller's stream waits for the last finalize.
+rf_status run_waves_overlapped(rf_plan* p, const SegmentGeom& g, const std::vector<Wave>& waves,
+                               DevStat* d_stats, cudaStream_t st) {
+  int prio_lo = 0, prio_hi = 0;
+  RF_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+  if (!p->ostream) RF_CUDA(cudaStreamCreateWithPriority(&p->ostream, cudaStreamNonBlocking, prio_lo));
+  for (cudaEvent_t& e : p->oev)
+    if (!e) RF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaStream_t so = p->ostream;
+  rf::PassLaunch pc, pr;
+  pc.one_per_sm = true;
+  pc.set_priority = pr.set_priority = true;
+  pc.priority = prio_hi;
+  pr.priority = prio_lo;
+  pr.items_per_block = kOverlapRowItems;
+  const size_t half = (size_t)p->slots_max / 2;
+  const size_t per_slot = (size_t)p->ncol * p->npix;
+  const size_t nrb = (size_t)p->shape.partials_per_image;
+  for (size_t wi = 0; wi < waves.size(); ++wi) {
+    const Wave& w = waves[wi];
+    const int h = (int)(wi & 1);
+    const int ng = w.g_end - w.g_begin;
+    const int ni = w.img_end - w.img_begin;
+    float2* T = p->d_T + h * half * per_slot;
+    StatPartial* part = p->d_partials + h * half * nrb;
+    float* colsq = p->d_colsq + h * half * p->ncol;
+    float* mean0 = p->d_mean0 + h * half;
+    RF_TIMED(p->prof, K_GRID_CELLS, st,
+             rf::launch_grid_cells(g, p->tb, p->d_groups, w.g_begin, ng, p->d_cellbuf, st));
+    if (wi >= 2) RF_CUDA(cudaStreamWaitEvent(st, p->oev[2 + h], 0));
+    RF_TIMED(p->prof, K_GRID_COLFFT, st,
+             rf::launch_colfft(g, p->tb, p->d_groups, w.g_begin, ng, w.img_begin, p->d_cellbuf, T, colsq, mean0,
+                               st, &pc));
+    RF_CUDA(cudaEventRecord(p->oev[h], st));
+    RF_CUDA(cudaStreamWaitEvent(so, p->oev[h], 0));
+    RF_TIMED(p->prof, K_ROWFFT_STATS, so,
+             rf::launch_rowfft_stats(g, p->tb, T, ni, w.img_begin, p->d_weight, part, nullptr,
+                                     p->tmap_H[h].nbox > 0 ? &p->tmap_H[h] : nullptr, p->d_err, so, nullptr,
+                                     &pr));
+    RF_TIMED(p->prof, K_FINALIZE, so,
+             rf::launch_finalize(g, part, colsq, mean0, p->d_img_info, p->d_weight, ni, w.img_begin, p->threshold,
+                                 p->d_cands, p->d_ncand, p->img_cap, d_stats, so, false));
+    RF_CUDA(cudaEventRecord(p->oev[2 + h], so));
+  }
+  RF_CUDA(cudaEventRecord(p->oev[4], so));
+  RF_CUDA(cudaStreamWaitEvent(st, p->oev[4], 0));
+  return RF_OK;
+}
+
 // Pass A / pass B / finalize over the image list currently on the device.
 rf_status run_waves(rf_plan* p, int nint, const std::vector<Wave>& waves, int nimg_total, DevStat* d_stats,
                     float* d_images, cudaStream_t st) {
@@ -1034,6 +1125,8 @@ rf_status run_waves(rf_plan* p, int nint, const std::vector<Wave>& waves, int ni
            rf::launch_weights(p->d_img_info, nimg_total, (p->flags & RF_EDGE_PARTIAL) != 0, g, p->tb,
                               (double)p->n_on, p->d_weight, st));
   const bool fused = d_images == nullptr && &waves == &p->waves && use_fused(p);
+  if (!fused && d_images == nullptr && &waves == &p->waves && p->waves_overlap && overlap_possible(p))
+    return run_waves_overlapped(p, g, waves, d_stats, st);
   for (size_t wi = 0; wi < waves.size(); ++wi) {
     const Wave& w = waves[wi];
     const int ng = w.g_end - w.g_begin;
@@ -1099,7 +1192,9 @@ rf_status run_waves_graph(rf_plan* p, int nint, int nimg, DevStat* d_stats, cuda
       return s;
     }
     if (ec != cudaSuccess) return fail(RF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ec));
-    const cudaError_t ei = cudaGraphInstantiate(&gc.exec, g, 0);
+    // overlapped waves carry per-launch priorities on their kernel nodes
+    const cudaError_t ei =
+        cudaGraphInstantiate(&gc.exec, g, p->waves_overlap ? cudaGraphInstantiateFlagUseNodePriority : 0);
     cudaGraphDestroy(g);
     if (ei != cudaSuccess) return fail(RF_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ei));
     p->prof.take(u0, &gc.ev, &gc.kind);
@@ -1905,6 +2000,17 @@ rf_status rf_plan_set_tuning(rf_plan* p, int32_t key, int64_t value) {
     if (!bg.owned) return fail(RF_ERR_BUSY, "plan is in use by another call");
     DeviceGuard dg(p->device);
     p->fused = value != 0;
+    p->cached_nint = -1;  // overlapped waves (half size) are built only without the fused pass
+    p->drop_graph();
+    return RF_OK;
+  }
+  if (key == RF_TUNE_OVERLAP) {
+    if (value != 0 && value != 1) return fail(RF_ERR_INVALID_ARG, "RF_TUNE_OVERLAP takes 0 or 1");
+    BusyGuard bg(&p->busy);
+    if (!bg.owned) return fail(RF_ERR_BUSY, "plan is in use by another call");
+    DeviceGuard dg(p->device);
+    p->overlap = value != 0;
+    p->cached_nint = -1;  // the waves' size depends on it
     p->drop_graph();
     return RF_OK;
   }
@@ -1945,7 +2051,7 @@ rf_status rf_plan_autotune(rf_plan* p, const void* vis, int32_t nint, void* stre
   RF_CUDA(cudaMemGetInfo(&free_b, &total_b));
   const size_t have = free_b / 2 + (size_t)p->slots_max * per_slot;  // the current scratch is reusable
   struct Cand {
-    int wave, graphs, fused, ring;
+    int wave, graphs, fused, ring, overlap;
   };
   std::vector<Cand> cands;
   auto fits = [&](int w) { return (size_t)std::max(w, B) * per_slot <= have; };
@@ -1953,8 +2059,9 @@ rf_status rf_plan_autotune(rf_plan* p, const void* vis, int32_t nint, void* stre
   if (can_fuse) {
     for (int w : {2048, 8192}) {
       if (!fits(w)) continue;
-      for (int ring : {2, 3, 4}) cands.push_back({w, 1, 1, ring});
-      cands.push_back({w, 1, 0, p->ring});
+      for (int ring : {2, 3, 4}) cands.push_back({w, 1, 1, ring, 0});
+      cands.push_back({w, 1, 0, p->ring, 0});
+      if (w / 2 >= B) cands.push_back({w, 1, 0, p->ring, 1});
       if (w >= nimg) break;
     }
   } else {
@@ -1962,11 +2069,13 @@ rf_status rf_plan_autotune(rf_plan* p, const void* vis, int32_t nint, void* stre
       const int wc = std::max(w, B);
       if (!fits(wc)) continue;
       if (!cands.empty() && cands.back().wave >= nimg) break;
-      cands.push_back({wc, 1, 0, p->ring});
-      cands.push_back({wc, 0, 0, p->ring});
+      cands.push_back({wc, 1, 0, p->ring, 0});
+      cands.push_back({wc, 0, 0, p->ring, 0});
+      if (wc >= 2048 && wc / 2 >= B && !(p->flags & RF_NOISE_CLIPPED)) cands.push_back({wc, 1, 0, p->ring, 1});
     }
   }
-  if (cands.empty()) cands.push_back({p->slots_max, p->use_graphs ? 1 : 0, p->fused ? 1 : 0, p->ring});
+  if (cands.empty())
+    cands.push_back({p->slots_max, p->use_graphs ? 1 : 0, p->fused ? 1 : 0, p->ring, p->overlap ? 1 : 0});
   // timing search: every (DM, dt) limited to its first nint/4 integrations
   const int span = nint >= 256 ? nint / 4 : 0;
   const bool prof_was = p->prof.on;
@@ -1990,6 +2099,8 @@ rf_status rf_plan_autotune(rf_plan* p, const void* vis, int32_t nint, void* stre
       if (s == RF_OK && c.fused && p->ring != c.ring) s = alloc_ring(p, c.ring);
       p->use_graphs = c.graphs != 0;
       p->fused = c.fused != 0;
+      p->overlap = c.overlap != 0;
+      p->cached_nint = -1;
       p->drop_graph();
     }
     if (s != RF_OK) break;
@@ -2015,6 +2126,7 @@ rf_status rf_plan_autotune(rf_plan* p, const void* vis, int32_t nint, void* stre
       report->tried_graphs[ntried] = c.graphs;
       report->tried_fused[ntried] = c.fused;
       report->tried_ring[ntried] = c.ring;
+      report->tried_overlap[ntried] = c.overlap;
       report->tried_ms[ntried] = ms;
     }
     ++ntried;
@@ -2033,12 +2145,15 @@ rf_status rf_plan_autotune(rf_plan* p, const void* vis, int32_t nint, void* stre
     if (best.fused && p->ring != best.ring && (s = alloc_ring(p, best.ring)) != RF_OK) return s;
     p->use_graphs = best.graphs != 0;
     p->fused = best.fused != 0;
+    p->overlap = best.overlap != 0;
+    p->cached_nint = -1;
     p->drop_graph();
   }
   if (report) {
     report->best_wave_images = best.wave;
     report->best_graphs = best.graphs;
     report->best_fused = best.fused;
+    report->best_overlap = best.overlap;
     report->best_ring = p->ring;
     report->ntried = std::min(ntried, 16);
   }
@@ -2061,6 +2176,10 @@ rf_status rf_plan_get_tuning(const rf_plan* p, int32_t key, int64_t* value) {
   }
   if (key == RF_TUNE_RING) {
     *value = p->ring;
+    return RF_OK;
+  }
+  if (key == RF_TUNE_OVERLAP) {
+    *value = p->overlap ? 1 : 0;
     return RF_OK;
   }
   if (key != RF_TUNE_WAVE_IMAGES) return fail(RF_ERR_INVALID_ARG, "unknown tuning key %d", key);

@@ -86,6 +86,21 @@ struct TileMap {
   int rows;
 };
 
+// Launch options of the column and row passes when the waves of a search
+// are overlapped (wave w + 1's column pass beside wave w's row pass, on two
+// streams).  one_per_sm: the column pass asks for enough shared memory that
+// a second column block no longer fits an SM, while a row block still does;
+// items_per_block > 0: the row pass runs blocks of that many work items
+// instead of one persistent block per slot, so that blocks of the two passes
+// can take turns on an SM; priority (if set_priority): the launch's
+// scheduling priority (lower values first).
+struct PassLaunch {
+  bool one_per_sm = false;
+  int items_per_block = 0;
+  bool set_priority = false;
+  int priority = 0;
+};
+
 // Boxes of at most 256 rows (a multiple of 8) covering ncol rows.
 inline void tile_boxes(int ncol, int* nbox, int* rows) {
   const int n0 = (ncol + 255) / 256;
@@ -226,7 +241,7 @@ cudaError_t launch_grid_cells(const SegmentGeom& g, const DevTables& tb, const G
 // mean0[slot] = Re H(u = 0, v = 0).
 cudaError_t launch_colfft(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin,
                           int ngroups, int img_base, const float2* cellbuf, float2* Tbuf, float* colsq,
-                          float* mean0, cudaStream_t st);
+                          float* mean0, cudaStream_t st, const PassLaunch* pl = nullptr);
 
 // Fused column + row pass (npix 1024 .. 4096) of the chunks [0, nchunks)
 // of one wave (chunks[] on the device, groups indexed absolutely, cellbuf
@@ -254,7 +269,8 @@ cudaError_t launch_clip_window(const SegmentGeom& g, const float* colsq, const f
 // the kept-pixel sums of the clipped noise.
 cudaError_t launch_rowfft_stats(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, int nimg,
                                 int img_base, const double* weight, StatPartial* partials, float* images,
-                                const TileMap* tm, int* err, cudaStream_t st, const float2* clip = nullptr);
+                                const TileMap* tm, int* err, cudaStream_t st, const float2* clip = nullptr,
+                                const PassLaunch* pl = nullptr);
 
 // Reduce row-block partials, compute sigma / snr, append candidates and
 // (optionally) per-image stats for images [img_base, img_base + nimg).

@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <utility>
 
 #include "rf_engine.h"
 #include "rf_async.cuh"
@@ -988,6 +989,45 @@ int max_dynamic_smem(Kernel kern) {
   return optin - (int)fa.sharedSizeBytes;
 }
 
+// Launch `kern`, with the scheduling priority of `pl` where it sets one (a
+// launch attribute, so that a captured graph keeps it on the kernel node).
+template <class... P, class... A>
+cudaError_t launch_with(void (*kern)(P...), dim3 grid, dim3 block, int smem, cudaStream_t st,
+                        const PassLaunch* pl, A&&... args) {
+  if (pl == nullptr || !pl->set_priority) {
+    kern<<<grid, block, smem, st>>>(std::forward<A>(args)...);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributePriority;
+  at[0].val.priority = pl->priority;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
+
+// Dynamic shared memory of a column-pass block that keeps a second column
+// block off an SM (two such blocks and their reserved shares exceed the
+// SM's shared memory) while one row-pass block of `row_smem` bytes still
+// fits beside it.  `smem` if that cannot be had (or is already so).
+inline int one_per_sm_smem(int smem, int row_smem, int smem_max) {
+  int dev = 0, sm_smem = 0, reserved = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return smem;
+  }
+  const int floor = sm_smem / 2 - reserved + 16;
+  if (smem >= floor || floor > smem_max || floor + row_smem + 2 * reserved > sm_smem) return smem;
+  return floor;
+}
+
 
 
 // Periodicity row pass (Sec. 3.1 footnote).  A pair is the two quadrature
@@ -1271,11 +1311,15 @@ cudaError_t run_rowfft_power(const SegmentGeom& g, const DevTables& tb, const fl
 
 
 template <int N>
+int rowfft_tile_rows(int ncol);
+
+template <int N>
 cudaError_t run_colfft(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin, int ngroups,
                        int img_base, const float2* cellbuf, float2* Tbuf, float* colsq, float* mean0,
-                       cudaStream_t st) {
+                       cudaStream_t st, const PassLaunch* pl) {
   using C = ColCfg<N>;
-  const int smem = C::SMEM_FIXED + g.max_cells * C::SMEM_PER_CELL;
+  using K = ImgCfg<N>;
+  int smem = C::SMEM_FIXED + g.max_cells * C::SMEM_PER_CELL;
   const int smem_max = max_dynamic_smem(k_colfft<N>);
   if (smem > smem_max) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_colfft<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
@@ -1284,9 +1328,12 @@ cudaError_t run_colfft(const SegmentGeom& g, const DevTables& tb, const Group* g
                            cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   if (ngroups <= 0) return cudaSuccess;
+  if (pl != nullptr && pl->one_per_sm)
+    smem = one_per_sm_smem(smem, K::SMEM_B_FIXED + (K::TILE_TMA ? 1024 : 0) + rowfft_tile_rows<N>(g.ncol) * K::CH * 16,
+                           smem_max);
   dim3 grid(ngroups, g.ncol);
-  k_colfft<N><<<grid, C::THREADS, smem, st>>>(g, tb, groups, g_begin, img_base, cellbuf, Tbuf, colsq, mean0);
-  return cudaGetLastError();
+  return launch_with(k_colfft<N>, grid, dim3(C::THREADS), smem, st, pl, g, tb, groups, g_begin, img_base, cellbuf,
+                     Tbuf, colsq, mean0);
 }
 
 // Rows of the row-pass tile: ncol, or the boxes' total under tensor copies.
@@ -1301,7 +1348,8 @@ int rowfft_tile_rows(int ncol) {
 template <int N, bool CLIP>
 cudaError_t run_rowfft_stats_k(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, int nimg,
                                int img_base, const double* weight, StatPartial* partials, float* images,
-                               const TileMap* tm, int* err, cudaStream_t st, const float2* clip) {
+                               const TileMap* tm, int* err, cudaStream_t st, const float2* clip,
+                               const PassLaunch* pl) {
   using K = ImgCfg<N>;
   const int smem = K::SMEM_B_FIXED + (K::TILE_TMA ? 1024 : 0) + rowfft_tile_rows<N>(g.ncol) * K::CH * 16;
   auto kern = k_rowfft_stats<N, CLIP>;
@@ -1316,23 +1364,28 @@ cudaError_t run_rowfft_stats_k(const SegmentGeom& g, const DevTables& tb, const 
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, K::THREADS_B, smem);
   if (e != cudaSuccess) return e;
   const long nitems = (long)nimg * (N / K::RB);
-  const long grid = std::min<long>(nitems, (long)std::max(per_sm, 1) * sm_count());
+  long grid = std::min<long>(nitems, (long)std::max(per_sm, 1) * sm_count());
+  // short-lived blocks of items_per_block items (the kernel strides by the grid)
+  if (pl != nullptr && pl->items_per_block > 0)
+    grid = std::max(grid, std::min<long>((nitems + pl->items_per_block - 1) / pl->items_per_block, INT_MAX));
   const bool tma = K::TILE_TMA && tm != nullptr && tm->nbox > 0 && err != nullptr;
   CUtensorMap none;
   memset(&none, 0, sizeof(none));
-  kern<<<(int)grid, K::THREADS_B, smem, st>>>(g, tb, Tbuf, nimg, img_base, weight, partials, images,
-                                              tma ? tm->map : none, tma ? tm->nbox : 0, tma ? tm->rows : 0, err,
-                                              clip);
-  return cudaGetLastError();
+  return launch_with(kern, dim3((unsigned)grid), dim3(K::THREADS_B), smem, st, pl, g, tb, Tbuf, nimg, img_base,
+                     weight, partials, images, tma ? tm->map : none, tma ? tm->nbox : 0, tma ? tm->rows : 0, err,
+                     clip);
 }
 
 template <int N>
 cudaError_t run_rowfft_stats(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, int nimg,
                              int img_base, const double* weight, StatPartial* partials, float* images,
-                             const TileMap* tm, int* err, cudaStream_t st, const float2* clip) {
+                             const TileMap* tm, int* err, cudaStream_t st, const float2* clip,
+                             const PassLaunch* pl) {
   if (clip != nullptr)
-    return run_rowfft_stats_k<N, true>(g, tb, Tbuf, nimg, img_base, weight, partials, images, tm, err, st, clip);
-  return run_rowfft_stats_k<N, false>(g, tb, Tbuf, nimg, img_base, weight, partials, images, tm, err, st, nullptr);
+    return run_rowfft_stats_k<N, true>(g, tb, Tbuf, nimg, img_base, weight, partials, images, tm, err, st, clip,
+                                       pl);
+  return run_rowfft_stats_k<N, false>(g, tb, Tbuf, nimg, img_base, weight, partials, images, tm, err, st, nullptr,
+                                      pl);
 }
 
 template <int N>
@@ -1386,10 +1439,11 @@ void fill_shape(ImageKernelShape* o) {
 
 #define RF_INSTANTIATE_IMAGE(N)                                                                              \
   template cudaError_t run_colfft<N>(const SegmentGeom&, const DevTables&, const Group*, int, int, int,      \
-                                     const float2*, float2*, float*, float*, cudaStream_t);                 \
+                                     const float2*, float2*, float*, float*, cudaStream_t,                  \
+                                     const PassLaunch*);                                                    \
   template cudaError_t run_rowfft_stats<N>(const SegmentGeom&, const DevTables&, const float2*, int, int,    \
                                            const double*, StatPartial*, float*, const TileMap*, int*,       \
-                                           cudaStream_t, const float2*);                                    \
+                                           cudaStream_t, const float2*, const PassLaunch*);                 \
   template void fill_shape<N>(ImageKernelShape*);                                                           \
   template cudaError_t run_rowfft_power<N>(const SegmentGeom&, const DevTables&, const float2*, const int4*, \
                                            int, StatPartial*, const TileMap*, int*, cudaStream_t);

@@ -576,10 +576,11 @@ cudaError_t launch_finalize(const SegmentGeom& g, const StatPartial* partials, c
 // --------------------------------------------------------------- dispatch --
 template <int N>
 cudaError_t run_colfft(const SegmentGeom&, const DevTables&, const Group*, int, int, int, const float2*, float2*,
-                       float*, float*, cudaStream_t);
+                       float*, float*, cudaStream_t, const PassLaunch*);
 template <int N>
 cudaError_t run_rowfft_stats(const SegmentGeom&, const DevTables&, const float2*, int, int, const double*,
-                             StatPartial*, float*, const TileMap*, int*, cudaStream_t, const float2*);
+                             StatPartial*, float*, const TileMap*, int*, cudaStream_t, const float2*,
+                             const PassLaunch*);
 template <int N>
 void fill_shape(ImageKernelShape*);
 template <int N>
@@ -623,11 +624,11 @@ cudaError_t launch_image_fused(const SegmentGeom& g, const DevTables& tb, const 
 
 cudaError_t launch_colfft(const SegmentGeom& g, const DevTables& tb, const Group* groups, int g_begin,
                           int ngroups, int img_base, const float2* cellbuf, float2* Tbuf, float* colsq,
-                          float* mean0, cudaStream_t st) {
+                          float* mean0, cudaStream_t st, const PassLaunch* pl) {
   switch (g.npix) {
 #define RF_CASE(N) \
   case N:          \
-    return run_colfft<N>(g, tb, groups, g_begin, ngroups, img_base, cellbuf, Tbuf, colsq, mean0, st);
+    return run_colfft<N>(g, tb, groups, g_begin, ngroups, img_base, cellbuf, Tbuf, colsq, mean0, st, pl);
     RF_FOR_EACH_N(RF_CASE)
 #undef RF_CASE
     default:
@@ -637,11 +638,12 @@ cudaError_t launch_colfft(const SegmentGeom& g, const DevTables& tb, const Group
 
 cudaError_t launch_rowfft_stats(const SegmentGeom& g, const DevTables& tb, const float2* Tbuf, int nimg,
                                 int img_base, const double* weight, StatPartial* partials, float* images,
-                                const TileMap* tm, int* err, cudaStream_t st, const float2* clip) {
+                                const TileMap* tm, int* err, cudaStream_t st, const float2* clip,
+                                const PassLaunch* pl) {
   switch (g.npix) {
 #define RF_CASE(N) \
   case N:          \
-    return run_rowfft_stats<N>(g, tb, Tbuf, nimg, img_base, weight, partials, images, tm, err, st, clip);
+    return run_rowfft_stats<N>(g, tb, Tbuf, nimg, img_base, weight, partials, images, tm, err, st, clip, pl);
     RF_FOR_EACH_N(RF_CASE)
 #undef RF_CASE
     default:

@@ -228,6 +228,20 @@ def test_fused_and_ring_tuning_keys(L):
             assert e.value.status == rf.RF_ERR_INVALID_ARG
 
 
+def test_overlap_tuning_key(L):
+    kw = _desc_kwargs(synth.config("tiny"))
+    with rf.Plan(**kw) as p:
+        assert rf.rf_plan_get_tuning(p.handle, rf.RF_TUNE_OVERLAP) == 0
+        p.set_overlap(True)
+        assert rf.rf_plan_get_tuning(p.handle, rf.RF_TUNE_OVERLAP) == 1
+        p.set_overlap(False)
+        assert rf.rf_plan_get_tuning(p.handle, rf.RF_TUNE_OVERLAP) == 0
+        for bad in (2, -1):
+            with pytest.raises(rf.RfError) as e:
+                rf.rf_plan_set_tuning(p.handle, rf.RF_TUNE_OVERLAP, bad)
+            assert e.value.status == rf.RF_ERR_INVALID_ARG
+
+
 def test_noalloc_rejects_host_memory(L):
     # a host (numpy) buffer is not device memory of a current device: the call
     # rejects it before any launch (on a machine without a GPU as on one with)
