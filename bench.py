@@ -345,7 +345,8 @@ def write_traffic(raw_csv, images_per_launch, command, workload, path=None):
     with open(raw_csv, newline="") as f:
         rows = [r for r in csv.reader(f) if r]
     hdr = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
-    names, units, data = rows[hdr], rows[hdr + 1], rows[hdr + 2:]
+    names, units = rows[hdr], rows[hdr + 1]
+    data = [r for r in rows[hdr + 2:] if len(r) == len(names)]  # launch rows (not ncu's notes)
     col = {n: i for i, n in enumerate(names)}
 
     def value(r, metric):

@@ -53,3 +53,20 @@ def test_traffic_is_taken_only_for_matching_sources(tmp_path, monkeypatch):
     assert bench.load_traffic("rowfft_stats", 1000) is not None
     (csrc / bench.KERNEL_SOURCES[0]).write_bytes(b"changed")
     assert bench.load_traffic("rowfft_stats", 1000) is None
+
+
+def test_write_traffic_reads_concatenated_logs_with_ncu_notes(tmp_path):
+    # one ncu log file per kernel, concatenated: each starts with ncu's one-field
+    # notes and repeats the header and unit rows; only launch rows count
+    parts = []
+    for i in range(2):
+        one = tmp_path / f"k{i}.csv"
+        _raw_csv(one)
+        parts.append("==WARNING== Note: a profiler note\n==PROF== Connected to process 1\n" + one.read_text())
+    raw = tmp_path / "all.csv"
+    raw.write_text("".join(parts))
+    doc = bench.write_traffic(str(raw), 256, "ncu ...", "realtime", path=str(tmp_path / "traffic.json"))
+    k = doc["kernels"]
+    assert k["grid_cells"]["launches_captured"] == 2
+    assert k["grid_cells"]["dram_bytes_per_launch"] == 185.5e6 + 15.4e6
+    assert k["rowfft_stats"]["launches_captured"] == 4
