@@ -308,7 +308,9 @@ rf_status rf_plan_get_tuning(const struct rf_plan* plan, int32_t key, int64_t* v
  * clipped noise), RF_TUNE_FUSED on with RF_TUNE_RING 2, 3 and 4, and off with
  * RF_TUNE_OVERLAP off and on, at waves of 2048 and 8192 images, graphs on;
  * elsewhere a ladder of wave sizes (256 .. 8192 images) with RF_TUNE_GRAPHS
- * on and off, and from 2048 images RF_TUNE_OVERLAP on.  Wave sizes whose
+ * on and off, and from 2048 images RF_TUNE_OVERLAP on.  Before either, waves
+ * of one, two and four image groups (below 256 images) whose column-FFT
+ * buffer fits the device's L2 cache, separate passes, graphs on.  Wave sizes whose
  * column-FFT buffer would not fit in half the free device memory are
  * skipped.  Each candidate is timed with CUDA events on `stream`, after one
  * warm-up, on a search of the segment in which every (DM, dt) is limited to

@@ -2056,6 +2056,15 @@ rf_status rf_plan_autotune(rf_plan* p, const void* vis, int32_t nint, void* stre
   std::vector<Cand> cands;
   auto fits = [&](int w) { return (size_t)std::max(w, B) * per_slot <= have; };
   const bool can_fuse = p->chunk_images > 0 && !(p->flags & RF_NOISE_CLIPPED);
+  // waves whose column-FFT output fits the L2 cache (one to four groups), so
+  // that the row pass may find it there instead of in HBM
+  int l2 = 0;
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, p->device) != cudaSuccess) {
+    cudaGetLastError();
+    l2 = 0;
+  }
+  for (int w = B; w <= 4 * B && w < 256; w *= 2)
+    if ((size_t)w * per_slot <= (size_t)l2 && fits(w) && w < nimg) cands.push_back({w, 1, 0, p->ring, 0});
   if (can_fuse) {
     for (int w : {2048, 8192}) {
       if (!fits(w)) continue;
@@ -2076,6 +2085,7 @@ rf_status rf_plan_autotune(rf_plan* p, const void* vis, int32_t nint, void* stre
   }
   if (cands.empty())
     cands.push_back({p->slots_max, p->use_graphs ? 1 : 0, p->fused ? 1 : 0, p->ring, p->overlap ? 1 : 0});
+
   // timing search: every (DM, dt) limited to its first nint/4 integrations
   const int span = nint >= 256 ? nint / 4 : 0;
   const bool prof_was = p->prof.on;
