@@ -1069,6 +1069,9 @@ rf_status resample_all(rf_plan* p, int nint, cudaStream_t st) {
 // of kOverlapRowItems work items, which fill whatever the column pass leaves.
 // Before a half is reused its previous wave's row pass and finalize must be
 // done (an event per half); the caller's stream waits for the last finalize.
+rf_status overlapped_loop(rf_plan* p, const SegmentGeom& g, const std::vector<Wave>& waves, DevStat* d_stats,
+                         cudaStream_t st, const rf::PassLaunch& pc, const rf::PassLaunch& pr);
+
 rf_status run_waves_overlapped(rf_plan* p, const SegmentGeom& g, const std::vector<Wave>& waves,
                                DevStat* d_stats, cudaStream_t st) {
   int prio_lo = 0, prio_hi = 0;
@@ -1083,6 +1086,21 @@ rf_status run_waves_overlapped(rf_plan* p, const SegmentGeom& g, const std::vect
   pc.priority = prio_hi;
   pr.priority = prio_lo;
   pr.items_per_block = kOverlapRowItems;
+  // the caller's stream waits for the second stream however the loop ends
+  // (a failed launch leaves no work of the plan unjoined behind the call)
+  const rf_status s = overlapped_loop(p, g, waves, d_stats, st, pc, pr);
+  const bool joined =
+      cudaEventRecord(p->oev[4], so) == cudaSuccess && cudaStreamWaitEvent(st, p->oev[4], 0) == cudaSuccess;
+  if (s != RF_OK) return s;
+  if (!joined)
+    return fail(RF_ERR_CUDA, "joining the overlapped waves' streams: %s", cudaGetErrorString(cudaGetLastError()));
+  return RF_OK;
+}
+
+// The wave loop of run_waves_overlapped (streams and events set up).
+rf_status overlapped_loop(rf_plan* p, const SegmentGeom& g, const std::vector<Wave>& waves, DevStat* d_stats,
+                         cudaStream_t st, const rf::PassLaunch& pc, const rf::PassLaunch& pr) {
+  cudaStream_t so = p->ostream;
   const size_t half = (size_t)p->slots_max / 2;
   const size_t per_slot = (size_t)p->ncol * p->npix;
   const size_t nrb = (size_t)p->shape.partials_per_image;
@@ -1112,8 +1130,6 @@ rf_status run_waves_overlapped(rf_plan* p, const SegmentGeom& g, const std::vect
                                  p->d_cands, p->d_ncand, p->img_cap, d_stats, so, false));
     RF_CUDA(cudaEventRecord(p->oev[2 + h], so));
   }
-  RF_CUDA(cudaEventRecord(p->oev[4], so));
-  RF_CUDA(cudaStreamWaitEvent(st, p->oev[4], 0));
   return RF_OK;
 }
 
